@@ -1,0 +1,227 @@
+/*
+ * lts.h -- C ABI of liblts.so: local time stepping (LTS3) for the TRiSK
+ * C-grid shallow-water equations on a Voronoi mesh, on one GB300 GPU.
+ *
+ * Method: Capodaglio & Petersen, "Local time stepping for the shallow water
+ * equations in MPAS" (arXiv:2106.07154), Section 2 (Algorithms 2.1 and 2.2,
+ * index sets of Eqs. (3)-(5)) and Appendix B (TRiSK operators).
+ *
+ * Conventions shared by every entry point
+ *  - Return value: LTS_OK (0) or a negative LTS_E* code; a message for the
+ *    last failure of the calling thread is in lts_last_error().  No C++
+ *    exception crosses this boundary.
+ *  - The caller owns every array it passes; the library copies what it keeps.
+ *    Arrays are host memory unless the name says otherwise.
+ *  - Indices are 0-based int32.  Lengths in metres, times in seconds.
+ *  - Orientation: the normal n_e of edge e points out of cellsOnEdge[2e+0]
+ *    (n_{e,i} = +1 for that cell, Appendix B) and verticesOnEdge[2e+1] is
+ *    the vertex in direction k x n_e (t_{e,v} = +1).  The mesh builders set
+ *    cellsOnEdge[2e+0] to the larger of the two cell indices, the rule of the
+ *    Remark in Appendix B.  The library never re-derives the orientation:
+ *    normal velocities u_e keep the caller's sign convention on input and
+ *    on output.
+ *  - Handles are opaque and owned by the library; destroy them with the
+ *    matching lts_*_destroy.  A state holds its mesh and regions alive
+ *    (reference counted), so destroy order does not matter.
+ */
+#ifndef LTS_H
+#define LTS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LTS_OK          0
+#define LTS_EINVAL     -1   /* bad argument, size or mesh                      */
+#define LTS_ENOMEM     -2   /* host or device allocation failed                */
+#define LTS_ECUDA      -3   /* a CUDA runtime call failed (message says which) */
+#define LTS_ENONFINITE -4   /* a thickness became <= 0 or non-finite           */
+#define LTS_ETIMEOUT   -5   /* a bounded device wait gave up                   */
+#define LTS_ENODEV     -6   /* no usable CUDA device                           */
+
+/* ------------------------------------------------------------------------
+ * Mesh description (MPAS-style arrays, host memory).
+ *   Appendix B: cells (Voronoi generators) carry h, b, K; edges carry the
+ *   normal velocity u_e; vertices (dual triangles) carry q_v.
+ *   l_e = dvEdge (primal edge length), d_e = dcEdge (cell-to-cell distance),
+ *   A_i = areaCell, A_v = areaTriangle, A_{i,v} = kiteAreasOnVertex.
+ * Layout: edgesOnCell/cellsOnCell/verticesOnCell are [nCells*maxEdges],
+ *   listed counter-clockwise; verticesOnCell[i*maxEdges+j] lies between
+ *   edgesOnCell[..+j] and edgesOnCell[..+j+1] (mod nEdgesOnCell[i]);
+ *   cellsOnCell[..+j] is the neighbour across edgesOnCell[..+j].
+ *   cellsOnEdge/verticesOnEdge are [nEdges*2]; edgesOnVertex/cellsOnVertex/
+ *   kiteAreasOnVertex are [nVertices*3] (kite k belongs to cellsOnVertex k).
+ * Optional arrays may be NULL: positions, bottom (flat), edgesOnEdge,
+ *   nEdgesOnEdge, weightsOnEdge ([nEdges*2*maxEdges]; if present they are
+ *   checked against the weights the library derives from the kite areas).
+ * Builders fill every required array with malloc'ed memory; free it with
+ *   lts_mesh_desc_free.  A caller-filled desc is never freed by the library.
+ * ------------------------------------------------------------------------ */
+typedef struct lts_mesh_desc {
+    int32_t nCells, nEdges, nVertices, maxEdges;
+    int32_t on_sphere;               /* 1: sphere of `radius`; 0: doubly periodic plane */
+    double radius;                   /* sphere radius [m]                                */
+    double period_x, period_y;       /* plane periods [m]                                */
+    double *xCell, *yCell, *zCell;   /* [nCells]     Cartesian positions (z = 0 on plane) */
+    double *xEdge, *yEdge, *zEdge;   /* [nEdges]     x_e                                  */
+    double *xVertex, *yVertex, *zVertex; /* [nVertices]                                   */
+    int32_t *nEdgesOnCell;           /* [nCells]                                          */
+    int32_t *edgesOnCell, *cellsOnCell, *verticesOnCell; /* [nCells*maxEdges]             */
+    int32_t *cellsOnEdge, *verticesOnEdge;               /* [nEdges*2]                    */
+    int32_t *edgesOnVertex, *cellsOnVertex;              /* [nVertices*3]                 */
+    double *areaCell;                /* [nCells]    A_i                                   */
+    double *areaTriangle;            /* [nVertices] A_v                                   */
+    double *kiteAreasOnVertex;       /* [nVertices*3] A_{i,v}                             */
+    double *dcEdge, *dvEdge;         /* [nEdges]    d_e, l_e                              */
+    double *fVertex;                 /* [nVertices] Coriolis parameter f_v                */
+    double *bottom;                  /* [nCells]    bottom topography b_i (NULL = 0)      */
+    int32_t *nEdgesOnEdge, *edgesOnEdge;  /* optional MPAS tables                         */
+    double *weightsOnEdge;                /* optional, w_{e,e'} of Appendix B Eq. (weights) */
+} lts_mesh_desc;
+
+/* One refined cap of a spherical density function.  The target spacing is
+ * s(x) = min over caps of  1/ratio + (1 - 1/ratio) (1 + tanh((d - radius)/width))/2
+ * (relative to the coarse spacing, d = great-circle angle from the cap
+ * centre) and the SCVT density is rho = s^-4, so `ratio` is the
+ * coarse-to-fine resolution ratio.  Angles in radians. */
+typedef struct lts_cap {
+    double lon, lat, radius, width, ratio;
+} lts_cap;
+
+typedef struct lts_density {
+    int32_t ncaps;                   /* 0 = uniform density                               */
+    lts_cap cap[4];
+} lts_density;
+
+/* Doubly periodic plane of regular hexagons (Appendix B geometry with
+ * x_e at the cell-pair midpoint).  nx*ny cells, cell spacing dc [m],
+ * Coriolis parameter f0 (f-plane).  ny must be even, nx,ny >= 4.
+ * Cells are numbered row by row.  Errors: LTS_EINVAL, LTS_ENOMEM. */
+int lts_build_hex_periodic(int32_t nx, int32_t ny, double dc, double f0,
+                           lts_mesh_desc* out);
+
+/* Spherical centroidal Voronoi tessellation (SCVT) with n generators on a
+ * sphere of `radius`, made by `lloyd_iters` Lloyd iterations from a seeded
+ * random start drawn with point density rho^(1/2) (rho from `rho`, NULL =
+ * uniform).  Voronoi vertices are circumcentres of the spherical Delaunay
+ * triangles; kite areas are signed spherical areas of (x_i, x_e1, x_v, x_e2);
+ * f_v = 2 Omega sin(lat_v) with Omega = 7.292e-5 s^-1.  Host only, uses
+ * OpenMP threads.  Errors: LTS_EINVAL (n < 12, radius <= 0), LTS_ENOMEM. */
+int lts_build_scvt(int64_t n, uint64_t seed, const lts_density* rho,
+                   int32_t lloyd_iters, double radius, lts_mesh_desc* out);
+
+/* Frees the arrays a builder allocated and zeroes the struct. */
+void lts_mesh_desc_free(lts_mesh_desc* d);
+
+/* ------------------------------------------------------------------------
+ * Device objects.
+ * ------------------------------------------------------------------------ */
+typedef struct lts_mesh_s* lts_mesh;
+typedef struct lts_regions_s* lts_regions;
+typedef struct lts_state_s* lts_state;
+
+/* Validates and copies the mesh (FP64 master copies stay on the host until
+ * regions are set).  Checks index ranges, orientation consistency, positive
+ * areas and lengths, kite sums (sum over a cell = A_i, over a vertex = A_v,
+ * relative 1e-9) and, if given, weightsOnEdge against the kite-derived
+ * weights (absolute 1e-9).  Errors: LTS_EINVAL, LTS_ENOMEM. */
+int lts_mesh_create(const lts_mesh_desc* d, lts_mesh* out);
+void lts_mesh_destroy(lts_mesh m);
+
+/* Region labelling of Eqs. (3)-(5) from a fine-cell mask ([nCells], nonzero
+ * = F^c), then band ordering: cells sorted by band
+ *   0 F deep | 1 F3 | 2 F2 | 3 F1 | 4 I1 | 5 I2 | 6 C1 | 7 C2 | 8 C rest
+ * (F1,F2 = the two fine layers of Eq. (4); F3 = the next fine layer; C1, C2 =
+ * the two coarse layers next to I2) and by a Hilbert curve inside each
+ * band; an edge takes the smaller band of its two cells (the fine-to-coarse
+ * assignment of Eq. (5)), a vertex the smallest band of its three cells.
+ * Every restricted phase then reads and writes contiguous index ranges.
+ * Uploads the band-ordered device tables (FP64 master geometry, FP32/FP64
+ * coefficient copies derived in FP64 and rounded once).
+ *   order:            3 (LTS3); other values -> LTS_EINVAL.
+ *   M:                fine substeps per coarse step, >= 1.
+ *   interface_layers: cells per interface layer (>= 1): I1 = cells at
+ *                     edge-distance 1..L from F, I2 = distance L+1..2L.
+ * Needs a CUDA device.  Errors: LTS_EINVAL, LTS_ENOMEM, LTS_ECUDA, LTS_ENODEV. */
+int lts_regions_set(lts_mesh m, const int8_t* fine_mask, int32_t order, int32_t M,
+                    int32_t interface_layers, lts_regions* out);
+void lts_regions_destroy(lts_regions r);
+
+/* Region labels in the caller's original order (host arrays):
+ *   cell_label [nCells]: 0 F \ Fbar, 1 F2, 2 F1, 3 I1, 4 I2, 5 C
+ *   edge_label [nEdges]: 0 F^e, 1 Fbar^e, 3 I1^e, 4 I2^e, 5 C^e
+ * Either pointer may be NULL. */
+int lts_regions_labels(lts_regions r, int8_t* cell_label, int8_t* edge_label);
+
+/* Number of cells, edges and vertices per band (arrays of 9). */
+int lts_regions_counts(lts_regions r, int64_t* cells, int64_t* edges, int64_t* vertices);
+
+/* Band-order permutations: perm_cell[new] = original index (any may be NULL). */
+int lts_regions_permutation(lts_regions r, int32_t* perm_cell, int32_t* perm_edge,
+                            int32_t* perm_vertex);
+
+#define LTS_FP32 0
+#define LTS_FP64 1
+#define LTS_MODE_LTS3   0   /* Algorithm 2.2 (LTS3), coarse step dt, M from regions */
+#define LTS_MODE_SSPRK3 1   /* Algorithm 2.1 (SSPRK3) on the whole mesh, step dt    */
+
+typedef struct lts_params {
+    double g;               /* gravity [m s^-2]                                        */
+    double dt;              /* coarse step (LTS3) or step (SSPRK3) [s]                 */
+    int32_t precision;      /* LTS_FP32 or LTS_FP64                                    */
+    int32_t mode;           /* LTS_MODE_LTS3 or LTS_MODE_SSPRK3                        */
+    int32_t compensated;    /* FP32: carry a compensation word with every state value
+                               (stage sums and flux divergence compensated); ignored
+                               for FP64                                                */
+    int32_t use_graph;      /* 1: capture one coarse step as a CUDA graph (default)    */
+    int32_t block_size;     /* threads per block, 0 = library default                 */
+    int32_t profile;        /* 1: time every launch with CUDA events (no graph)        */
+    void* stream;           /* cudaStream_t to enqueue on; NULL = a library stream     */
+} lts_params;
+
+/* Allocates the device state (band order) and uploads (h0, u0), given in the
+ * caller's original order ([nCells], [nEdges], FP64 host arrays).  Captures
+ * the CUDA graphs of one coarse step when use_graph = 1 (so create the state
+ * outside any stream capture).  Errors: LTS_EINVAL (dt <= 0, g <= 0, bad
+ * precision/mode), LTS_ENOMEM, LTS_ECUDA. */
+int lts_state_create(lts_mesh m, lts_regions r, const double* h0, const double* u0,
+                     const lts_params* p, lts_state* out);
+void lts_state_destroy(lts_state s);
+
+/* Enqueues n_coarse coarse steps (LTS3) or steps (SSPRK3) on the state's
+ * stream.  Asynchronous: returns after enqueueing.  n_coarse >= 0. */
+int lts_step(lts_state s, int32_t n_coarse);
+
+typedef struct lts_diag {
+    double mass;            /* sum_i A_i h_i (FP64 reduction of the FP64 or FP32+compensation state) */
+    double energy;          /* sum_i A_i h_i (K_i + g (h_i/2 + b_i))                               */
+    double time;            /* simulated time [s]                                                  */
+    int64_t steps;          /* coarse steps taken                                                  */
+} lts_diag;
+
+/* Synchronises the state's stream and copies the state to the caller in the
+ * original order and orientation (h [nCells], u [nEdges], FP64; either may
+ * be NULL), plus diagnostics (d may be NULL).  Returns LTS_ENONFINITE if any
+ * stage produced a thickness <= 0 or a non-finite value since the last read. */
+int lts_read(lts_state s, double* h, double* u, lts_diag* d);
+
+/* Replaces the state (original order, FP64 host arrays), e.g. to resume from
+ * a saved lts_read; `time`/`steps` set the clock.  Enqueued on the stream. */
+int lts_write(lts_state s, const double* h, const double* u, double time, int64_t steps);
+
+/* Launch statistics of one coarse step: number of kernel launches, and per
+ * launch kind k (0 = vertex+cell launch, 1 = edge launch) the algorithmic
+ * bytes summed over the step (each array element the kernels touch counted
+ * once per launch).  With profile = 1, ms[k] is the summed event time of
+ * those launches in the last lts_step call (0 otherwise).  Arrays of 2. */
+int lts_step_stats(lts_state s, int32_t* launches_per_step, double* bytes, double* ms,
+                   int32_t* launches_per_kind);
+
+const char* lts_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

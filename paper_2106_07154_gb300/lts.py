@@ -1,0 +1,186 @@
+"""ctypes binding of liblts.so (include/lts.h), same names as the C ABI.
+
+Argument marshalling only: every step of the hot path runs in the library's
+CUDA kernels.  Loading fails loudly if the in-tree liblts.so is missing; there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from pathlib import Path
+
+import numpy as np
+
+PKG = Path(__file__).resolve().parent
+LIB_PATH = PKG / "liblts.so"
+
+LTS_OK = 0
+LTS_EINVAL = -1
+LTS_ENOMEM = -2
+LTS_ECUDA = -3
+LTS_ENONFINITE = -4
+LTS_ETIMEOUT = -5
+LTS_ENODEV = -6
+LTS_FP32 = 0
+LTS_FP64 = 1
+LTS_MODE_LTS3 = 0
+LTS_MODE_SSPRK3 = 1
+
+NBANDS = 9
+BAND_NAMES = ("F_deep", "F3", "F2", "F1", "I1", "I2", "C1", "C2", "C_rest")
+
+_DP = C.POINTER(C.c_double)
+_IP = C.POINTER(C.c_int32)
+
+
+class LtsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"liblts error {code}: {msg}")
+        self.code = code
+
+
+class lts_mesh_desc(C.Structure):
+    _fields_ = [
+        ("nCells", C.c_int32), ("nEdges", C.c_int32), ("nVertices", C.c_int32),
+        ("maxEdges", C.c_int32), ("on_sphere", C.c_int32), ("radius", C.c_double),
+        ("period_x", C.c_double), ("period_y", C.c_double),
+        ("xCell", _DP), ("yCell", _DP), ("zCell", _DP),
+        ("xEdge", _DP), ("yEdge", _DP), ("zEdge", _DP),
+        ("xVertex", _DP), ("yVertex", _DP), ("zVertex", _DP),
+        ("nEdgesOnCell", _IP), ("edgesOnCell", _IP), ("cellsOnCell", _IP),
+        ("verticesOnCell", _IP), ("cellsOnEdge", _IP), ("verticesOnEdge", _IP),
+        ("edgesOnVertex", _IP), ("cellsOnVertex", _IP),
+        ("areaCell", _DP), ("areaTriangle", _DP), ("kiteAreasOnVertex", _DP),
+        ("dcEdge", _DP), ("dvEdge", _DP), ("fVertex", _DP), ("bottom", _DP),
+        ("nEdgesOnEdge", _IP), ("edgesOnEdge", _IP), ("weightsOnEdge", _DP),
+    ]
+
+
+class lts_cap(C.Structure):
+    _fields_ = [("lon", C.c_double), ("lat", C.c_double), ("radius", C.c_double),
+                ("width", C.c_double), ("ratio", C.c_double)]
+
+
+class lts_density(C.Structure):
+    _fields_ = [("ncaps", C.c_int32), ("cap", lts_cap * 4)]
+
+
+class lts_params(C.Structure):
+    _fields_ = [("g", C.c_double), ("dt", C.c_double), ("precision", C.c_int32),
+                ("mode", C.c_int32), ("compensated", C.c_int32), ("use_graph", C.c_int32),
+                ("block_size", C.c_int32), ("profile", C.c_int32), ("stream", C.c_void_p)]
+
+
+class lts_diag(C.Structure):
+    _fields_ = [("mass", C.c_double), ("energy", C.c_double), ("time", C.c_double),
+                ("steps", C.c_int64)]
+
+
+# (field, dtype, length key) of every array in lts_mesh_desc
+_CELL, _EDGE, _VERT = "nCells", "nEdges", "nVertices"
+MESH_ARRAYS = [
+    ("xCell", np.float64, (_CELL, 1)), ("yCell", np.float64, (_CELL, 1)),
+    ("zCell", np.float64, (_CELL, 1)), ("xEdge", np.float64, (_EDGE, 1)),
+    ("yEdge", np.float64, (_EDGE, 1)), ("zEdge", np.float64, (_EDGE, 1)),
+    ("xVertex", np.float64, (_VERT, 1)), ("yVertex", np.float64, (_VERT, 1)),
+    ("zVertex", np.float64, (_VERT, 1)),
+    ("nEdgesOnCell", np.int32, (_CELL, 1)), ("edgesOnCell", np.int32, (_CELL, "maxEdges")),
+    ("cellsOnCell", np.int32, (_CELL, "maxEdges")), ("verticesOnCell", np.int32, (_CELL, "maxEdges")),
+    ("cellsOnEdge", np.int32, (_EDGE, 2)), ("verticesOnEdge", np.int32, (_EDGE, 2)),
+    ("edgesOnVertex", np.int32, (_VERT, 3)), ("cellsOnVertex", np.int32, (_VERT, 3)),
+    ("areaCell", np.float64, (_CELL, 1)), ("areaTriangle", np.float64, (_VERT, 1)),
+    ("kiteAreasOnVertex", np.float64, (_VERT, 3)), ("dcEdge", np.float64, (_EDGE, 1)),
+    ("dvEdge", np.float64, (_EDGE, 1)), ("fVertex", np.float64, (_VERT, 1)),
+    ("bottom", np.float64, (_CELL, 1)),
+]
+SCALARS = ["nCells", "nEdges", "nVertices", "maxEdges", "on_sphere", "radius", "period_x",
+           "period_y"]
+
+_lib = None
+
+
+def lib():
+    """The loaded liblts.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not LIB_PATH.exists():
+            raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() first")
+        L = C.CDLL(str(LIB_PATH))
+        L.lts_last_error.restype = C.c_char_p
+        L.lts_build_hex_periodic.argtypes = [C.c_int32, C.c_int32, C.c_double, C.c_double,
+                                             C.POINTER(lts_mesh_desc)]
+        L.lts_build_scvt.argtypes = [C.c_int64, C.c_uint64, C.POINTER(lts_density), C.c_int32,
+                                     C.c_double, C.POINTER(lts_mesh_desc)]
+        L.lts_mesh_desc_free.argtypes = [C.POINTER(lts_mesh_desc)]
+        L.lts_mesh_desc_free.restype = None
+        if hasattr(L, "lts_mesh_create"):
+            L.lts_mesh_create.argtypes = [C.POINTER(lts_mesh_desc), C.POINTER(C.c_void_p)]
+            L.lts_mesh_destroy.argtypes = [C.c_void_p]
+            L.lts_mesh_destroy.restype = None
+            L.lts_regions_set.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32,
+                                          C.POINTER(C.c_void_p)]
+            L.lts_regions_destroy.argtypes = [C.c_void_p]
+            L.lts_regions_destroy.restype = None
+            L.lts_regions_labels.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+            L.lts_regions_counts.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+            L.lts_regions_permutation.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+            L.lts_state_create.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                           C.POINTER(lts_params), C.POINTER(C.c_void_p)]
+            L.lts_state_destroy.argtypes = [C.c_void_p]
+            L.lts_state_destroy.restype = None
+            L.lts_step.argtypes = [C.c_void_p, C.c_int32]
+            L.lts_read.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(lts_diag)]
+            L.lts_write.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int64]
+            L.lts_step_stats.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                         C.c_void_p]
+        _lib = L
+    return _lib
+
+
+def lts_last_error() -> str:
+    return lib().lts_last_error().decode()
+
+
+def _check(rc: int):
+    if rc != LTS_OK:
+        raise LtsError(rc, lts_last_error())
+
+
+def _desc_to_dict(d: lts_mesh_desc) -> dict:
+    out = {k: getattr(d, k) for k in SCALARS}
+    for name, dt, (nkey, width) in MESH_ARRAYS:
+        ptr = getattr(d, name)
+        if not ptr:
+            out[name] = None
+            continue
+        n = out[nkey] * (out[width] if isinstance(width, str) else width)
+        arr = np.ctypeslib.as_array(ptr, shape=(n,)).copy().astype(dt, copy=False)
+        if not isinstance(width, int) or width != 1:
+            arr = arr.reshape(out[nkey], -1)
+        out[name] = arr
+    return out
+
+
+def lts_build_hex_periodic(nx: int, ny: int, dc: float, f0: float) -> dict:
+    """Doubly periodic hexagonal mesh as a dict of MPAS arrays (see include/lts.h)."""
+    d = lts_mesh_desc()
+    _check(lib().lts_build_hex_periodic(nx, ny, dc, f0, C.byref(d)))
+    try:
+        return _desc_to_dict(d)
+    finally:
+        lib().lts_mesh_desc_free(C.byref(d))
+
+
+def lts_build_scvt(n: int, seed: int, caps, lloyd_iters: int, radius: float) -> dict:
+    """Spherical SCVT; caps = list of (lon, lat, radius, width, ratio) in radians."""
+    den = lts_density()
+    den.ncaps = len(caps)
+    for k, c in enumerate(caps):
+        den.cap[k] = lts_cap(*map(float, c))
+    d = lts_mesh_desc()
+    _check(lib().lts_build_scvt(int(n), int(seed) & (2**64 - 1), C.byref(den), int(lloyd_iters),
+                                float(radius), C.byref(d)))
+    try:
+        return _desc_to_dict(d)
+    finally:
+        lib().lts_mesh_desc_free(C.byref(d))
