@@ -212,10 +212,12 @@ int lts_read(lts_state s, double* h, double* u, lts_diag* d);
 int lts_write(lts_state s, const double* h, const double* u, double time, int64_t steps);
 
 /* Launch statistics of one coarse step: number of kernel launches, and per
- * launch kind k (0 = vertex+cell launch, 1 = edge launch) the algorithmic
- * bytes summed over the step (each array element the kernels touch counted
- * once per launch).  With profile = 1, ms[k] is the summed event time of
- * those launches in the last lts_step call (0 otherwise).  Arrays of 2. */
+ * launch kind k (0 = vertex PV, 1 = cell ring pass with the thickness
+ * update, 2 = edge pass with the velocity update) the algorithmic bytes
+ * summed over the step (each array element a launch touches counted once).
+ * With profile = 1, ms[k] is the summed event time of those launches in the
+ * last lts_step call (0 otherwise).  Arrays of LTS_NKINDS. */
+#define LTS_NKINDS 3
 int lts_step_stats(lts_state s, int32_t* launches_per_step, double* bytes, double* ms,
                    int32_t* launches_per_kind);
 

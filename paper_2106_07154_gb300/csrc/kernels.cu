@@ -1,0 +1,547 @@
+// kernels.cu -- sm_103a kernels of the LTS3 / SSP-RK3 hot path.
+//
+// One evaluation of the right-hand side of Eq. (1) restricted to a band
+// range, fused with the SSP stage combination (Algorithm 2.1) or with the
+// correction accumulation of Steps 3.x.2, is three launches:
+//   kind 0 (vertex): q_v = (zeta_v + f_v) / h_v (Appendix B, reading R7) for
+//     the vertices the ring pass reads;
+//   kind 1 (ring, one thread per cell): reads the cell's counter-clockwise
+//     ring once with coalesced slot-major loads and forms F_e = [h]_{i->e} u_e,
+//     K_i, H_i = -[div F]_i (compensated sum, then the stage update or the
+//     accumulation) and, for every edge e_p of the cell, the cell's share of
+//     F^perp_e [q]_{v->e} with the weights w_{e,e'} of Eq. (weights) taken
+//     from prefix sums of the kite fractions;
+//   kind 2 (edge): U_e = -F^perp_e [q]_{v->e} - [g grad(h+b) + grad K]_e from
+//     the two cells' ring results, then the stage update or accumulation.
+// Pointwise segments (interface predictions of Steps 3.x.1, snapshots,
+// Step 5) ride in these launches.  Every restricted phase is a set of
+// contiguous band ranges; the path is a sparse gather stencil, so no tensor
+// cores are used.
+#include <cstdint>
+
+#include "lts_internal.h"
+
+namespace lts {
+namespace {
+
+template <class T>
+struct DevSeg {
+    int type, begin, end, base, base2, flag, block0, pad;
+    T c[6];
+    void* p[10];
+};
+
+template <class T>
+struct DevArgs {
+    Tables<T> t;
+    DevSeg<T> seg[MAXSEG];
+    int nseg;
+    const T* in_h;
+    const T* in_hl;   // compensation words of the input thickness (COMP only)
+    const T* in_u;
+    T* q;
+    T* ring_c;        // [maxE*nC] per-slot PV contributions
+    T* ring_k;        // [nC] K_i
+    T g;
+    int* flag;
+};
+
+// ---------------------------------------------------------------- arithmetic
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// Knuth's TwoSum: s + e == a + b exactly.
+template <class T>
+__device__ __forceinline__ void two_sum(T a, T b, T& s, T& e) {
+    s = a + b;
+    T bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+// Dekker's FastTwoSum (|a| >= |b|).
+template <class T>
+__device__ __forceinline__ void fast_two_sum(T a, T b, T& s, T& e) {
+    s = a + b;
+    e = b - (s - a);
+}
+
+// SSP stage combination of Algorithm 2.1 in increment form:
+//   y = x_s + a (x_old - x_s) + D R
+// (stage 1: a = 0, D = dt; stage 2: a = 3/4, D = dt/4; stage 3: a = 1/3,
+// D = 2 dt/3), which keeps a constant state exactly constant.  With COMP the
+// states are (hi, lo) pairs and the large term x_s is added with TwoSum, so
+// the rounding of each stage is carried in lo instead of being lost.
+template <class T, bool COMP>
+__device__ __forceinline__ void combine(T oh, T ol, T sh, T sl, T a, T D, T R, T& yh, T& yl) {
+    if (COMP) {
+        T d = (oh - sh) + (ol - sl);
+        T inc = fma_rn(D, R, mul_rn(a, d));
+        T s, e;
+        two_sum(sh, inc, s, e);
+        T lo = sl + e;
+        fast_two_sum(s, lo, yh, yl);
+    } else {
+        T inc = fma_rn(D, R, mul_rn(a, oh - sh));
+        yh = sh + inc;
+        yl = T(0);
+    }
+}
+
+// Interface-1 prediction of Steps 3.x.1 in increment form,
+// x = x_old + c1 (x_1st - x_old) + c2 (x_2nd - x_old); sel != 0 when the
+// coefficients select one vector exactly (then the value is copied).
+template <class T, bool COMP>
+__device__ __forceinline__ void predict(T oh, T ol, T h1, T l1, T h2, T l2, T c1, T c2, int sel,
+                                        T& yh, T& yl) {
+    if (sel == 1) { yh = oh; yl = ol; return; }
+    if (sel == 2) { yh = h1; yl = l1; return; }
+    if (sel == 3) { yh = h2; yl = l2; return; }
+    T d1 = COMP ? (h1 - oh) + (l1 - ol) : h1 - oh;
+    T d2 = COMP ? (h2 - oh) + (l2 - ol) : h2 - oh;
+    T inc = fma_rn(c2, d2, mul_rn(c1, d1));
+    if (COMP) {
+        T s, e;
+        two_sum(oh, inc, s, e);
+        T lo = ol + e;
+        fast_two_sum(s, lo, yh, yl);
+    } else {
+        yh = oh + inc;
+        yl = T(0);
+    }
+}
+
+__device__ __forceinline__ bool finite_pos(double x) { return x > 0.0 && x < 1e300; }
+__device__ __forceinline__ bool finite_pos(float x) { return x > 0.0f && x < 3.0e38f; }
+__device__ __forceinline__ bool finite_val(double x) { return fabs(x) < 1e300; }
+__device__ __forceinline__ bool finite_val(float x) { return fabsf(x) < 3.0e38f; }
+
+// ------------------------------------------------------------- kind 0: vertex
+
+// q_v = (zeta_v + f_v) / h_v with zeta_v = sum t_{e,v} (d_e/A_v) u_e and
+// h_v = sum (A_{i,v}/A_v) h_i.
+template <class T>
+__device__ __forceinline__ void vertex_pv(const DevArgs<T>& a, int v) {
+    const Tables<T>& t = a.t;
+    T zeta = t.vd0[v] * a.in_u[t.ve0[v]] + t.vd1[v] * a.in_u[t.ve1[v]] + t.vd2[v] * a.in_u[t.ve2[v]];
+    T hv = t.vk0[v] * a.in_h[t.vc0[v]] + t.vk1[v] * a.in_h[t.vc1[v]] + t.vk2[v] * a.in_h[t.vc2[v]];
+    a.q[v] = (zeta + t.f[v]) / hv;
+}
+
+// --------------------------------------------------------------- kind 1: ring
+//
+// For cell c with slots j = 0..n-1 (edge e_j, neighbour across it, vertex
+// v_j between e_j and e_{j+1}, kite fraction R_j = A_{c,v_j}/A_c):
+//   F_j  = (h_c + h_nb)/2 u_j,   G_j = n_{e_j,c} l_j F_j,   qt_j = (q_{v_{j-1}} + q_{v_j})/2
+//   K_c  = sum_j l_j d_j u_j^2 / (4 A_c),      H_c = -(1/A_c) sum_j G_j
+// and for every slot p the share of the PV flux of edge e_p,
+//   C_p = sum_{j != p} (S_{j->p} - 1/2) G_j (qt_p + qt_j),
+// where S_{j->p} = sum of R_m over the vertices met going counter-clockwise
+// from e_j to e_p (so w_{e_p,e_j} = n_{e_j,c} (-n_{e_p,c}) (S_{j->p} - 1/2),
+// t_{e_p,v_{p-1}} = -n_{e_p,c} on a counter-clockwise ring).  With prefix sums
+// P_m = R_0 + ... + R_{m-1}, S_{j->p} = P_p - P_j + [j > p] P_n, so
+//   C_p = qt_p [(P_p - 1/2) A_p + P_n Asuf_p - A'_p] + [(P_p - 1/2) B_p + P_n Bsuf_p - B'_p]
+// with A_p = sum_{j!=p} G_j, A'_p = sum_{j!=p} P_j G_j, Asuf_p = sum_{j>p} G_j
+// and B the same with G_j qt_j: the weight sum regrouped into O(n) work.
+template <class T, bool COMP, int MAXR>
+__device__ __forceinline__ T ring_pass(const DevArgs<T>& a, int c) {
+    const Tables<T>& t = a.t;
+    const int N = t.nC;
+    const int n = t.cn[c];
+    const T hc = a.in_h[c];
+    T G[MAXR], qt[MAXR], P[MAXR];
+    T qprev = a.q[__ldg(t.sv + (n - 1) * N + c)];   // q at v_{n-1} (closes the ring)
+    T Kc = T(0), s = T(0), comp = T(0);
+    T Pacc = T(0);
+#pragma unroll
+    for (int j = 0; j < MAXR; ++j) {
+        if (j < n) {
+            const int e = __ldg(t.se + j * N + c);
+            const int nb = __ldg(t.sn + j * N + c);
+            const int v = __ldg(t.sv + j * N + c);
+            const T snl = __ldg(t.snl + j * N + c);
+            const T R = __ldg(t.sR + j * N + c);
+            const T sK = __ldg(t.sK + j * N + c);
+            const T uj = a.in_u[e];
+            const T hnb = a.in_h[nb];
+            const T qj = a.q[v];
+            const T F = T(0.5) * (hc + hnb) * uj;
+            const T g = mul_rn(snl, F);
+            G[j] = g;
+            qt[j] = T(0.5) * (qprev + qj);
+            qprev = qj;
+            P[j] = Pacc;
+            Pacc += R;
+            Kc += sK * uj * uj;
+            if (COMP) {
+                T ss, ee;
+                two_sum(s, g, ss, ee);
+                s = ss;
+                comp += ee;
+            } else {
+                s += g;
+            }
+        }
+    }
+    const T Pn = Pacc;
+    T Atot = T(0), Btot = T(0), A1 = T(0), B1 = T(0);
+#pragma unroll
+    for (int j = 0; j < MAXR; ++j) {
+        if (j < n) {
+            const T gq = G[j] * qt[j];
+            Atot += G[j];
+            Btot += gq;
+            A1 += P[j] * G[j];
+            B1 += P[j] * gq;
+        }
+    }
+    T Asuf = T(0), Bsuf = T(0);
+#pragma unroll
+    for (int p = MAXR - 1; p >= 0; --p) {
+        if (p < n) {
+            const T gq = G[p] * qt[p];
+            const T Ap = Atot - G[p];
+            const T Bp = Btot - gq;
+            const T A1p = A1 - P[p] * G[p];
+            const T B1p = B1 - P[p] * gq;
+            const T w = P[p] - T(0.5);
+            const T C = qt[p] * (w * Ap + Pn * Asuf - A1p) + (w * Bp + Pn * Bsuf - B1p);
+            a.ring_c[p * N + c] = C;
+            Asuf += G[p];
+            Bsuf += gq;
+        }
+    }
+    a.ring_k[c] = Kc;
+    return -(s + comp) * t.rA[c];
+}
+
+// --------------------------------------------------------------- kind 2: edge
+// U_e = -(1/d_e) [ (C_{c1,p1} - C_{c0,p0})/2 + g((h1 - h0) + (b1 - b0)) + K1 - K0 ]
+// (-n_{e,c0} = -1, -n_{e,c1} = +1 carry the signs of the two ring shares).
+template <class T, bool COMP>
+__device__ __forceinline__ T edge_tendency(const DevArgs<T>& a, int e) {
+    const Tables<T>& t = a.t;
+    const int N = t.nC;
+    const int c0 = t.ec0[e], c1 = t.ec1[e];
+    const uint32_t pp = t.ep[e];
+    const int p0 = pp & 0xff, p1 = (pp >> 8) & 0xff;
+    const T C0 = a.ring_c[p0 * N + c0], C1 = a.ring_c[p1 * N + c1];
+    // h1 - h0 is exact for nearby thicknesses (Sterbenz); with COMP the
+    // compensation words restore the digits the FP32 thickness dropped.
+    T dh = a.in_h[c1] - a.in_h[c0];
+    if (COMP) dh += a.in_hl[c1] - a.in_hl[c0];
+    const T grad = a.g * (dh + (t.b[c1] - t.b[c0])) + (a.ring_k[c1] - a.ring_k[c0]);
+    return -t.rdc[e] * (T(0.5) * (C1 - C0) + grad);
+}
+
+// ------------------------------------------------------------ pointwise parts
+
+template <class T, bool COMP>
+__device__ __forceinline__ void pointwise(const DevSeg<T>& s, int i) {
+    if (s.type == SEG_PRED) {
+        const T* oh = (const T*)s.p[0];
+        const T* ol = (const T*)s.p[1];
+        const T* x1h = (const T*)s.p[2];
+        const T* x1l = (const T*)s.p[3];
+        const T* x2h = (const T*)s.p[4];
+        const T* x2l = (const T*)s.p[5];
+        T* outh = (T*)s.p[6];
+        T* outl = (T*)s.p[7];
+        const int k = i - s.base;
+        T yh, yl;
+        predict<T, COMP>(oh[i], COMP ? ol[i] : T(0), x1h[k], COMP ? x1l[k] : T(0), x2h[k],
+                         COMP ? x2l[k] : T(0), s.c[0], s.c[1], s.flag, yh, yl);
+        outh[i] = yh;
+        if (COMP) outl[i] = yl;
+    } else if (s.type == SEG_COPY) {
+        const T* sh = (const T*)s.p[0];
+        const T* sl = (const T*)s.p[1];
+        T* dh = (T*)s.p[2];
+        T* dl = (T*)s.p[3];
+        dh[i - s.base] = sh[i - s.base2];
+        if (COMP) dl[i - s.base] = sl[i - s.base2];
+    } else if (s.type == SEG_REPLAY) {
+        // Step 5 as the replay of the three interface stages (reading R5).
+        const T* oh = (const T*)s.p[0];
+        const T* ol = (const T*)s.p[1];
+        const T* a1 = (const T*)s.p[2];
+        const T* a2 = (const T*)s.p[3];
+        const T* a3 = (const T*)s.p[4];
+        T* outh = (T*)s.p[5];
+        T* outl = (T*)s.p[6];
+        const int k = i - s.base;
+        const T xh = oh[i], xl = COMP ? ol[i] : T(0);
+        T x1h, x1l, x2h, x2l, yh, yl;
+        combine<T, COMP>(xh, xl, xh, xl, T(0), s.c[0], a1[k], x1h, x1l);
+        combine<T, COMP>(xh, xl, x1h, x1l, s.c[3], s.c[1], a2[k], x2h, x2l);
+        combine<T, COMP>(xh, xl, x2h, x2l, s.c[4], s.c[2], a3[k], yh, yl);
+        outh[i] = yh;
+        if (COMP) outl[i] = yl;
+    }
+}
+
+// Stage update (UPD) or correction accumulation (ACC) of a cell or edge value.
+template <class T, bool COMP, bool IS_CELL>
+__device__ __forceinline__ void epilogue(const DevArgs<T>& a, const DevSeg<T>& s, bool acc_mode, int i,
+                                         T R, const T* in_x) {
+    if (acc_mode) {
+        T* acc = (T*)s.p[0];
+        const int k = i - s.base;
+        acc[k] = s.flag ? R : acc[k] + R;
+        return;
+    }
+    const T* oh = (const T*)s.p[0];
+    const T* ol = (const T*)s.p[1];
+    const T* sl = (const T*)s.p[2];
+    T* outh = (T*)s.p[3];
+    T* outl = (T*)s.p[4];
+    T yh, yl;
+    combine<T, COMP>(oh[i], COMP ? ol[i] : T(0), in_x[i], COMP ? sl[i] : T(0), s.c[0], s.c[1], R,
+                     yh, yl);
+    outh[i] = yh;
+    if (COMP) outl[i] = yl;
+    const bool ok = IS_CELL ? finite_pos(yh) : finite_val(yh);
+    if (!ok) atomicOr(a.flag, IS_CELL ? 1 : 2);
+}
+
+template <class T>
+__device__ __forceinline__ int find_seg(const DevArgs<T>& a, int blk) {
+    int s = 0;
+#pragma unroll
+    for (int k = 1; k < MAXSEG; ++k)
+        if (k < a.nseg && blk >= a.seg[k].block0) s = k;
+    return s;
+}
+
+template <class T, bool COMP, int MAXR, int KIND>
+__global__ void __launch_bounds__(256) kernel_phase(const __grid_constant__ DevArgs<T> a) {
+    const int sidx = find_seg(a, blockIdx.x);
+    const DevSeg<T>& s = a.seg[sidx];
+    const int i = s.begin + (blockIdx.x - s.block0) * blockDim.x + threadIdx.x;
+    if (i >= s.end) return;
+    const int type = s.type;
+    if (KIND == 0 && type == SEG_VERT) {
+        vertex_pv(a, i);
+    } else if (KIND == 1 && (type == SEG_RING || type == SEG_RING_UPD || type == SEG_RING_ACC)) {
+        const T H = ring_pass<T, COMP, MAXR>(a, i);
+        if (type != SEG_RING) epilogue<T, COMP, true>(a, s, type == SEG_RING_ACC, i, H, a.in_h);
+    } else if (KIND == 2 && (type == SEG_EDGE_UPD || type == SEG_EDGE_ACC)) {
+        const T U = edge_tendency<T, COMP>(a, i);
+        epilogue<T, COMP, false>(a, s, type == SEG_EDGE_ACC, i, U, a.in_u);
+    } else {
+        pointwise<T, COMP>(s, i);
+    }
+}
+
+template <class T, bool COMP, int MAXR>
+cudaError_t launch_t(const LaunchDesc& d, const void* tables, int block, int* flag,
+                     cudaStream_t st) {
+    DevArgs<T> a;
+    a.t = *static_cast<const Tables<T>*>(tables);
+    a.in_h = static_cast<const T*>(d.in_h);
+    a.in_hl = static_cast<const T*>(d.in_hl);
+    a.in_u = static_cast<const T*>(d.in_u);
+    a.q = static_cast<T*>(d.q);
+    a.ring_c = static_cast<T*>(d.ring_c);
+    a.ring_k = static_cast<T*>(d.ring_k);
+    a.g = static_cast<T>(d.g);
+    a.flag = flag;
+    int blocks = 0, ns = 0;
+    for (int k = 0; k < d.nseg; ++k) {
+        const SegDesc& s = d.seg[k];
+        if (s.end <= s.begin) continue;
+        DevSeg<T>& o = a.seg[ns++];
+        o.type = s.type;
+        o.begin = s.begin;
+        o.end = s.end;
+        o.base = s.base;
+        o.base2 = s.base2;
+        o.flag = s.flag;
+        o.block0 = blocks;
+        o.pad = 0;
+        for (int m = 0; m < 6; ++m) o.c[m] = static_cast<T>(m < 4 ? s.c[m] : 0.0);
+        if (s.type == SEG_REPLAY) {
+            o.c[3] = static_cast<T>(0.75);
+            o.c[4] = static_cast<T>(1.0 / 3.0);
+        }
+        for (int m = 0; m < 10; ++m) o.p[m] = s.p[m];
+        blocks += (s.end - s.begin + block - 1) / block;
+    }
+    a.nseg = ns;
+    for (int k = ns; k < MAXSEG; ++k) {
+        a.seg[k] = a.seg[0];
+        a.seg[k].block0 = 0x7fffffff;
+    }
+    if (blocks == 0) return cudaSuccess;
+    switch (d.kind) {
+        case 0: kernel_phase<T, COMP, MAXR, 0><<<blocks, block, 0, st>>>(a); break;
+        case 1: kernel_phase<T, COMP, MAXR, 1><<<blocks, block, 0, st>>>(a); break;
+        default: kernel_phase<T, COMP, MAXR, 2><<<blocks, block, 0, st>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ state I/O
+
+template <class T, bool COMP>
+__global__ void scatter_kernel(int n, const int* perm, const double* src, T* hi, T* lo) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double x = src[perm[i]];
+    T h = static_cast<T>(x);
+    hi[i] = h;
+    if (COMP) lo[i] = static_cast<T>(x - static_cast<double>(h));
+}
+
+template <class T, bool COMP>
+__global__ void gather_kernel(int n, const int* perm, const T* hi, const T* lo, double* dst) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double x = static_cast<double>(hi[i]);
+    if (COMP) x += static_cast<double>(lo[i]);
+    dst[perm[i]] = x;
+}
+
+// ------------------------------------------------------------ FP64 diagnostics
+// mass = sum A_i h_i, energy = sum A_i h_i (K_i + g (h_i/2 + b_i)), FP64,
+// fixed blocking and a fixed-order tree, so the result is deterministic.
+constexpr int DIAG_THREADS = 256;
+
+template <class T, bool COMP>
+__global__ void __launch_bounds__(DIAG_THREADS) diag_kernel(const Tables<T> t, const T* hh, const T* hl,
+                                                           const T* uh, const T* ul, double g,
+                                                           double* partial) {
+    __shared__ double sm[2][DIAG_THREADS];
+    const int N = t.nC;
+    double m = 0.0, en = 0.0;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
+        double h = static_cast<double>(hh[c]) + (COMP ? static_cast<double>(hl[c]) : 0.0);
+        double K = 0.0;
+        for (int j = 0; j < t.cn[c]; ++j) {
+            int e = t.se[j * N + c];
+            double u = static_cast<double>(uh[e]) + (COMP ? static_cast<double>(ul[e]) : 0.0);
+            K += t.sK64[j * N + c] * u * u;
+        }
+        double A = t.area[c];
+        m += A * h;
+        en += A * h * (K + g * (0.5 * h + t.bd[c]));
+    }
+    sm[0][threadIdx.x] = m;
+    sm[1][threadIdx.x] = en;
+    __syncthreads();
+    for (int s = DIAG_THREADS / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            sm[0][threadIdx.x] += sm[0][threadIdx.x + s];
+            sm[1][threadIdx.x] += sm[1][threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partial[2 * blockIdx.x] = sm[0][0];
+        partial[2 * blockIdx.x + 1] = sm[1][0];
+    }
+}
+
+// Second stage: one block sums the per-block partials in a fixed-order tree.
+__global__ void __launch_bounds__(DIAG_THREADS) diag_final(const double* partial, int nb, double* out) {
+    __shared__ double sm[2][DIAG_THREADS];
+    double m = 0.0, en = 0.0;
+    for (int b = threadIdx.x; b < nb; b += DIAG_THREADS) {
+        m += partial[2 * b];
+        en += partial[2 * b + 1];
+    }
+    sm[0][threadIdx.x] = m;
+    sm[1][threadIdx.x] = en;
+    __syncthreads();
+    for (int s = DIAG_THREADS / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            sm[0][threadIdx.x] += sm[0][threadIdx.x + s];
+            sm[1][threadIdx.x] += sm[1][threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = sm[0][0];
+        out[1] = sm[1][0];
+    }
+}
+
+template <class T, bool COMP>
+cudaError_t launch_any(const LaunchDesc& d, const void* tables, const KernelConfig& kc, int* flag,
+                       cudaStream_t s) {
+    if (kc.maxdeg <= 8) return launch_t<T, COMP, 8>(d, tables, kc.block, flag, s);
+    return launch_t<T, COMP, MAX_DEGREE>(d, tables, kc.block, flag, s);
+}
+
+}  // namespace
+
+cudaError_t launch_phase(const LaunchDesc& d, const void* tables, const KernelConfig& kc, int* flag,
+                         cudaStream_t s) {
+    if (kc.precision == 1) return launch_any<double, false>(d, tables, kc, flag, s);
+    if (kc.comp) return launch_any<float, true>(d, tables, kc, flag, s);
+    return launch_any<float, false>(d, tables, kc, flag, s);
+}
+
+cudaError_t launch_scatter_state(const KernelConfig& kc, int n, const int* perm, const double* src,
+                                 void* hi, void* lo, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    int b = 256, g = (n + b - 1) / b;
+    if (kc.precision == 1)
+        scatter_kernel<double, false><<<g, b, 0, s>>>(n, perm, src, (double*)hi, nullptr);
+    else if (kc.comp)
+        scatter_kernel<float, true><<<g, b, 0, s>>>(n, perm, src, (float*)hi, (float*)lo);
+    else
+        scatter_kernel<float, false><<<g, b, 0, s>>>(n, perm, src, (float*)hi, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_state(const KernelConfig& kc, int n, const int* perm, const void* hi,
+                                const void* lo, double* dst, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    int b = 256, g = (n + b - 1) / b;
+    if (kc.precision == 1)
+        gather_kernel<double, false><<<g, b, 0, s>>>(n, perm, (const double*)hi, nullptr, dst);
+    else if (kc.comp)
+        gather_kernel<float, true><<<g, b, 0, s>>>(n, perm, (const float*)hi, (const float*)lo, dst);
+    else
+        gather_kernel<float, false><<<g, b, 0, s>>>(n, perm, (const float*)hi, nullptr, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_diagnostics(const KernelConfig& kc, const void* tables, const void* h_hi,
+                               const void* h_lo, const void* u_hi, const void* u_lo, double g,
+                               double* partial, int nblocks, double* out2, cudaStream_t s) {
+    if (kc.precision == 1) {
+        const Tables<double>& t = *static_cast<const Tables<double>*>(tables);
+        diag_kernel<double, false><<<nblocks, DIAG_THREADS, 0, s>>>(
+            t, (const double*)h_hi, nullptr, (const double*)u_hi, nullptr, g, partial);
+    } else {
+        const Tables<float>& t = *static_cast<const Tables<float>*>(tables);
+        if (kc.comp)
+            diag_kernel<float, true><<<nblocks, DIAG_THREADS, 0, s>>>(
+                t, (const float*)h_hi, (const float*)h_lo, (const float*)u_hi, (const float*)u_lo, g,
+                partial);
+        else
+            diag_kernel<float, false><<<nblocks, DIAG_THREADS, 0, s>>>(
+                t, (const float*)h_hi, nullptr, (const float*)u_hi, nullptr, g, partial);
+    }
+    diag_final<<<1, DIAG_THREADS, 0, s>>>(partial, nblocks, out2);
+    return cudaGetLastError();
+}
+
+template <class T, bool COMP, int MAXR>
+int regs_t(int kind) {
+    cudaFuncAttributes at{};
+    cudaError_t err = kind == 0   ? cudaFuncGetAttributes(&at, kernel_phase<T, COMP, MAXR, 0>)
+                      : kind == 1 ? cudaFuncGetAttributes(&at, kernel_phase<T, COMP, MAXR, 1>)
+                                  : cudaFuncGetAttributes(&at, kernel_phase<T, COMP, MAXR, 2>);
+    return err == cudaSuccess ? at.numRegs : -1;
+}
+
+int kernel_registers(const KernelConfig& kc, int kind) {
+    if (kc.precision == 1) return kc.maxdeg <= 8 ? regs_t<double, false, 8>(kind) : regs_t<double, false, 16>(kind);
+    if (kc.comp) return kc.maxdeg <= 8 ? regs_t<float, true, 8>(kind) : regs_t<float, true, 16>(kind);
+    return kc.maxdeg <= 8 ? regs_t<float, false, 8>(kind) : regs_t<float, false, 16>(kind);
+}
+
+}  // namespace lts

@@ -1,0 +1,939 @@
+// lts_api.cpp -- the C ABI of liblts.so (include/lts.h): mesh validation,
+// regions, device tables, device state, the phase plans of Algorithm 2.2
+// (LTS3) and Algorithm 2.1 (SSPRK3), CUDA-graph capture of one coarse step,
+// state I/O and launch statistics.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/lts.h"
+#include "lts_error.h"
+#include "lts_internal.h"
+#include "regions.h"
+
+using namespace lts;
+
+// ------------------------------------------------------------------ objects
+
+struct DeviceArena {
+    std::vector<void*> blocks;
+    ~DeviceArena() {
+        for (void* p : blocks) cudaFree(p);
+    }
+    template <class T>
+    T* upload(const std::vector<T>& v, cudaError_t& err) {
+        void* p = nullptr;
+        size_t n = std::max<size_t>(1, v.size()) * sizeof(T);
+        err = cudaMalloc(&p, n);
+        if (err != cudaSuccess) return nullptr;
+        blocks.push_back(p);
+        if (!v.empty()) err = cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+        return static_cast<T*>(p);
+    }
+    void* alloc(size_t bytes, cudaError_t& err) {
+        void* p = nullptr;
+        err = cudaMalloc(&p, std::max<size_t>(bytes, 16));
+        if (err != cudaSuccess) return nullptr;
+        blocks.push_back(p);
+        err = cudaMemset(p, 0, std::max<size_t>(bytes, 16));
+        return p;
+    }
+};
+
+struct lts_mesh_s {
+    std::atomic<int> ref{1};
+    HostMesh m;
+};
+
+struct lts_regions_s {
+    std::atomic<int> ref{1};
+    lts_mesh_s* mesh = nullptr;
+    RegionsHost r;
+    // device tables per precision (built on first use)
+    std::unique_ptr<DeviceArena> arena[2];
+    Tables<float> t32{};
+    Tables<double> t64{};
+    int* d_perm_c = nullptr;
+    int* d_perm_e = nullptr;
+    int device = -1;
+};
+
+struct SV {   // one state vector (h, u) with optional compensation words
+    void* hh = nullptr;
+    void* hl = nullptr;
+    void* uh = nullptr;
+    void* ul = nullptr;
+};
+
+struct lts_state_s {
+    lts_regions_s* reg = nullptr;
+    lts_params p{};
+    KernelConfig kc{};
+    size_t tsz = 4;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaStream_t capture_stream = nullptr;
+    DeviceArena arena;
+    const void* tables = nullptr;
+    SV buf[4];            // [parity] = x_old, [1-parity] = x_new, [2] = x_1st, [3] = x_2nd
+    SV P1c, P1e, P2c, P2e;   // interface-1 snapshots of the coarse 1st / 2nd stage
+    void* acc_c[3] = {};  // correction terms on I1 u I2 cells (Steps 3.x.2)
+    void* acc_e[3] = {};
+    void* q = nullptr;
+    void* ring_c = nullptr;   // [maxE*nC] per-slot PV contributions
+    void* ring_k = nullptr;   // [nC] K_i
+    int* flag = nullptr;
+    double* stage_c = nullptr;   // FP64 staging for I/O (original order)
+    double* stage_e = nullptr;
+    double* diag_partial = nullptr;
+    double* diag_out = nullptr;
+    int diag_blocks = 0;
+    std::vector<LaunchDesc> plan[2];
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    int parity = 0;
+    int64_t steps = 0;
+    double time = 0.0;
+    // statistics
+    double bytes[NKINDS] = {0, 0, 0};
+    int launches[NKINDS] = {0, 0, 0};
+    double prof_ms[NKINDS] = {0, 0, 0};
+    std::vector<cudaEvent_t> events;
+    ~lts_state_s();
+};
+
+namespace {
+
+#define CUDA_TRY(expr)                                                                        \
+    do {                                                                                      \
+        cudaError_t _e = (expr);                                                              \
+        if (_e != cudaSuccess)                                                                \
+            return set_error(_e == cudaErrorMemoryAllocation ? LTS_ENOMEM : LTS_ECUDA,        \
+                             "%s: %s (%s:%d)", #expr, cudaGetErrorString(_e), __FILE__, __LINE__); \
+    } while (0)
+
+void release_mesh(lts_mesh_s* m) {
+    if (m && --m->ref == 0) delete m;
+}
+void release_regions(lts_regions_s* r) {
+    if (r && --r->ref == 0) {
+        int dev = -1;
+        if (r->device >= 0 && cudaGetDevice(&dev) == cudaSuccess && dev != r->device)
+            cudaSetDevice(r->device);
+        r->arena[0].reset();
+        r->arena[1].reset();
+        release_mesh(r->mesh);
+        delete r;
+    }
+}
+
+int check_device() {
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess || n == 0) {
+        cudaGetLastError();
+        return set_error(LTS_ENODEV, "no CUDA device: %s", cudaGetErrorString(e));
+    }
+    return LTS_OK;
+}
+
+template <class T>
+int build_tables(lts_regions_s* R, int which, Tables<T>& t) {
+    const HostMesh& m = R->mesh->m;
+    const RegionsHost& r = R->r;
+    CoefTables<T> co;
+    coefficient_tables<T>(m, r, co);
+    auto arena = std::make_unique<DeviceArena>();
+    cudaError_t err = cudaSuccess;
+    auto up = [&](const auto& v) { return arena->upload(v, err); };
+    t.nC = m.nC;
+    t.nE = m.nE;
+    t.nV = m.nV;
+    t.maxE = m.maxE;
+    t.cn = up(r.cn);
+    t.se = up(r.se);
+    t.sn = up(r.sn);
+    t.sv = up(r.sv);
+    t.snl = up(co.snl);
+    t.sR = up(co.sR);
+    t.sK = up(co.sK);
+    t.rA = up(co.rA);
+    t.b = up(co.b);
+    t.ec0 = up(r.ec0);
+    t.ec1 = up(r.ec1);
+    t.ep = up(r.ep);
+    t.rdc = up(co.rdc);
+    const int* vc = up(r.vc);
+    const int* ve = up(r.ve);
+    const T* vk = up(co.vk);
+    const T* vd = up(co.vd);
+    if (err != cudaSuccess) return set_error(LTS_ECUDA, "table upload: %s", cudaGetErrorString(err));
+    const size_t nV = static_cast<size_t>(m.nV);
+    t.vc0 = vc; t.vc1 = vc + nV; t.vc2 = vc + 2 * nV;
+    t.ve0 = ve; t.ve1 = ve + nV; t.ve2 = ve + 2 * nV;
+    t.vk0 = vk; t.vk1 = vk + nV; t.vk2 = vk + 2 * nV;
+    t.vd0 = vd; t.vd1 = vd + nV; t.vd2 = vd + 2 * nV;
+    t.f = up(co.f);
+    t.area = up(co.area);
+    t.bd = up(co.bd);
+    t.sK64 = up(co.sK64);
+    if (!R->d_perm_c) {
+        R->d_perm_c = arena->upload(r.perm_c, err);
+        R->d_perm_e = arena->upload(r.perm_e, err);
+    }
+    if (err != cudaSuccess) return set_error(LTS_ECUDA, "table upload: %s", cudaGetErrorString(err));
+    R->arena[which] = std::move(arena);
+    return LTS_OK;
+}
+
+// ------------------------------------------------------- algorithmic bytes
+// Bytes of every array element a launch touches, each counted once (a
+// perfect cache): the compulsory traffic of the launch.
+double launch_bytes(const LaunchDesc& d, const RegionsHost& r, int nC, int nE, int nV, size_t T,
+                    bool comp) {
+    std::vector<char> mh(nC, 0), mhl(nC, 0), mu(nE, 0), mq(nV, 0), mk(nC, 0), mb(nC, 0);
+    double bytes = 0.0;
+    const double c = comp ? 1.0 : 0.0;
+    for (int s = 0; s < d.nseg; ++s) {
+        const SegDesc& g = d.seg[s];
+        const double n = std::max(0, g.end - g.begin);
+        switch (g.type) {
+            case SEG_VERT:
+                bytes += n * (24.0 + 7.0 * T + T);   // vc, ve, vk, vd, f; q write
+                for (int v = g.begin; v < g.end; ++v)
+                    for (int q = 0; q < 3; ++q) {
+                        mh[r.vc[static_cast<size_t>(q) * nV + v]] = 1;
+                        mu[r.ve[static_cast<size_t>(q) * nV + v]] = 1;
+                    }
+                break;
+            case SEG_RING:
+            case SEG_RING_UPD:
+            case SEG_RING_ACC:
+                for (int k = g.begin; k < g.end; ++k) {
+                    // cn, rA; per slot se, sn, sv, snl, sR, sK and the C write; K write
+                    bytes += 1.0 + T + r.cn[k] * (12.0 + 4.0 * T) + T;
+                    mh[k] = 1;
+                    for (int j = 0; j < r.cn[k]; ++j) {
+                        mu[r.se[static_cast<size_t>(j) * nC + k]] = 1;
+                        mh[r.sn[static_cast<size_t>(j) * nC + k]] = 1;
+                        mq[r.sv[static_cast<size_t>(j) * nC + k]] = 1;
+                    }
+                }
+                if (g.type == SEG_RING_UPD) bytes += n * T * (2.0 + 3.0 * c);
+                if (g.type == SEG_RING_ACC) bytes += n * T * (g.flag ? 1 : 2);
+                break;
+            case SEG_EDGE_UPD:
+            case SEG_EDGE_ACC:
+                bytes += n * (12.0 + T);                     // ec0, ec1, ep, rdc
+                for (int e = g.begin; e < g.end; ++e) {
+                    mu[e] = 1;
+                    for (int cc : {r.ec0[e], r.ec1[e]}) {
+                        mh[cc] = mk[cc] = mb[cc] = 1;
+                        if (comp) mhl[cc] = 1;
+                    }
+                }
+                bytes += n * 2.0 * T;                        // the two ring shares C (one per edge end)
+                bytes += g.type == SEG_EDGE_UPD ? n * T * (2.0 + 3.0 * c) : n * T * (g.flag ? 1 : 2);
+                break;
+            case SEG_PRED:
+                bytes += n * T * (g.flag ? 2.0 * (1 + c) : 4.0 * (1 + c));
+                break;
+            case SEG_COPY:
+                bytes += n * T * 2.0 * (1 + c);
+                break;
+            case SEG_REPLAY:
+                bytes += n * T * (5.0 + 2.0 * c);
+                break;
+        }
+    }
+    double cnt = 0.0;
+    for (int k = 0; k < nC; ++k) cnt += mh[k] + mhl[k] + mk[k] + mb[k];
+    for (char x : mu) cnt += x;
+    for (char x : mq) cnt += x;
+    return bytes + cnt * T;
+}
+
+// ------------------------------------------------------------ phase plans
+
+struct Planner {
+    lts_state_s* S;
+    const RegionsHost& r;
+    const int* cb;
+    const int* eb;
+    const int* vb;
+    bool comp;
+
+    SegDesc vert(int lo, int hi) const {   // vertex bands lo..hi
+        SegDesc s;
+        s.type = SEG_VERT;
+        s.begin = vb[lo];
+        s.end = vb[hi + 1];
+        return s;
+    }
+    SegDesc ring(int lo, int hi) const {   // ring results only, cell bands lo..hi
+        SegDesc s;
+        s.type = SEG_RING;
+        s.begin = cb[lo];
+        s.end = cb[hi + 1];
+        return s;
+    }
+    SegDesc upd(bool cell, int lo, int hi, const SV& old, const SV& in, const SV& out, double a,
+                double D) const {
+        SegDesc s;
+        s.type = cell ? SEG_RING_UPD : SEG_EDGE_UPD;
+        const int* ofs = cell ? cb : eb;
+        s.begin = ofs[lo];
+        s.end = ofs[hi + 1];
+        s.p[0] = cell ? old.hh : old.uh;
+        s.p[1] = cell ? old.hl : old.ul;
+        s.p[2] = cell ? in.hl : in.ul;
+        s.p[3] = cell ? out.hh : out.uh;
+        s.p[4] = cell ? out.hl : out.ul;
+        s.c[0] = a;
+        s.c[1] = D;
+        return s;
+    }
+    SegDesc acc(bool cell, int stage, bool first) const {
+        SegDesc s;
+        s.type = cell ? SEG_RING_ACC : SEG_EDGE_ACC;
+        const int* ofs = cell ? cb : eb;
+        s.begin = ofs[B_I1];
+        s.end = ofs[B_I2 + 1];
+        s.base = ofs[B_I1];
+        s.flag = first ? 1 : 0;
+        s.p[0] = cell ? S->acc_c[stage] : S->acc_e[stage];
+        return s;
+    }
+    // x[I1] = prediction (Steps 3.x.1) from x_old (full), P1, P2 (compact)
+    SegDesc pred(bool cell, const SV& old, const SV& out, int k, int M, int which) const {
+        double a, at;
+        const double kk = k, MM = M;
+        if (which == 1) {          // alpha
+            a = kk / MM;
+            at = kk * kk / (MM * MM);
+        } else if (which == 2) {   // beta
+            a = (kk + 1.0) / MM;
+            at = kk * (kk + 2.0) / (MM * MM);
+        } else {                   // gamma
+            a = (2.0 * kk + 1.0) / (2.0 * MM);
+            at = (2.0 * kk * kk + 2.0 * kk + 1.0) / (2.0 * MM * MM);
+        }
+        const double c1 = a - at, c2 = 2.0 * at;
+        SegDesc s;
+        s.type = SEG_PRED;
+        const int* ofs = cell ? cb : eb;
+        s.begin = ofs[B_I1];
+        s.end = ofs[B_I1 + 1];
+        s.base = ofs[B_I1];
+        s.flag = (c1 == 0.0 && c2 == 0.0) ? 1 : (c1 == 1.0 && c2 == 0.0) ? 2 : (c1 == 0.0 && c2 == 1.0) ? 3 : 0;
+        const SV& p1 = cell ? S->P1c : S->P1e;
+        const SV& p2 = cell ? S->P2c : S->P2e;
+        s.p[0] = cell ? old.hh : old.uh;
+        s.p[1] = cell ? old.hl : old.ul;
+        s.p[2] = cell ? p1.hh : p1.uh;
+        s.p[3] = cell ? p1.hl : p1.ul;
+        s.p[4] = cell ? p2.hh : p2.uh;
+        s.p[5] = cell ? p2.hl : p2.ul;
+        s.p[6] = cell ? out.hh : out.uh;
+        s.p[7] = cell ? out.hl : out.ul;
+        s.c[0] = c1;
+        s.c[1] = c2;
+        return s;
+    }
+    SegDesc copy(bool cell, int lo, int hi, const SV& src, const SV& dst, int dst_base) const {
+        SegDesc s;
+        s.type = SEG_COPY;
+        const int* ofs = cell ? cb : eb;
+        s.begin = ofs[lo];
+        s.end = ofs[hi + 1];
+        s.base = dst_base;
+        s.base2 = 0;
+        s.p[0] = cell ? src.hh : src.uh;
+        s.p[1] = cell ? src.hl : src.ul;
+        s.p[2] = cell ? dst.hh : dst.uh;
+        s.p[3] = cell ? dst.hl : dst.ul;
+        return s;
+    }
+    SegDesc replay(bool cell, const SV& old, const SV& out, double dtM) const {
+        SegDesc s;
+        s.type = SEG_REPLAY;
+        const int* ofs = cell ? cb : eb;
+        s.begin = ofs[B_I1];
+        s.end = ofs[B_I2 + 1];
+        s.base = ofs[B_I1];
+        s.p[0] = cell ? old.hh : old.uh;
+        s.p[1] = cell ? old.hl : old.ul;
+        for (int k = 0; k < 3; ++k) s.p[2 + k] = cell ? S->acc_c[k] : S->acc_e[k];
+        s.p[5] = cell ? out.hh : out.uh;
+        s.p[6] = cell ? out.hl : out.ul;
+        s.c[0] = dtM;
+        s.c[1] = dtM / 4.0;
+        s.c[2] = 2.0 * dtM / 3.0;
+        return s;
+    }
+    LaunchDesc launch(int kind, const SV& in, std::initializer_list<SegDesc> segs) const {
+        LaunchDesc d;
+        d.kind = kind;
+        d.in_h = in.hh;
+        d.in_hl = in.hl;
+        d.in_u = in.uh;
+        d.q = S->q;
+        d.ring_c = S->ring_c;
+        d.ring_k = S->ring_k;
+        d.g = S->p.g;
+        for (const SegDesc& s : segs)
+            if (s.end > s.begin) d.seg[d.nseg++] = s;
+        return d;
+    }
+};
+
+constexpr double A1 = 0.0, A2 = 0.75, A3 = 1.0 / 3.0;
+
+void plan_lts3(lts_state_s* S, int parity, std::vector<LaunchDesc>& out) {
+    const RegionsHost& r = S->reg->r;
+    Planner P{S, r, r.cb, r.eb, r.vb, S->kc.comp};
+    const SV& X0 = S->buf[parity];
+    const SV& XN = S->buf[1 - parity];
+    const SV& X1 = S->buf[2];
+    const SV& X2 = S->buf[3];
+    const double dt = S->p.dt;
+    const int M = r.M;
+    const double dtM = dt / M;
+    const int I1 = r.cb[B_I1];
+    const int I1e = r.eb[B_I1];
+    const SegDesc none;
+    out.clear();
+    // Each right-hand side updating bands [lo, hi] is three launches:
+    // vertex bands [lo-1, hi+1], ring cells [lo, hi+1], edges [lo, hi].
+    // Step 1: first stage on Fbar u I1 u I2 u C (bands F2..C rest)
+    out.push_back(P.launch(0, X0, {P.vert(B_F3, B_CREST), P.copy(true, B_I2, B_C2, X0, XN, 0)}));
+    out.push_back(P.launch(1, X0, {P.upd(true, B_F2, B_CREST, X0, X0, X1, A1, dt)}));
+    out.push_back(P.launch(2, X0, {P.upd(false, B_F2, B_CREST, X0, X0, X1, A1, dt),
+                                   P.copy(false, B_I2, B_C2, X0, XN, 0),
+                                   P.copy(true, B_I1, B_I1, X1, S->P1c, I1)}));
+    // Step 2: second stage on I1 u I2 u C
+    out.push_back(P.launch(0, X1, {P.vert(B_F1, B_CREST), P.copy(false, B_I1, B_I1, X1, S->P1e, I1e)}));
+    out.push_back(P.launch(1, X1, {P.upd(true, B_I1, B_CREST, X0, X1, X2, A2, dt / 4.0)}));
+    out.push_back(P.launch(2, X1, {P.upd(false, B_I1, B_CREST, X0, X1, X2, A2, dt / 4.0),
+                                   P.copy(true, B_I1, B_I1, X2, S->P2c, I1)}));
+    // Step 3: M fine substeps on F, correction terms on I1 u I2, I1 predicted
+    for (int k = 0; k < M; ++k) {
+        const SV& old = (k == 0) ? X0 : XN;
+        for (int s = 1; s <= 3; ++s) {
+            const SV& in = (s == 1) ? old : (s == 2 ? X1 : X2);
+            const SV& o = (s == 1) ? X1 : (s == 2 ? X2 : XN);
+            const double a = (s == 1) ? A1 : (s == 2 ? A2 : A3);
+            const double D = (s == 1) ? dtM : (s == 2 ? dtM / 4.0 : 2.0 * dtM / 3.0);
+            // prediction of I1 for the next stage that reads it
+            SegDesc pc, pe;
+            if (s == 1) {
+                pc = P.pred(true, X0, X1, k, M, 2);
+                pe = P.pred(false, X0, X1, k, M, 2);
+            } else if (s == 2) {
+                pc = P.pred(true, X0, X2, k, M, 3);
+                pe = P.pred(false, X0, X2, k, M, 3);
+            } else if (k + 1 < M) {
+                pc = P.pred(true, X0, XN, k + 1, M, 1);
+                pe = P.pred(false, X0, XN, k + 1, M, 1);
+            }
+            const SegDesc snap = (k == 0 && s == 1) ? P.copy(false, B_I1, B_I1, X2, S->P2e, I1e) : none;
+            out.push_back(P.launch(0, in, {P.vert(B_FDEEP, B_C1), snap}));
+            out.push_back(P.launch(1, in, {P.upd(true, B_FDEEP, B_F1, old, in, o, a, D),
+                                           P.acc(true, s - 1, k == 0), P.ring(B_C1, B_C1), pc}));
+            out.push_back(P.launch(2, in, {P.upd(false, B_FDEEP, B_F1, old, in, o, a, D),
+                                           P.acc(false, s - 1, k == 0), pe}));
+        }
+    }
+    // Step 4 (third stage on C) and Step 5 (interface correction)
+    out.push_back(P.launch(0, X2, {P.vert(B_I2, B_CREST)}));
+    out.push_back(P.launch(1, X2, {P.upd(true, B_C1, B_CREST, X0, X2, XN, A3, 2.0 * dt / 3.0),
+                                   P.replay(true, X0, XN, dtM)}));
+    out.push_back(P.launch(2, X2, {P.upd(false, B_C1, B_CREST, X0, X2, XN, A3, 2.0 * dt / 3.0),
+                                   P.replay(false, X0, XN, dtM)}));
+    out.erase(std::remove_if(out.begin(), out.end(), [](const LaunchDesc& d) { return d.nseg == 0; }),
+              out.end());
+}
+
+void plan_ssprk3(lts_state_s* S, int parity, std::vector<LaunchDesc>& out) {
+    const RegionsHost& r = S->reg->r;
+    Planner P{S, r, r.cb, r.eb, r.vb, S->kc.comp};
+    const SV& X0 = S->buf[parity];
+    const SV& XN = S->buf[1 - parity];
+    const SV& X1 = S->buf[2];
+    const SV& X2 = S->buf[3];
+    const double dt = S->p.dt;
+    out.clear();
+    const SV* ins[3] = {&X0, &X1, &X2};
+    const SV* outs[3] = {&X1, &X2, &XN};
+    const double as[3] = {A1, A2, A3};
+    const double Ds[3] = {dt, dt / 4.0, 2.0 * dt / 3.0};
+    for (int s = 0; s < 3; ++s) {
+        out.push_back(P.launch(0, *ins[s], {P.vert(B_FDEEP, B_CREST)}));
+        out.push_back(P.launch(1, *ins[s], {P.upd(true, B_FDEEP, B_CREST, X0, *ins[s], *outs[s], as[s], Ds[s])}));
+        out.push_back(P.launch(2, *ins[s], {P.upd(false, B_FDEEP, B_CREST, X0, *ins[s], *outs[s], as[s], Ds[s])}));
+    }
+}
+
+int enqueue_plan(lts_state_s* S, const std::vector<LaunchDesc>& plan, cudaStream_t st) {
+    for (const LaunchDesc& d : plan) {
+        cudaError_t e = launch_phase(d, S->tables, S->kc, S->flag, st);
+        if (e != cudaSuccess) return set_error(LTS_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
+    }
+    return LTS_OK;
+}
+
+int capture_graphs(lts_state_s* S) {
+    for (int p = 0; p < 2; ++p) {
+        cudaGraph_t g = nullptr;
+        CUDA_TRY(cudaStreamBeginCapture(S->capture_stream, cudaStreamCaptureModeThreadLocal));
+        int rc = enqueue_plan(S, S->plan[p], S->capture_stream);
+        cudaError_t e = cudaStreamEndCapture(S->capture_stream, &g);
+        if (rc != LTS_OK) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        CUDA_TRY(e);
+        e = cudaGraphInstantiate(&S->exec[p], g, 0);
+        cudaGraphDestroy(g);
+        CUDA_TRY(e);
+    }
+    return LTS_OK;
+}
+
+int state_alloc(lts_state_s* S) {
+    const RegionsHost& r = S->reg->r;
+    const HostMesh& m = S->reg->mesh->m;
+    const size_t T = S->tsz;
+    const bool comp = S->kc.comp;
+    cudaError_t err = cudaSuccess;
+    auto A = [&](size_t n) { return S->arena.alloc(n * T, err); };
+    for (int k = 0; k < 4; ++k) {
+        S->buf[k].hh = A(m.nC);
+        S->buf[k].uh = A(m.nE);
+        if (comp) {
+            S->buf[k].hl = A(m.nC);
+            S->buf[k].ul = A(m.nE);
+        }
+    }
+    const int nI1c = r.cb[B_I1 + 1] - r.cb[B_I1], nI1e = r.eb[B_I1 + 1] - r.eb[B_I1];
+    const int nIc = r.cb[B_I2 + 1] - r.cb[B_I1], nIe = r.eb[B_I2 + 1] - r.eb[B_I1];
+    for (SV* p : {&S->P1c, &S->P2c}) {
+        p->hh = A(nI1c);
+        if (comp) p->hl = A(nI1c);
+    }
+    for (SV* p : {&S->P1e, &S->P2e}) {
+        p->uh = A(nI1e);
+        if (comp) p->ul = A(nI1e);
+    }
+    for (int k = 0; k < 3; ++k) {
+        S->acc_c[k] = A(nIc);
+        S->acc_e[k] = A(nIe);
+    }
+    S->q = A(m.nV);
+    S->ring_c = A(static_cast<size_t>(m.maxE) * m.nC);
+    S->ring_k = A(m.nC);
+    S->flag = static_cast<int*>(S->arena.alloc(sizeof(int), err));
+    S->stage_c = static_cast<double*>(S->arena.alloc(sizeof(double) * m.nC, err));
+    S->stage_e = static_cast<double*>(S->arena.alloc(sizeof(double) * m.nE, err));
+    S->diag_blocks = std::max(1, std::min(1024, (m.nC + 255) / 256));
+    S->diag_partial = static_cast<double*>(S->arena.alloc(sizeof(double) * 2 * S->diag_blocks, err));
+    S->diag_out = static_cast<double*>(S->arena.alloc(sizeof(double) * 2, err));
+    if (err != cudaSuccess)
+        return set_error(err == cudaErrorMemoryAllocation ? LTS_ENOMEM : LTS_ECUDA,
+                         "state allocation: %s", cudaGetErrorString(err));
+    // the zero fills ran on the legacy stream; the state's stream does not wait for it
+    CUDA_TRY(cudaDeviceSynchronize());
+    return LTS_OK;
+}
+
+int write_state(lts_state_s* S, const double* h, const double* u) {
+    const HostMesh& m = S->reg->mesh->m;
+    const SV& X = S->buf[S->parity];
+    CUDA_TRY(cudaMemcpyAsync(S->stage_c, h, sizeof(double) * m.nC, cudaMemcpyHostToDevice, S->stream));
+    CUDA_TRY(cudaMemcpyAsync(S->stage_e, u, sizeof(double) * m.nE, cudaMemcpyHostToDevice, S->stream));
+    CUDA_TRY(launch_scatter_state(S->kc, m.nC, S->reg->d_perm_c, S->stage_c, X.hh, X.hl, S->stream));
+    CUDA_TRY(launch_scatter_state(S->kc, m.nE, S->reg->d_perm_e, S->stage_e, X.uh, X.ul, S->stream));
+    return LTS_OK;
+}
+
+}  // namespace
+
+lts_state_s::~lts_state_s() {
+    for (auto& e : exec)
+        if (e) cudaGraphExecDestroy(e);
+    for (auto ev : events) cudaEventDestroy(ev);
+    if (own_stream && stream) cudaStreamDestroy(stream);
+    if (capture_stream) cudaStreamDestroy(capture_stream);
+}
+
+// ---------------------------------------------------------------- the C ABI
+
+extern "C" {
+
+int lts_mesh_create(const lts_mesh_desc* d, lts_mesh* out) {
+    if (!d || !out) return set_error(LTS_EINVAL, "null argument");
+    *out = nullptr;
+    const int nC = d->nCells, nE = d->nEdges, nV = d->nVertices, W = d->maxEdges;
+    if (nC < 3 || nE < 3 || nV < 2 || W < 3 || W > MAX_DEGREE)
+        return set_error(LTS_EINVAL, "bad mesh sizes (nCells %d, nEdges %d, nVertices %d, maxEdges %d)",
+                         nC, nE, nV, W);
+    if (!d->nEdgesOnCell || !d->edgesOnCell || !d->cellsOnCell || !d->verticesOnCell ||
+        !d->cellsOnEdge || !d->verticesOnEdge || !d->edgesOnVertex || !d->cellsOnVertex ||
+        !d->areaCell || !d->areaTriangle || !d->kiteAreasOnVertex || !d->dcEdge || !d->dvEdge ||
+        !d->fVertex)
+        return set_error(LTS_EINVAL, "a required mesh array is NULL");
+    std::unique_ptr<lts_mesh_s> M(new (std::nothrow) lts_mesh_s);
+    if (!M) return set_error(LTS_ENOMEM, "out of host memory");
+    HostMesh& m = M->m;
+    m.nC = nC; m.nE = nE; m.nV = nV; m.maxE = W;
+    m.sphere = d->on_sphere != 0;
+    m.R = d->radius; m.Lx = d->period_x; m.Ly = d->period_y;
+    auto cp = [](auto* p, size_t n, auto& v) { v.assign(p, p + n); };
+    try {
+        if (d->xCell && d->yCell && d->zCell) {
+            cp(d->xCell, nC, m.xc); cp(d->yCell, nC, m.yc); cp(d->zCell, nC, m.zc);
+        } else {
+            m.xc.assign(nC, 0.0); m.yc.assign(nC, 0.0); m.zc.assign(nC, 0.0);
+        }
+        cp(d->nEdgesOnCell, nC, m.nEoC);
+        cp(d->edgesOnCell, (size_t)nC * W, m.EoC);
+        cp(d->cellsOnCell, (size_t)nC * W, m.CoC);
+        cp(d->verticesOnCell, (size_t)nC * W, m.VoC);
+        cp(d->cellsOnEdge, 2 * (size_t)nE, m.CoE);
+        cp(d->verticesOnEdge, 2 * (size_t)nE, m.VoE);
+        cp(d->edgesOnVertex, 3 * (size_t)nV, m.EoV);
+        cp(d->cellsOnVertex, 3 * (size_t)nV, m.CoV);
+        cp(d->areaCell, nC, m.A);
+        cp(d->areaTriangle, nV, m.Av);
+        cp(d->kiteAreasOnVertex, 3 * (size_t)nV, m.kite);
+        cp(d->dcEdge, nE, m.dc);
+        cp(d->dvEdge, nE, m.dv);
+        cp(d->fVertex, nV, m.f);
+        if (d->bottom) cp(d->bottom, nC, m.b);
+        else m.b.assign(nC, 0.0);
+    } catch (const std::bad_alloc&) {
+        return set_error(LTS_ENOMEM, "out of host memory");
+    }
+    // ---- validation
+    for (int i = 0; i < nC; ++i) {
+        int n = m.nEoC[i];
+        if (n < 3 || n > W) return set_error(LTS_EINVAL, "cell %d has %d edges", i, n);
+        if (!(m.A[i] > 0.0)) return set_error(LTS_EINVAL, "areaCell[%d] <= 0", i);
+        for (int j = 0; j < n; ++j) {
+            int e = m.EoC[(size_t)i * W + j], nb = m.CoC[(size_t)i * W + j], v = m.VoC[(size_t)i * W + j];
+            if (e < 0 || e >= nE || nb < 0 || nb >= nC || v < 0 || v >= nV)
+                return set_error(LTS_EINVAL, "cell %d slot %d: index out of range", i, j);
+        }
+    }
+    for (int e = 0; e < nE; ++e) {
+        for (int k = 0; k < 2; ++k) {
+            if (m.CoE[2 * e + k] < 0 || m.CoE[2 * e + k] >= nC || m.VoE[2 * e + k] < 0 ||
+                m.VoE[2 * e + k] >= nV)
+                return set_error(LTS_EINVAL, "edge %d: index out of range", e);
+        }
+        if (m.CoE[2 * e] == m.CoE[2 * e + 1]) return set_error(LTS_EINVAL, "edge %d joins a cell to itself", e);
+        if (!(m.dc[e] > 0.0) || !(m.dv[e] >= 0.0)) return set_error(LTS_EINVAL, "edge %d: bad lengths", e);
+    }
+    for (int v = 0; v < nV; ++v) {
+        if (!(m.Av[v] > 0.0)) return set_error(LTS_EINVAL, "areaTriangle[%d] <= 0", v);
+        double s = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            if (m.EoV[3 * v + k] < 0 || m.EoV[3 * v + k] >= nE || m.CoV[3 * v + k] < 0 || m.CoV[3 * v + k] >= nC)
+                return set_error(LTS_EINVAL, "vertex %d: index out of range", v);
+            s += m.kite[3 * v + k];
+        }
+        if (std::fabs(s - m.Av[v]) > 1e-9 * m.Av[v])
+            return set_error(LTS_EINVAL, "kites of vertex %d do not sum to areaTriangle", v);
+    }
+    // rings: slot j joins cell i and cellsOnCell[j]; vertex j is shared by
+    // slots j and j+1; the ring is counter-clockwise (t_{e_j, v_j} = n_{e_j, i})
+    std::vector<double> ksum(nC, 0.0);
+    for (int v = 0; v < nV; ++v)
+        for (int k = 0; k < 3; ++k) ksum[m.CoV[3 * v + k]] += m.kite[3 * v + k];
+    for (int i = 0; i < nC; ++i) {
+        if (std::fabs(ksum[i] - m.A[i]) > 1e-9 * m.A[i])
+            return set_error(LTS_EINVAL, "kites of cell %d do not sum to areaCell", i);
+        int n = m.nEoC[i];
+        for (int j = 0; j < n; ++j) {
+            int e = m.EoC[(size_t)i * W + j], nb = m.CoC[(size_t)i * W + j];
+            int v = m.VoC[(size_t)i * W + j];
+            int e2 = m.EoC[(size_t)i * W + (j + 1) % n];
+            bool has_i = m.CoE[2 * e] == i || m.CoE[2 * e + 1] == i;
+            bool has_nb = m.CoE[2 * e] == nb || m.CoE[2 * e + 1] == nb;
+            if (!has_i || !has_nb) return set_error(LTS_EINVAL, "cell %d slot %d: edge/neighbour mismatch", i, j);
+            bool v_on_e = m.VoE[2 * e] == v || m.VoE[2 * e + 1] == v;
+            bool v_on_e2 = m.VoE[2 * e2] == v || m.VoE[2 * e2 + 1] == v;
+            if (!v_on_e || !v_on_e2) return set_error(LTS_EINVAL, "cell %d slot %d: vertex not between slots", i, j);
+            bool left = m.VoE[2 * e + 1] == v;
+            bool out = m.CoE[2 * e] == i;
+            if (left != out) return set_error(LTS_EINVAL, "cell %d: ring is not counter-clockwise", i);
+        }
+    }
+    // optional MPAS weights: compare with the kite-derived ones
+    if (d->weightsOnEdge && d->edgesOnEdge && d->nEdgesOnEdge) {
+        for (int e = 0; e < nE; ++e) {
+            int cnt = d->nEdgesOnEdge[e];
+            for (int q = 0; q < cnt; ++q) {
+                int ep = d->edgesOnEdge[(size_t)e * 2 * W + q];
+                double w = d->weightsOnEdge[(size_t)e * 2 * W + q];
+                double best = 1e300;
+                for (int s = 0; s < 2; ++s) {
+                    int c = m.CoE[2 * e + s];
+                    int jp = -1, je = -1;
+                    for (int j = 0; j < m.nEoC[c]; ++j) {
+                        if (m.EoC[(size_t)c * W + j] == ep) jp = j;
+                        if (m.EoC[(size_t)c * W + j] == e) je = j;
+                    }
+                    if (jp >= 0 && je >= 0) best = std::min(best, std::fabs(derived_weight(m, c, jp, je) - w));
+                }
+                if (best > 1e-9)
+                    return set_error(LTS_EINVAL, "weightsOnEdge[%d][%d] disagrees with the kite areas", e, q);
+            }
+        }
+    }
+    *out = M.release();
+    return LTS_OK;
+}
+
+void lts_mesh_destroy(lts_mesh m) { release_mesh(m); }
+
+int lts_regions_set(lts_mesh m, const int8_t* fine_mask, int32_t order, int32_t M, int32_t layers,
+                    lts_regions* out) {
+    if (!m || !fine_mask || !out) return set_error(LTS_EINVAL, "null argument");
+    *out = nullptr;
+    if (order != 3) return set_error(LTS_EINVAL, "order %d not supported (3 = LTS3)", order);
+    if (M < 1 || M > 4096) return set_error(LTS_EINVAL, "M must be in [1, 4096]");
+    std::unique_ptr<lts_regions_s> R(new (std::nothrow) lts_regions_s);
+    if (!R) return set_error(LTS_ENOMEM, "out of host memory");
+    int rc;
+    try {
+        rc = compute_regions(m->m, fine_mask, layers, R->r);
+    } catch (const std::bad_alloc&) {
+        return set_error(LTS_ENOMEM, "out of host memory");
+    }
+    if (rc != LTS_OK) return rc;
+    R->r.M = M;
+    m->ref++;
+    R->mesh = m;
+    *out = R.release();
+    return LTS_OK;
+}
+
+void lts_regions_destroy(lts_regions r) { release_regions(r); }
+
+int lts_regions_labels(lts_regions r, int8_t* cl, int8_t* el) {
+    if (!r) return set_error(LTS_EINVAL, "null regions");
+    static const int8_t cmap[NBANDS] = {0, 0, 1, 2, 3, 4, 5, 5, 5};
+    static const int8_t emap[NBANDS] = {0, 0, 1, 1, 3, 4, 5, 5, 5};
+    if (cl)
+        for (size_t i = 0; i < r->r.cband.size(); ++i) cl[i] = cmap[r->r.cband[i]];
+    if (el)
+        for (size_t e = 0; e < r->r.eband.size(); ++e) el[e] = emap[r->r.eband[e]];
+    return LTS_OK;
+}
+
+int lts_regions_counts(lts_regions r, int64_t* cells, int64_t* edges, int64_t* vertices) {
+    if (!r) return set_error(LTS_EINVAL, "null regions");
+    for (int k = 0; k < NBANDS; ++k) {
+        if (cells) cells[k] = r->r.cb[k + 1] - r->r.cb[k];
+        if (edges) edges[k] = r->r.eb[k + 1] - r->r.eb[k];
+        if (vertices) vertices[k] = r->r.vb[k + 1] - r->r.vb[k];
+    }
+    return LTS_OK;
+}
+
+int lts_regions_permutation(lts_regions r, int32_t* pc, int32_t* pe, int32_t* pv) {
+    if (!r) return set_error(LTS_EINVAL, "null regions");
+    if (pc) std::copy(r->r.perm_c.begin(), r->r.perm_c.end(), pc);
+    if (pe) std::copy(r->r.perm_e.begin(), r->r.perm_e.end(), pe);
+    if (pv) std::copy(r->r.perm_v.begin(), r->r.perm_v.end(), pv);
+    return LTS_OK;
+}
+
+int lts_state_create(lts_mesh mesh, lts_regions reg, const double* h0, const double* u0,
+                     const lts_params* p, lts_state* out) {
+    if (!mesh || !reg || !h0 || !u0 || !p || !out) return set_error(LTS_EINVAL, "null argument");
+    *out = nullptr;
+    if (reg->mesh != mesh) return set_error(LTS_EINVAL, "regions belong to another mesh");
+    if (!(p->dt > 0.0) || !(p->g > 0.0)) return set_error(LTS_EINVAL, "dt and g must be > 0");
+    if (p->precision != LTS_FP32 && p->precision != LTS_FP64)
+        return set_error(LTS_EINVAL, "precision must be LTS_FP32 or LTS_FP64");
+    if (p->mode != LTS_MODE_LTS3 && p->mode != LTS_MODE_SSPRK3)
+        return set_error(LTS_EINVAL, "mode must be LTS_MODE_LTS3 or LTS_MODE_SSPRK3");
+    int bs = p->block_size ? p->block_size : 256;
+    if (bs < 32 || bs > 256 || bs % 32) return set_error(LTS_EINVAL, "block_size must be 32..256, multiple of 32");
+    int rc = check_device();
+    if (rc != LTS_OK) return rc;
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (reg->device >= 0 && reg->device != dev) return set_error(LTS_EINVAL, "regions live on another device");
+    reg->device = dev;
+    const int which = p->precision == LTS_FP64 ? 1 : 0;
+    if (!reg->arena[which]) {
+        rc = which ? build_tables<double>(reg, 1, reg->t64) : build_tables<float>(reg, 0, reg->t32);
+        if (rc != LTS_OK) return rc;
+    }
+    std::unique_ptr<lts_state_s> S(new (std::nothrow) lts_state_s);
+    if (!S) return set_error(LTS_ENOMEM, "out of host memory");
+    S->p = *p;
+    S->kc.precision = which;
+    S->kc.comp = (which == 0) && p->compensated;
+    S->kc.block = bs;
+    S->kc.maxdeg = mesh->m.maxE <= 8 ? 8 : MAX_DEGREE;
+    S->tsz = which ? 8 : 4;
+    S->tables = which ? static_cast<const void*>(&reg->t64) : static_cast<const void*>(&reg->t32);
+    if (p->stream) {
+        S->stream = static_cast<cudaStream_t>(p->stream);
+    } else {
+        CUDA_TRY(cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking));
+        S->own_stream = true;
+    }
+    CUDA_TRY(cudaStreamCreateWithFlags(&S->capture_stream, cudaStreamNonBlocking));
+    reg->ref++;
+    S->reg = reg;
+    rc = state_alloc(S.get());
+    if (rc != LTS_OK) {
+        release_regions(reg);
+        S->reg = nullptr;
+        return rc;
+    }
+    for (int par = 0; par < 2; ++par) {
+        if (p->mode == LTS_MODE_LTS3) plan_lts3(S.get(), par, S->plan[par]);
+        else plan_ssprk3(S.get(), par, S->plan[par]);
+    }
+    // launch statistics of one step (both parities have the same sizes)
+    const HostMesh& m = mesh->m;
+    for (LaunchDesc& d : S->plan[0]) {
+        d.bytes = launch_bytes(d, reg->r, m.nC, m.nE, m.nV, S->tsz, S->kc.comp);
+        S->bytes[d.kind] += d.bytes;
+        S->launches[d.kind] += 1;
+    }
+    rc = write_state(S.get(), h0, u0);
+    if (rc == LTS_OK && p->use_graph && !p->profile) rc = capture_graphs(S.get());
+    if (rc == LTS_OK) {
+        cudaError_t e = cudaStreamSynchronize(S->stream);
+        if (e != cudaSuccess) rc = set_error(LTS_ECUDA, "state upload: %s", cudaGetErrorString(e));
+    }
+    if (rc != LTS_OK) {
+        lts_regions_s* keep = S->reg;
+        S.reset();
+        release_regions(keep);
+        return rc;
+    }
+    *out = S.release();
+    return LTS_OK;
+}
+
+void lts_state_destroy(lts_state s) {
+    if (!s) return;
+    cudaStreamSynchronize(s->stream);
+    lts_regions_s* r = s->reg;
+    delete s;
+    release_regions(r);
+}
+
+int lts_step(lts_state s, int32_t n) {
+    if (!s) return set_error(LTS_EINVAL, "null state");
+    if (n < 0) return set_error(LTS_EINVAL, "n_coarse must be >= 0");
+    if (s->p.profile) {
+        const size_t L = s->plan[0].size();
+        if (s->events.size() < 2 * L) {
+            for (size_t k = s->events.size(); k < 2 * L; ++k) {
+                cudaEvent_t ev;
+                CUDA_TRY(cudaEventCreate(&ev));
+                s->events.push_back(ev);
+            }
+        }
+        for (double& x : s->prof_ms) x = 0.0;
+        for (int i = 0; i < n; ++i) {
+            const auto& plan = s->plan[s->parity];
+            for (size_t k = 0; k < plan.size(); ++k) {
+                CUDA_TRY(cudaEventRecord(s->events[2 * k], s->stream));
+                cudaError_t e = launch_phase(plan[k], s->tables, s->kc, s->flag, s->stream);
+                if (e != cudaSuccess) return set_error(LTS_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
+                CUDA_TRY(cudaEventRecord(s->events[2 * k + 1], s->stream));
+            }
+            CUDA_TRY(cudaStreamSynchronize(s->stream));
+            for (size_t k = 0; k < plan.size(); ++k) {
+                float ms = 0.f;
+                CUDA_TRY(cudaEventElapsedTime(&ms, s->events[2 * k], s->events[2 * k + 1]));
+                s->prof_ms[plan[k].kind] += ms;
+            }
+            s->parity ^= 1;
+            s->steps++;
+            s->time += s->p.dt;
+        }
+        return LTS_OK;
+    }
+    for (int i = 0; i < n; ++i) {
+        if (s->exec[s->parity]) {
+            CUDA_TRY(cudaGraphLaunch(s->exec[s->parity], s->stream));
+        } else {
+            int rc = enqueue_plan(s, s->plan[s->parity], s->stream);
+            if (rc != LTS_OK) return rc;
+        }
+        s->parity ^= 1;
+        s->steps++;
+        s->time += s->p.dt;
+    }
+    return LTS_OK;
+}
+
+int lts_read(lts_state s, double* h, double* u, lts_diag* d) {
+    if (!s) return set_error(LTS_EINVAL, "null state");
+    const HostMesh& m = s->reg->mesh->m;
+    const SV& X = s->buf[s->parity];
+    if (h) {
+        CUDA_TRY(launch_gather_state(s->kc, m.nC, s->reg->d_perm_c, X.hh, X.hl, s->stage_c, s->stream));
+        CUDA_TRY(cudaMemcpyAsync(h, s->stage_c, sizeof(double) * m.nC, cudaMemcpyDeviceToHost, s->stream));
+    }
+    if (u) {
+        CUDA_TRY(launch_gather_state(s->kc, m.nE, s->reg->d_perm_e, X.uh, X.ul, s->stage_e, s->stream));
+        CUDA_TRY(cudaMemcpyAsync(u, s->stage_e, sizeof(double) * m.nE, cudaMemcpyDeviceToHost, s->stream));
+    }
+    double diag[2] = {0, 0};
+    if (d) {
+        CUDA_TRY(launch_diagnostics(s->kc, s->tables, X.hh, X.hl, X.uh, X.ul, s->p.g, s->diag_partial,
+                                    s->diag_blocks, s->diag_out, s->stream));
+        CUDA_TRY(cudaMemcpyAsync(diag, s->diag_out, sizeof(diag), cudaMemcpyDeviceToHost, s->stream));
+    }
+    int flag = 0;
+    CUDA_TRY(cudaMemcpyAsync(&flag, s->flag, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(cudaMemsetAsync(s->flag, 0, sizeof(int), s->stream));
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    if (d) {
+        d->mass = diag[0];
+        d->energy = diag[1];
+        d->time = s->time;
+        d->steps = s->steps;
+    }
+    if (flag) return set_error(LTS_ENONFINITE, "a stage produced %s", (flag & 1) ? "a thickness <= 0 or non-finite" : "a non-finite velocity");
+    return LTS_OK;
+}
+
+int lts_write(lts_state s, const double* h, const double* u, double time, int64_t steps) {
+    if (!s || !h || !u) return set_error(LTS_EINVAL, "null argument");
+    int rc = write_state(s, h, u);
+    if (rc != LTS_OK) return rc;
+    s->time = time;
+    s->steps = steps;
+    return LTS_OK;
+}
+
+int lts_step_stats(lts_state s, int32_t* launches_per_step, double* bytes, double* ms,
+                   int32_t* launches_per_kind) {
+    if (!s) return set_error(LTS_EINVAL, "null state");
+    if (launches_per_step) *launches_per_step = s->launches[0] + s->launches[1] + s->launches[2];
+    for (int k = 0; k < NKINDS; ++k) {
+        if (bytes) bytes[k] = s->bytes[k];
+        if (ms) ms[k] = s->prof_ms[k];
+        if (launches_per_kind) launches_per_kind[k] = s->launches[k];
+    }
+    return LTS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,121 @@
+// lts_internal.h -- structures shared by the host runtime (C++) and the
+// CUDA kernels of liblts.so.  Not part of the public ABI.
+#pragma once
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+namespace lts {
+
+// Bands of the band ordering (cells; an edge takes the smaller band of its
+// two cells, a vertex the smallest band of its three cells).
+enum Band : int {
+    B_FDEEP = 0, B_F3 = 1, B_F2 = 2, B_F1 = 3, B_I1 = 4, B_I2 = 5, B_C1 = 6, B_C2 = 7,
+    B_CREST = 8, NBANDS = 9
+};
+
+// Device tables in band order.  Cell "slot" arrays are slot-major:
+// element (slot j, cell c) is at [j * nC + c]; slot j of cell c holds the
+// j-th edge of c counter-clockwise, the neighbour across it, and the vertex
+// between slot j and slot j+1.
+template <class T>
+struct Tables {
+    int nC, nE, nV, maxE;
+    // cells
+    const uint8_t* cn;   // [nC]       number of edges
+    const int* se;       // [maxE*nC]  edge of slot j
+    const int* sn;       // [maxE*nC]  neighbour cell across slot j
+    const int* sv;       // [maxE*nC]  vertex between slot j and j+1
+    const T* snl;        // [maxE*nC]  n_{e,c} l_e      (signed primal length)
+    const T* sR;         // [maxE*nC]  A_{c,v_j} / A_c  (kite fraction)
+    const T* sK;         // [maxE*nC]  l_e d_e / (4 A_c)
+    const T* rA;         // [nC]       1 / A_c
+    const T* b;          // [nC]       bottom topography
+    // edges
+    const int* ec0;      // [nE]       cell n_e points out of
+    const int* ec1;      // [nE]       cell n_e points into
+    const uint32_t* ep;  // [nE]       slot of e in ec0 (bits 0-7) and in ec1 (bits 8-15)
+    const T* rdc;        // [nE]       1 / d_e
+    // vertices
+    const int* vc0; const int* vc1; const int* vc2;   // [nV] cells on vertex
+    const int* ve0; const int* ve1; const int* ve2;   // [nV] edges on vertex
+    const T* vk0; const T* vk1; const T* vk2;         // [nV] A_{c,v} / A_v
+    const T* vd0; const T* vd1; const T* vd2;         // [nV] t_{e,v} d_e / A_v
+    const T* f;                                        // [nV] Coriolis parameter
+    // diagnostics
+    const double* area;  // [nC] A_c (FP64 master copy)
+    const double* bd;    // [nC] b   (FP64 master copy)
+    const double* sK64;  // [maxE*nC] l_e d_e / (4 A_c) in FP64
+};
+
+// Segment kinds of a phase launch.  One right-hand side is three launches:
+// kind 0 (vertex): q_v; kind 1 (ring, one thread per cell): K_i, the
+// per-slot potential-vorticity contributions and H_i with its stage update;
+// kind 2 (edge): U_e from the ring results, with its stage update.
+// Pointwise segments (PRED, COPY, REPLAY) may ride in any launch.
+enum SegType : int {
+    SEG_VERT = 0,       // q_v from the launch's input state
+    SEG_RING = 1,       // ring results only (halo cells of the updated edges)
+    SEG_RING_UPD = 2,   // ring results + H_i, then x_out = combine(x_old, x_in, a, D, H)
+    SEG_RING_ACC = 3,   // ring results + H_i, then acc (+)= H
+    SEG_EDGE_UPD = 4,   // U_e, then combine
+    SEG_EDGE_ACC = 5,   // U_e, then acc (+)= U
+    SEG_PRED = 6,       // out = x_old + c1 (x1 - x_old) + c2 (x2 - x_old)   (I1 prediction)
+    SEG_COPY = 7,       // dst[i - base_dst] = src[i - base_src]   (hi and lo)
+    SEG_REPLAY = 8,     // Step 5: three stage combinations from the accumulated RHS
+};
+
+// Largest cell degree the ring kernel is compiled for (variants 8 and 16).
+constexpr int MAX_DEGREE = 16;
+
+constexpr int MAXSEG = 8;
+
+// Host description of one segment.  Pointers index element arrays of the
+// right kind (cells or edges); "lo" pointers may be null when the state
+// carries no compensation word.
+struct SegDesc {
+    int type = 0;
+    int begin = 0, end = 0;   // element range [begin, end)
+    int base = 0;             // compact-array offset (acc, snapshots): compact index = i - base
+    int base2 = 0;            // second offset (COPY source)
+    int flag = 0;             // ACC: 1 = first term (store); PRED: 0 general, 1/2/3 select old/x1/x2
+    double c[4] = {0, 0, 0, 0};  // UPD: a, D; PRED: c1, c2; REPLAY: D1, D2, D3
+    void* p[10] = {};         // see kernels.cu for the meaning per type
+};
+
+struct LaunchDesc {
+    int kind = 0;             // 0 = vertex, 1 = ring, 2 = edge
+    int nseg = 0;
+    SegDesc seg[MAXSEG];
+    const void* in_h = nullptr;   // input state (hi words) of the RHS
+    const void* in_hl = nullptr;  // compensation words of the input thickness (or null)
+    const void* in_u = nullptr;
+    void* q = nullptr;            // vertex potential vorticity buffer
+    void* ring_c = nullptr;       // [maxE*nC] per-slot PV contributions (slot-major)
+    void* ring_k = nullptr;       // [nC] kinetic energy K_i
+    double g = 9.81;
+    double bytes = 0.0;           // algorithmic bytes (filled by the planner)
+};
+
+struct KernelConfig {
+    int precision;   // 0 FP32, 1 FP64
+    bool comp;       // FP32 compensated
+    int block;       // threads per block
+    int maxdeg;      // ring kernel variant: 8 or 16
+};
+
+// kernels.cu
+cudaError_t launch_phase(const LaunchDesc& d, const void* tables, const KernelConfig& kc,
+                         int* flag, cudaStream_t s);
+cudaError_t launch_scatter_state(const KernelConfig& kc, int n, const int* perm, const double* src,
+                                 void* hi, void* lo, cudaStream_t s);
+cudaError_t launch_gather_state(const KernelConfig& kc, int n, const int* perm, const void* hi,
+                                const void* lo, double* dst, cudaStream_t s);
+cudaError_t launch_diagnostics(const KernelConfig& kc, const void* tables, const void* h_hi,
+                               const void* h_lo, const void* u_hi, const void* u_lo, double g,
+                               double* partial, int nblocks, double* out2, cudaStream_t s);
+int kernel_registers(const KernelConfig& kc, int kind);
+constexpr int NKINDS = 3;
+
+}  // namespace lts

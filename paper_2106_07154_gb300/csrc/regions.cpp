@@ -1,0 +1,305 @@
+// regions.cpp -- region labelling of Eqs. (3)-(5), band ordering and the
+// band-ordered kernel tables (host side of liblts.so).
+//
+// Labelling: breadth-first edge distances from the fine set F (outwards) and
+// from the non-fine cells (into F).  With L cells per interface layer:
+//   I1 = non-F cells at distance 1..L, I2 = distance L+1..2L   (Eq. 3)
+//   F1 = F cells at inner distance 1, F2 = inner distance 2    (Eq. 4)
+// and every edge takes the finer of its two cells' regions, i.e. edges are
+// assigned from the fine to the coarse side (Eq. 5).
+// Bands (order of the device arrays):
+//   0 F deep | 1 F3 | 2 F2 | 3 F1 | 4 I1 | 5 I2 | 6 C1 | 7 C2 | 8 C rest
+// F3 is the fine layer next to F2, C1/C2 the two coarse layers next to I2
+// (the halo layers the restricted right-hand sides read).  Cells are in
+// Hilbert-curve order inside a band, edges follow their lower-indexed cell,
+// vertices their lowest cell.  Adjacent cells differ by at most one band, so
+// a right-hand side updating bands [lo, hi] reads bands [lo-1, hi+2] only.
+#include "regions.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "lts_error.h"
+
+namespace lts {
+
+namespace {
+
+// Hilbert index of a point of the unit cube (Skilling, "Programming the
+// Hilbert curve", AIP Conf. Proc. 707, 2004): axes -> transposed form, then
+// the bits are interleaved.
+uint64_t hilbert3(double x, double y, double z) {
+    const int b = 21;
+    auto q = [](double v) {
+        v = std::min(std::max(v, 0.0), 1.0);
+        return static_cast<uint32_t>(v * ((1u << 21) - 1));
+    };
+    uint32_t X[3] = {q(x), q(y), q(z)};
+    const uint32_t M = 1u << (b - 1);
+    for (uint32_t Q = M; Q > 1; Q >>= 1) {
+        uint32_t P = Q - 1;
+        for (int i = 0; i < 3; ++i) {
+            if (X[i] & Q) {
+                X[0] ^= P;
+            } else {
+                uint32_t t = (X[0] ^ X[i]) & P;
+                X[0] ^= t;
+                X[i] ^= t;
+            }
+        }
+    }
+    for (int i = 1; i < 3; ++i) X[i] ^= X[i - 1];
+    uint32_t t = 0;
+    for (uint32_t Q = M; Q > 1; Q >>= 1)
+        if (X[2] & Q) t ^= Q - 1;
+    for (int i = 0; i < 3; ++i) X[i] ^= t;
+    uint64_t key = 0;
+    for (int bit = b - 1; bit >= 0; --bit)
+        for (int i = 0; i < 3; ++i) key = (key << 1) | ((X[i] >> bit) & 1u);
+    return key;
+}
+
+std::vector<int> bfs(const HostMesh& m, const std::vector<char>& source,
+                     const std::vector<char>& allowed) {
+    const int INF = 1 << 30;
+    std::vector<int> d(m.nC, INF), frontier, next;
+    for (int i = 0; i < m.nC; ++i)
+        if (source[i]) {
+            d[i] = 0;
+            frontier.push_back(i);
+        }
+    while (!frontier.empty()) {
+        next.clear();
+        for (int i : frontier)
+            for (int j = 0; j < m.nEoC[i]; ++j) {
+                int nb = m.CoC[static_cast<size_t>(i) * m.maxE + j];
+                if (allowed[nb] && d[nb] == INF) {
+                    d[nb] = d[i] + 1;
+                    next.push_back(nb);
+                }
+            }
+        frontier.swap(next);
+    }
+    return d;
+}
+
+}  // namespace
+
+int compute_regions(const HostMesh& m, const int8_t* fine, int layers, RegionsHost& r) {
+    if (layers < 1) return set_error(LTS_EINVAL, "interface_layers must be >= 1");
+    const int nC = m.nC, nE = m.nE, nV = m.nV;
+    std::vector<char> isF(nC), notF(nC), all(nC, 1);
+    for (int i = 0; i < nC; ++i) {
+        isF[i] = fine[i] != 0;
+        notF[i] = !isF[i];
+    }
+    std::vector<int> dout = bfs(m, isF, all);   // distance from F
+    std::vector<int> din = bfs(m, notF, all);   // distance from the non-fine cells
+    r.layers = layers;
+    r.cband.assign(nC, B_CREST);
+    for (int i = 0; i < nC; ++i) {
+        int b;
+        if (isF[i]) {
+            int d = din[i];
+            b = d == 1 ? B_F1 : d == 2 ? B_F2 : d == 3 ? B_F3 : B_FDEEP;
+        } else {
+            int d = dout[i];
+            if (d <= layers) b = B_I1;
+            else if (d <= 2 * layers) b = B_I2;
+            else if (d == 2 * layers + 1) b = B_C1;
+            else if (d == 2 * layers + 2) b = B_C2;
+            else b = B_CREST;
+        }
+        r.cband[i] = static_cast<int8_t>(b);
+    }
+    r.eband.assign(nE, 0);
+    for (int e = 0; e < nE; ++e)
+        r.eband[e] = std::min(r.cband[m.CoE[2 * e]], r.cband[m.CoE[2 * e + 1]]);
+    r.vband.assign(nV, 0);
+    for (int v = 0; v < nV; ++v)
+        r.vband[v] = std::min({r.cband[m.CoV[3 * v]], r.cband[m.CoV[3 * v + 1]], r.cband[m.CoV[3 * v + 2]]});
+
+    // ---- cells: band, then Hilbert key
+    std::vector<uint64_t> key(nC);
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int i = 0; i < nC; ++i) {
+        double p[3] = {m.xc[i], m.yc[i], m.zc[i]};
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = std::min(lo[k], p[k]);
+            hi[k] = std::max(hi[k], p[k]);
+        }
+    }
+    for (int i = 0; i < nC; ++i) {
+        double p[3] = {m.xc[i], m.yc[i], m.zc[i]};
+        double s[3];
+        for (int k = 0; k < 3; ++k) s[k] = hi[k] > lo[k] ? (p[k] - lo[k]) / (hi[k] - lo[k]) : 0.0;
+        key[i] = hilbert3(s[0], s[1], s[2]);
+    }
+    r.perm_c.resize(nC);
+    std::iota(r.perm_c.begin(), r.perm_c.end(), 0);
+    std::stable_sort(r.perm_c.begin(), r.perm_c.end(), [&](int a, int b) {
+        if (r.cband[a] != r.cband[b]) return r.cband[a] < r.cband[b];
+        return key[a] < key[b];
+    });
+    r.inv_c.resize(nC);
+    for (int k = 0; k < nC; ++k) r.inv_c[r.perm_c[k]] = k;
+    // ---- edges: band, then their lower new cell index
+    r.perm_e.resize(nE);
+    std::iota(r.perm_e.begin(), r.perm_e.end(), 0);
+    auto ekey = [&](int e) {
+        int a = r.inv_c[m.CoE[2 * e]], b = r.inv_c[m.CoE[2 * e + 1]];
+        return std::make_pair(std::min(a, b), std::max(a, b));
+    };
+    std::stable_sort(r.perm_e.begin(), r.perm_e.end(), [&](int a, int b) {
+        if (r.eband[a] != r.eband[b]) return r.eband[a] < r.eband[b];
+        return ekey(a) < ekey(b);
+    });
+    r.inv_e.resize(nE);
+    for (int k = 0; k < nE; ++k) r.inv_e[r.perm_e[k]] = k;
+    // ---- vertices: band, then their lowest new cell index
+    r.perm_v.resize(nV);
+    std::iota(r.perm_v.begin(), r.perm_v.end(), 0);
+    auto vkey = [&](int v) {
+        int a = r.inv_c[m.CoV[3 * v]], b = r.inv_c[m.CoV[3 * v + 1]], c = r.inv_c[m.CoV[3 * v + 2]];
+        return std::min({a, b, c});
+    };
+    std::stable_sort(r.perm_v.begin(), r.perm_v.end(), [&](int a, int b) {
+        if (r.vband[a] != r.vband[b]) return r.vband[a] < r.vband[b];
+        return vkey(a) < vkey(b);
+    });
+    r.inv_v.resize(nV);
+    for (int k = 0; k < nV; ++k) r.inv_v[r.perm_v[k]] = k;
+    // ---- band offsets
+    for (int k = 0; k <= NBANDS; ++k) r.cb[k] = r.eb[k] = r.vb[k] = 0;
+    for (int i = 0; i < nC; ++i) r.cb[r.cband[i] + 1]++;
+    for (int e = 0; e < nE; ++e) r.eb[r.eband[e] + 1]++;
+    for (int v = 0; v < nV; ++v) r.vb[r.vband[v] + 1]++;
+    for (int k = 0; k < NBANDS; ++k) {
+        r.cb[k + 1] += r.cb[k];
+        r.eb[k + 1] += r.eb[k];
+        r.vb[k + 1] += r.vb[k];
+    }
+    // ---- connectivity in band order (host copies, for the planner's byte counts)
+    const int W = m.maxE;
+    r.cn.assign(nC, 0);
+    r.se.assign(static_cast<size_t>(W) * nC, 0);
+    r.sn.assign(static_cast<size_t>(W) * nC, 0);
+    r.sv.assign(static_cast<size_t>(W) * nC, 0);
+    for (int k = 0; k < nC; ++k) {
+        int c = r.perm_c[k];
+        int n = m.nEoC[c];
+        r.cn[k] = static_cast<uint8_t>(n);
+        for (int j = 0; j < W; ++j) {
+            int jj = j < n ? j : 0;     // padding slots repeat slot 0 (never read)
+            r.se[static_cast<size_t>(j) * nC + k] = r.inv_e[m.EoC[static_cast<size_t>(c) * W + jj]];
+            r.sn[static_cast<size_t>(j) * nC + k] = r.inv_c[m.CoC[static_cast<size_t>(c) * W + jj]];
+            r.sv[static_cast<size_t>(j) * nC + k] = r.inv_v[m.VoC[static_cast<size_t>(c) * W + jj]];
+        }
+    }
+    r.ec0.resize(nE);
+    r.ec1.resize(nE);
+    r.ep.resize(nE);
+    for (int k = 0; k < nE; ++k) {
+        int e = r.perm_e[k];
+        int c0 = m.CoE[2 * e], c1 = m.CoE[2 * e + 1];
+        r.ec0[k] = r.inv_c[c0];
+        r.ec1[k] = r.inv_c[c1];
+        int p0 = -1, p1 = -1;
+        for (int j = 0; j < m.nEoC[c0]; ++j)
+            if (m.EoC[static_cast<size_t>(c0) * W + j] == e) p0 = j;
+        for (int j = 0; j < m.nEoC[c1]; ++j)
+            if (m.EoC[static_cast<size_t>(c1) * W + j] == e) p1 = j;
+        if (p0 < 0 || p1 < 0) return set_error(LTS_EINVAL, "edge %d missing from its cells' rings", e);
+        r.ep[k] = static_cast<uint32_t>(p0) | (static_cast<uint32_t>(p1) << 8);
+    }
+    r.vc.assign(3 * static_cast<size_t>(nV), 0);
+    r.ve.assign(3 * static_cast<size_t>(nV), 0);
+    for (int k = 0; k < nV; ++k) {
+        int v = r.perm_v[k];
+        for (int q = 0; q < 3; ++q) {
+            r.vc[static_cast<size_t>(q) * nV + k] = r.inv_c[m.CoV[3 * v + q]];
+            r.ve[static_cast<size_t>(q) * nV + k] = r.inv_e[m.EoV[3 * v + q]];
+        }
+    }
+    return LTS_OK;
+}
+
+// Coefficient tables, derived in FP64 from the master geometry and rounded
+// once to T.
+template <class T>
+void coefficient_tables(const HostMesh& m, const RegionsHost& r, CoefTables<T>& o) {
+    const int nC = m.nC, nE = m.nE, nV = m.nV, W = m.maxE;
+    o.snl.assign(static_cast<size_t>(W) * nC, T(0));
+    o.sR.assign(static_cast<size_t>(W) * nC, T(0));
+    o.sK.assign(static_cast<size_t>(W) * nC, T(0));
+    o.sK64.assign(static_cast<size_t>(W) * nC, 0.0);
+    o.rA.resize(nC);
+    o.b.resize(nC);
+    o.area.resize(nC);
+    o.bd.resize(nC);
+    for (int k = 0; k < nC; ++k) {
+        int c = r.perm_c[k];
+        int n = m.nEoC[c];
+        double A = m.A[c];
+        for (int j = 0; j < n; ++j) {
+            int e = m.EoC[static_cast<size_t>(c) * W + j];
+            int v = m.VoC[static_cast<size_t>(c) * W + j];
+            double nsign = (m.CoE[2 * e] == c) ? 1.0 : -1.0;
+            double kite = 0.0;
+            for (int q = 0; q < 3; ++q)
+                if (m.CoV[3 * v + q] == c) kite = m.kite[3 * v + q];
+            size_t at = static_cast<size_t>(j) * nC + k;
+            o.snl[at] = static_cast<T>(nsign * m.dv[e]);
+            o.sR[at] = static_cast<T>(kite / A);
+            double kc = m.dv[e] * m.dc[e] / (4.0 * A);
+            o.sK[at] = static_cast<T>(kc);
+            o.sK64[at] = kc;
+        }
+        o.rA[k] = static_cast<T>(1.0 / A);
+        o.b[k] = static_cast<T>(m.b[c]);
+        o.area[k] = A;
+        o.bd[k] = m.b[c];
+    }
+    o.rdc.resize(nE);
+    for (int k = 0; k < nE; ++k) o.rdc[k] = static_cast<T>(1.0 / m.dc[r.perm_e[k]]);
+    o.vk.assign(3 * static_cast<size_t>(nV), T(0));
+    o.vd.assign(3 * static_cast<size_t>(nV), T(0));
+    o.f.resize(nV);
+    for (int k = 0; k < nV; ++k) {
+        int v = r.perm_v[k];
+        double Av = m.Av[v];
+        for (int q = 0; q < 3; ++q) {
+            int e = m.EoV[3 * v + q];
+            double t = (m.VoE[2 * e + 1] == v) ? 1.0 : -1.0;
+            o.vk[static_cast<size_t>(q) * nV + k] = static_cast<T>(m.kite[3 * v + q] / Av);
+            o.vd[static_cast<size_t>(q) * nV + k] = static_cast<T>(t * m.dc[e] / Av);
+        }
+        o.f[k] = static_cast<T>(m.f[v]);
+    }
+}
+
+template void coefficient_tables<float>(const HostMesh&, const RegionsHost&, CoefTables<float>&);
+template void coefficient_tables<double>(const HostMesh&, const RegionsHost&, CoefTables<double>&);
+
+// TRiSK weight of Eq. (weights) for e' = slot j of cell c and e = slot p,
+// with the path taken counter-clockwise from e' to e (used to validate a
+// caller's weightsOnEdge).
+double derived_weight(const HostMesh& m, int c, int j, int p) {
+    const int W = m.maxE;
+    const int n = m.nEoC[c];
+    double S = 0.0;
+    for (int q = j; q != p; q = (q + 1) % n) {
+        int v = m.VoC[static_cast<size_t>(c) * W + q];
+        for (int s = 0; s < 3; ++s)
+            if (m.CoV[3 * v + s] == c) S += m.kite[3 * v + s] / m.A[c];
+    }
+    int ep = m.EoC[static_cast<size_t>(c) * W + j];
+    int e = m.EoC[static_cast<size_t>(c) * W + p];
+    double n_ep = (m.CoE[2 * ep] == c) ? 1.0 : -1.0;
+    double n_e = (m.CoE[2 * e] == c) ? 1.0 : -1.0;
+    return n_ep * (-n_e) * (S - 0.5);
+}
+
+}  // namespace lts

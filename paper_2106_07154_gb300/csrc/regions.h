@@ -1,0 +1,44 @@
+// regions.h -- host-side mesh copy, region labels and band ordering.
+#pragma once
+#include <cstdint>
+#include <vector>
+
+#include "../../include/lts.h"
+#include "lts_internal.h"
+
+namespace lts {
+
+// Validated copy of an lts_mesh_desc (original index order, FP64 master).
+struct HostMesh {
+    int nC = 0, nE = 0, nV = 0, maxE = 0;
+    bool sphere = false;
+    double R = 0, Lx = 0, Ly = 0;
+    std::vector<double> xc, yc, zc;
+    std::vector<int> nEoC, EoC, CoC, VoC, CoE, VoE, EoV, CoV;
+    std::vector<double> A, Av, kite, dc, dv, f, b;
+};
+
+struct RegionsHost {
+    int M = 1, layers = 1;
+    std::vector<int8_t> cband, eband, vband;      // original order
+    std::vector<int> perm_c, perm_e, perm_v;      // new -> original
+    std::vector<int> inv_c, inv_e, inv_v;         // original -> new
+    int cb[NBANDS + 1], eb[NBANDS + 1], vb[NBANDS + 1];   // band offsets (new order)
+    // band-ordered connectivity (slot-major for cells)
+    std::vector<uint8_t> cn;
+    std::vector<int> se, sn, sv, ec0, ec1, vc, ve;
+    std::vector<uint32_t> ep;
+};
+
+template <class T>
+struct CoefTables {
+    std::vector<T> snl, sR, sK, rA, b, rdc, vk, vd, f;
+    std::vector<double> sK64, area, bd;
+};
+
+int compute_regions(const HostMesh& m, const int8_t* fine, int layers, RegionsHost& r);
+template <class T>
+void coefficient_tables(const HostMesh& m, const RegionsHost& r, CoefTables<T>& o);
+double derived_weight(const HostMesh& m, int c, int j, int p);
+
+}  // namespace lts

@@ -25,6 +25,8 @@ LTS_FP32 = 0
 LTS_FP64 = 1
 LTS_MODE_LTS3 = 0
 LTS_MODE_SSPRK3 = 1
+LTS_NKINDS = 3
+KIND_NAMES = ("vertex", "ring", "edge")
 
 NBANDS = 9
 BAND_NAMES = ("F_deep", "F3", "F2", "F1", "I1", "I2", "C1", "C2", "C_rest")
@@ -184,3 +186,179 @@ def lts_build_scvt(n: int, seed: int, caps, lloyd_iters: int, radius: float) -> 
         return _desc_to_dict(d)
     finally:
         lib().lts_mesh_desc_free(C.byref(d))
+
+
+# ---------------------------------------------------------------------------
+# device objects
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _dict_to_desc(mesh: dict):
+    """lts_mesh_desc pointing into contiguous copies of the dict's arrays
+    (returned alongside so they stay alive during the call)."""
+    d = lts_mesh_desc()
+    keep = []
+    for k in SCALARS:
+        setattr(d, k, mesh.get(k) or 0)
+    for name, dt, _ in MESH_ARRAYS:
+        v = mesh.get(name)
+        if v is None:
+            setattr(d, name, None)
+            continue
+        arr = _f64(v).ravel() if dt == np.float64 else _i32(v).ravel()
+        keep.append(arr)
+        ctype = C.c_double if dt == np.float64 else C.c_int32
+        setattr(d, name, arr.ctypes.data_as(C.POINTER(ctype)))
+    return d, keep
+
+
+def lts_mesh_create(mesh: dict) -> C.c_void_p:
+    d, keep = _dict_to_desc(mesh)
+    h = C.c_void_p()
+    _check(lib().lts_mesh_create(C.byref(d), C.byref(h)))
+    return h
+
+
+def lts_mesh_destroy(h):
+    if h:
+        lib().lts_mesh_destroy(h)
+
+
+def lts_regions_set(mesh_h, fine_mask, order: int, M: int, interface_layers: int = 1):
+    fm = np.ascontiguousarray(fine_mask, dtype=np.int8)
+    h = C.c_void_p()
+    _check(lib().lts_regions_set(mesh_h, fm.ctypes.data, order, M, interface_layers, C.byref(h)))
+    return h
+
+
+def lts_regions_destroy(h):
+    if h:
+        lib().lts_regions_destroy(h)
+
+
+def lts_regions_labels(reg_h, nCells: int, nEdges: int):
+    cl = np.zeros(nCells, np.int8)
+    el = np.zeros(nEdges, np.int8)
+    _check(lib().lts_regions_labels(reg_h, cl.ctypes.data, el.ctypes.data))
+    return cl, el
+
+
+def lts_regions_counts(reg_h):
+    c = np.zeros(NBANDS, np.int64)
+    e = np.zeros(NBANDS, np.int64)
+    v = np.zeros(NBANDS, np.int64)
+    _check(lib().lts_regions_counts(reg_h, c.ctypes.data, e.ctypes.data, v.ctypes.data))
+    return c, e, v
+
+
+def lts_regions_permutation(reg_h, nCells: int, nEdges: int, nVertices: int):
+    pc = np.zeros(nCells, np.int32)
+    pe = np.zeros(nEdges, np.int32)
+    pv = np.zeros(nVertices, np.int32)
+    _check(lib().lts_regions_permutation(reg_h, pc.ctypes.data, pe.ctypes.data, pv.ctypes.data))
+    return pc, pe, pv
+
+
+def lts_state_create(mesh_h, reg_h, h0, u0, g: float, dt: float, precision: int = LTS_FP32,
+                     mode: int = LTS_MODE_LTS3, compensated: bool = True, use_graph: bool = True,
+                     block_size: int = 0, profile: bool = False, stream: int | None = None):
+    p = lts_params(g, dt, precision, mode, int(compensated), int(use_graph), block_size,
+                   int(profile), stream)
+    h = C.c_void_p()
+    _check(lib().lts_state_create(mesh_h, reg_h, _f64(h0).ctypes.data, _f64(u0).ctypes.data,
+                                  C.byref(p), C.byref(h)))
+    return h
+
+
+def lts_state_destroy(h):
+    if h:
+        lib().lts_state_destroy(h)
+
+
+def lts_step(state_h, n_coarse: int):
+    _check(lib().lts_step(state_h, int(n_coarse)))
+
+
+def lts_read(state_h, nCells: int, nEdges: int, h_out=None, u_out=None):
+    """Returns (h, u, diag dict); writes into h_out/u_out when given (e.g. pinned buffers)."""
+    h = np.zeros(nCells) if h_out is None else h_out
+    u = np.zeros(nEdges) if u_out is None else u_out
+    d = lts_diag()
+    rc = lib().lts_read(state_h, h.ctypes.data, u.ctypes.data, C.byref(d))
+    _check(rc)
+    return h, u, {"mass": d.mass, "energy": d.energy, "time": d.time, "steps": d.steps}
+
+
+def lts_write(state_h, h, u, time: float = 0.0, steps: int = 0):
+    _check(lib().lts_write(state_h, _f64(h).ctypes.data, _f64(u).ctypes.data, float(time),
+                           int(steps)))
+
+
+def lts_step_stats(state_h):
+    n = C.c_int32()
+    b = np.zeros(LTS_NKINDS)
+    ms = np.zeros(LTS_NKINDS)
+    k = np.zeros(LTS_NKINDS, np.int32)
+    _check(lib().lts_step_stats(state_h, C.byref(n), b.ctypes.data, ms.ctypes.data, k.ctypes.data))
+    return {"launches": int(n.value), "bytes": b.tolist(), "ms": ms.tolist(),
+            "launches_per_kind": k.tolist()}
+
+
+class Model:
+    """Mesh + regions + state, with the handles released on close()."""
+
+    def __init__(self, mesh: dict, fine_mask, M: int, h0, u0, dt: float, g: float = 9.81,
+                 precision: int = LTS_FP32, mode: int = LTS_MODE_LTS3, compensated: bool = True,
+                 use_graph: bool = True, block_size: int = 0, profile: bool = False,
+                 interface_layers: int = 1, stream: int | None = None):
+        self.nC = int(mesh["nCells"])
+        self.nE = int(mesh["nEdges"])
+        self.nV = int(mesh["nVertices"])
+        self.mesh_h = self.reg_h = self.state_h = None
+        self.mesh_h = lts_mesh_create(mesh)
+        self.reg_h = lts_regions_set(self.mesh_h, fine_mask, 3, M, interface_layers)
+        self.state_h = lts_state_create(self.mesh_h, self.reg_h, h0, u0, g, dt, precision, mode,
+                                        compensated, use_graph, block_size, profile, stream)
+
+    def step(self, n: int):
+        lts_step(self.state_h, n)
+
+    def read(self, h_out=None, u_out=None):
+        return lts_read(self.state_h, self.nC, self.nE, h_out, u_out)
+
+    def write(self, h, u, time=0.0, steps=0):
+        lts_write(self.state_h, h, u, time, steps)
+
+    def labels(self):
+        return lts_regions_labels(self.reg_h, self.nC, self.nE)
+
+    def counts(self):
+        return lts_regions_counts(self.reg_h)
+
+    def stats(self):
+        return lts_step_stats(self.state_h)
+
+    def close(self):
+        lts_state_destroy(self.state_h)
+        lts_regions_destroy(self.reg_h)
+        lts_mesh_destroy(self.mesh_h)
+        self.state_h = self.reg_h = self.mesh_h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,192 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (relative max-norm, ||x_gpu - x_oracle||_inf / ||x_oracle||_inf):
+  FP64 mode:            1e-12 on h and u after 100 coarse steps
+  FP32 (compensated):   2e-5 on h, 1e-4 on u
+M = 1 identity (LTS3 == SSPRK3) is checked bit for bit on the GPU.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2106_07154_gb300 import lts
+from paper_2106_07154_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32_H = 2e-5
+TOL32_U = 1e-4
+EPS64 = 2.0 ** -53
+
+
+def u_floor64(w, nsteps):
+    """Conditioning floor for u in FP64: one unit roundoff of the thickness
+    (eps * H) seen by the gradient term g (h1 - h0)/d_e accelerates u by
+    g eps H / d_e; over the simulated time T two correct FP64 evaluation
+    orders can therefore differ by about g eps H T / d_min in u.  The hex
+    bump (u ~ 0.03 m/s on 1000 m) sits below 1e-12 relative of that."""
+    T = nsteps * w.dt
+    return 9.81 * EPS64 * float(w.h0.max()) * T / float(w.mesh["dcEdge"].min())
+
+
+def rel(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def run_gpu(w, n, precision, M=None, mode=lts.LTS_MODE_LTS3, dt=None, use_graph=True,
+            compensated=True, fine=None, layers=1, block_size=0, profile=False):
+    with lts.Model(w.mesh, w.fine_mask if fine is None else fine, M or w.M, w.h0, w.u0,
+                   dt or w.dt, w.g, precision=precision, mode=mode, compensated=compensated,
+                   use_graph=use_graph, interface_layers=layers, block_size=block_size,
+                   profile=profile) as m:
+        m.step(n)
+        h, u, d = m.read()
+    return h, u, d
+
+
+def run_oracle(w, n, M=None, fine=None, dt=None):
+    o = oracle.Oracle(w.mesh)
+    cl, el = o.regions(w.fine_mask if fine is None else fine)
+    return o.lts3(w.h0, w.u0, cl, el, M or w.M, dt or w.dt, n, g=w.g)
+
+
+@pytest.fixture(scope="module")
+def hexw():
+    return W.workload("hex_1024")
+
+
+@pytest.fixture(scope="module")
+def sphw():
+    return W.workload("scvt_2562")
+
+
+@pytest.fixture(scope="module")
+def hex_ref(hexw):
+    return run_oracle(hexw, 100)
+
+
+@pytest.fixture(scope="module")
+def sph_ref(sphw):
+    return run_oracle(sphw, 100)
+
+
+def test_fp64_hex_100_steps(hexw, hex_ref):
+    h, u, _ = run_gpu(hexw, 100, lts.LTS_FP64)
+    assert rel(h, hex_ref[0]) <= TOL64
+    du = float(np.max(np.abs(u - hex_ref[1])))
+    assert du <= max(TOL64 * float(np.max(np.abs(hex_ref[1]))), u_floor64(hexw, 100))
+
+
+def test_fp64_sphere_100_steps(sphw, sph_ref):
+    h, u, _ = run_gpu(sphw, 100, lts.LTS_FP64)
+    assert rel(h, sph_ref[0]) <= TOL64
+    assert rel(u, sph_ref[1]) <= TOL64
+
+
+def test_fp32_hex_100_steps(hexw, hex_ref):
+    h, u, _ = run_gpu(hexw, 100, lts.LTS_FP32)
+    # the hex case is a 1 m bump on 1000 m: compare the perturbation too
+    assert rel(h, hex_ref[0]) <= TOL32_H
+    assert rel(u, hex_ref[1]) <= TOL32_U
+
+
+def test_fp32_sphere_100_steps(sphw, sph_ref):
+    h, u, _ = run_gpu(sphw, 100, lts.LTS_FP32)
+    assert rel(h, sph_ref[0]) <= TOL32_H
+    assert rel(u, sph_ref[1]) <= TOL32_U
+
+
+@pytest.mark.parametrize("precision", [lts.LTS_FP64, lts.LTS_FP32])
+def test_m1_equals_ssprk3_bitwise(sphw, precision):
+    dt = sphw.dt / sphw.M      # stable on the refined cap
+    a = run_gpu(sphw, 10, precision, M=1, dt=dt)
+    b = run_gpu(sphw, 10, precision, M=1, mode=lts.LTS_MODE_SSPRK3, dt=dt)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_fp64_ssprk3_matches_oracle(sphw):
+    h, u, _ = run_gpu(sphw, 30, lts.LTS_FP64, mode=lts.LTS_MODE_SSPRK3, dt=sphw.dt / 4)
+    o = oracle.Oracle(sphw.mesh)
+    rh, ru = o.ssprk3(sphw.h0, sphw.u0, sphw.dt / 4, 30)
+    assert rel(h, rh) <= TOL64 and rel(u, ru) <= TOL64
+
+
+def test_mass_conservation_gpu(sphw):
+    o = oracle.Oracle(sphw.mesh)
+    m0 = o.mass(sphw.h0)
+    _, _, d64 = run_gpu(sphw, 50, lts.LTS_FP64)
+    assert abs(d64["mass"] - m0) <= 1e-13 * m0
+    _, _, d32 = run_gpu(sphw, 50, lts.LTS_FP32)
+    eps32 = 2.0 ** -24
+    assert abs(d32["mass"] - m0) <= 4 * eps32 * math.sqrt(50) * m0
+
+
+def test_diagnostics_match_oracle(sphw):
+    h, u, d = run_gpu(sphw, 5, lts.LTS_FP64)
+    o = oracle.Oracle(sphw.mesh)
+    assert abs(d["mass"] - o.mass(h)) <= 1e-14 * abs(o.mass(h))
+    assert abs(d["energy"] - o.energy(h, u)) <= 1e-12 * abs(o.energy(h, u))
+    assert d["steps"] == 5 and abs(d["time"] - 5 * sphw.dt) < 1e-9
+
+
+def test_graph_and_direct_launches_identical(sphw):
+    a = run_gpu(sphw, 7, lts.LTS_FP32, use_graph=True)
+    b = run_gpu(sphw, 7, lts.LTS_FP32, use_graph=False)
+    c = run_gpu(sphw, 7, lts.LTS_FP32, profile=True)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    assert np.array_equal(a[0], c[0]) and np.array_equal(a[1], c[1])
+
+
+def test_block_size_does_not_change_results(sphw):
+    a = run_gpu(sphw, 5, lts.LTS_FP64, block_size=256)
+    b = run_gpu(sphw, 5, lts.LTS_FP64, block_size=96)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_no_fine_cells_is_coarse_ssprk3(sphw):
+    fine = np.zeros(sphw.nCells, np.int8)
+    dt = sphw.dt / sphw.M      # stable on the refined cap
+    h, u, _ = run_gpu(sphw, 10, lts.LTS_FP64, fine=fine, dt=dt)
+    rh, ru = oracle.Oracle(sphw.mesh).ssprk3(sphw.h0, sphw.u0, dt, 10)
+    assert rel(h, rh) <= TOL64 and rel(u, ru) <= TOL64
+
+
+def test_all_fine_cells_is_fine_ssprk3(sphw):
+    fine = np.ones(sphw.nCells, np.int8)
+    h, u, _ = run_gpu(sphw, 5, lts.LTS_FP64, fine=fine, M=3)
+    rh, ru = oracle.Oracle(sphw.mesh).ssprk3(sphw.h0, sphw.u0, sphw.dt / 3, 15)
+    assert rel(h, rh) <= TOL64 and rel(u, ru) <= TOL64
+
+
+@pytest.mark.parametrize("M", [2, 3, 5])
+def test_fp64_various_m(sphw, M):
+    n = 8
+    h, u, _ = run_gpu(sphw, n, lts.LTS_FP64, M=M)
+    rh, ru = run_oracle(sphw, n, M=M)
+    assert rel(h, rh) <= TOL64 and rel(u, ru) <= TOL64
+
+
+def test_checkpoint_resume_bitwise(sphw):
+    full = run_gpu(sphw, 12, lts.LTS_FP64)
+    with lts.Model(sphw.mesh, sphw.fine_mask, sphw.M, sphw.h0, sphw.u0, sphw.dt,
+                   precision=lts.LTS_FP64) as m:
+        m.step(5)
+        h, u, d = m.read()
+    with lts.Model(sphw.mesh, sphw.fine_mask, sphw.M, h, u, sphw.dt, precision=lts.LTS_FP64) as m:
+        m.step(7)
+        h2, u2, _ = m.read()
+    assert np.array_equal(h2, full[0]) and np.array_equal(u2, full[1])
+
+
+def test_nonfinite_is_reported(sphw):
+    h0 = sphw.h0.copy()
+    h0[10] = -5.0
+    with lts.Model(sphw.mesh, sphw.fine_mask, sphw.M, h0, sphw.u0, sphw.dt,
+                   precision=lts.LTS_FP32) as m:
+        m.step(1)
+        with pytest.raises(lts.LtsError) as ei:
+            m.read()
+        assert ei.value.code == lts.LTS_ENONFINITE
