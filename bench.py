@@ -1,0 +1,396 @@
+"""Benchmark of the LTS3 coarse step (Algorithm 2.2) on one or more GB300s.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lts|reference]
+
+A "step" is one LTS3 coarse step of the whole hot path (Steps 1-5 with M fine
+substeps) over the synthetic 655,362-cell spherical SCVT with an 8:1 refined
+cap (M = 8), FP32 state with compensation words.  The JSON line reports
+coarse-step cell-updates/s (nCells x coarse steps / time), timed with CUDA
+events on the state's stream over exactly K steps after W warm-up steps,
+max over ranks.  Under torchrun every rank advances its own replica (the path
+has no exchange step on one GPU), so the aggregate is weak scaling.
+
+--impl reference times the FP64 CPU oracle (the reference arm of this
+build) on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "LTS coarse-step cell-updates/s"
+UNIT = "cell-updates/s"
+PEAKS = ROOT / "MEASURED_PEAKS.json"
+HBM_FALLBACK_GBS = 6800.0
+TRAFFIC_SUMMARY = ROOT / "profiles" / "ring_kernel_scvt655362_fp32c.md"
+KERNEL_SRC = ROOT / "paper_2106_07154_gb300" / "csrc" / "kernels.cu"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="lts", choices=["lts", "reference"])
+    ap.add_argument("--workload", default="scvt_655362")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--e2e-steps", type=int, default=100)
+    ap.add_argument("--no-extras", action="store_true", help="skip e2e/roofline/baselines")
+    ap.add_argument("--no-graph", action="store_true", help="direct launches instead of the graph")
+    ap.add_argument("--no-pdl", action="store_true", help="no programmatic dependent launch")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# --------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------- helpers
+
+def kernel_hash() -> str:
+    return hashlib.sha256(KERNEL_SRC.read_bytes()).hexdigest()[:16]
+
+
+def hbm_peak():
+    try:
+        p = json.loads(PEAKS.read_text())
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def dram_traffic_per_launch():
+    """DRAM bytes per launch of the ring kernel from the committed ncu
+    summary, or None when the kernel source changed since the capture."""
+    try:
+        text = TRAFFIC_SUMMARY.read_text()
+        m = re.search(r"```json\s*(\{.*?\})\s*```", text, re.S)
+        data = json.loads(m.group(1))
+        if data.get("kernels_cu_sha256_16") != kernel_hash():
+            return None
+        return float(data["ring_dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def oracle_sample(w, nsteps_cap=3, budget_s=20.0):
+    """Times the FP64 oracle's LTS3 coarse step on the full workload; returns
+    (cell-updates/s, steps, seconds, threads, result)."""
+    import oracle
+
+    o = oracle.Oracle(w.mesh)
+    cl, el = o.regions(w.fine_mask)
+    h, u = w.h0, w.u0
+    steps, t_total = 0, 0.0
+    while steps < nsteps_cap and t_total < budget_s:
+        t0 = time.perf_counter()
+        h, u = o.lts3(h, u, cl, el, w.M, w.dt, 1, g=w.g)
+        t_total += time.perf_counter() - t0
+        steps += 1
+    return w.nCells * steps / t_total, steps, t_total, oracle.num_threads(), (h, u)
+
+
+# --------------------------------------------------------------------- arms
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2106_07154_gb300 import workloads as W
+
+    w = W.workload(args.workload)
+    import oracle
+
+    o = oracle.Oracle(w.mesh)
+    cl, el = o.regions(w.fine_mask)
+    h, u = w.h0, w.u0
+    # one oracle coarse step takes seconds; warm-up and timed steps are capped
+    # so the whole arm ends within a few minutes
+    warm = min(args.warmup, 1)
+    for _ in range(warm):
+        h, u = o.lts3(h, u, cl, el, w.M, w.dt, 1, g=w.g)
+    t0 = time.perf_counter()
+    steps = 0
+    while steps < args.steps:
+        h, u = o.lts3(h, u, cl, el, w.M, w.dt, 1, g=w.g)
+        steps += 1
+        if time.perf_counter() - t0 > 90.0:
+            break
+    el_s = time.perf_counter() - t0
+    value = w.nCells * steps / el_s
+    cores = oracle.num_threads()
+    sample = (f"{steps} LTS3 coarse steps (M={w.M}) of the full {w.nCells}-cell mesh by the FP64 "
+              f"C oracle (full-mesh right-hand sides), {warm} warm-up; capped at 90 s")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": steps, "warmup": warm, "ms_per_step": 1e3 * el_s / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": workload_config(w, "fp64-oracle"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample, "cpu": cpu_model()},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(w, precision):
+    return {"workload": f"{w.name}: spherical SCVT, {w.nCells} cells, 200 Lloyd iterations, "
+                        f"{int(w.info.get('ratio', 0))}:1 cap, LTS3 M={w.M}",
+            "nCells": w.nCells, "nEdges": int(w.mesh["nEdges"]), "M": w.M,
+            "dt_coarse_s": w.dt, "precision": precision,
+            "l2": "inputs larger than L2 (each coarse step streams the whole mesh)",
+            "parallelism": "replicas"}
+
+
+def run_lts(args):
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU for --impl lts")
+    torch.cuda.set_device(local)
+    from paper_2106_07154_gb300 import lts
+    from paper_2106_07154_gb300 import workloads as W
+
+    # rank 0 builds (and caches) the mesh first, the others load it
+    if world > 1 and rank != 0:
+        torch.distributed.barrier()
+    w = W.workload(args.workload)
+    if world > 1 and rank == 0:
+        torch.distributed.barrier()
+    prec = lts.LTS_FP32 if args.precision == "fp32" else lts.LTS_FP64
+    stream = torch.cuda.Stream()
+    model = lts.Model(w.mesh, w.fine_mask, w.M, w.h0, w.u0, w.dt, w.g, precision=prec,
+                      compensated=True, use_graph=not args.no_graph, stream=stream.cuda_stream,
+                      pdl=not args.no_pdl)
+    stats = model.stats()
+    model.step(args.warmup)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    start.record(stream)
+    model.step(args.steps)
+    stop.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = start.elapsed_time(stop)
+    if world > 1:
+        torch.distributed.barrier()
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    h_gpu, u_gpu, diag = model.read()
+    value = world * w.nCells * args.steps / (ms * 1e-3)
+    launch_cfg = ("direct launches" if args.no_graph else "one CUDA graph per coarse step") + \
+        ("" if args.no_pdl else ", programmatic dependent launch")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if prec == lts.LTS_FP32 else "f64", "data": "synthetic",
+            "config": workload_config(w, args.precision + ("+compensation" if prec == 0 else "")),
+            "gpu_launches": stats["launches"] * args.steps, "clocks": clk, "launch": launch_cfg,
+            "sim_seconds_per_wall_second": w.dt * args.steps / (ms * 1e-3)}
+    if not args.no_extras and rank == 0:
+        line.update(extras(args, w, model, stats, stream, h_gpu, u_gpu, diag))
+    model.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def extras(args, w, model, stats, stream, h_gpu, u_gpu, diag):
+    import torch
+    from paper_2106_07154_gb300 import lts
+
+    out = {}
+    prec = lts.LTS_FP32 if args.precision == "fp32" else lts.LTS_FP64
+    nC, nE = w.nCells, int(w.mesh["nEdges"])
+    # ---- end to end through the C ABI with pinned host buffers
+    hb = torch.empty(nC, dtype=torch.float64, pin_memory=True).numpy()
+    ub = torch.empty(nE, dtype=torch.float64, pin_memory=True).numpy()
+    hb[:] = w.h0
+    ub[:] = w.u0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        model.write(hb, ub)
+        model.step(1)
+        model.read(hb, ub)
+    e2e_s = time.perf_counter() - t0
+    out["e2e"] = {"value": nC * args.e2e_steps / e2e_s, "unit": UNIT,
+                  "h2d_bytes_per_step": 8 * (nC + nE),
+                  "d2h_bytes_per_step": 8 * (nC + nE) + 16 + 4,
+                  "steps": args.e2e_steps,
+                  "note": "lts_write (H2D of h,u) + lts_step(1) + lts_read (D2H of h,u, FP64 "
+                          "mass/energy), pinned host buffers, wall clock"}
+    # ---- per-kernel timing: the same coarse-step graph with an event-record
+    #      node before and after every kernel node, on the state's stream
+    prof = lts.Model(w.mesh, w.fine_mask, w.M, w.h0, w.u0, w.dt, w.g, precision=prec,
+                     compensated=True, profile=2, stream=stream.cuda_stream)
+    nprof = 20
+    prof.step(2)
+    ms_sum = np.zeros(lts.LTS_NKINDS)
+    for _ in range(nprof):
+        prof.step(1)
+        ms_sum += np.array(prof.stats()["ms"])
+    prof.close()
+    ms_kind = ms_sum / nprof
+    bytes_kind = np.array(stats["bytes"])
+    launches_kind = np.array(stats["launches_per_kind"])
+    gbs = bytes_kind / (ms_kind * 1e-3) / 1e9
+    dom = int(np.argmax(ms_kind))
+    peak, peak_src = hbm_peak()
+    traffic = dram_traffic_per_launch() if dom == 1 else None
+    out["roofline"] = {
+        "bound": "hbm", "kernel": lts.KIND_NAMES[dom],
+        "achieved": float(gbs[dom]), "peak": peak, "unit": "GB/s", "frac": float(gbs[dom] / peak),
+        "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback 6.8 TB/s",
+        "traffic": traffic,
+        "algorithmic_bytes_per_launch": float(bytes_kind[dom] / launches_kind[dom]),
+        "avg_launch_ms": float(ms_kind[dom] / launches_kind[dom]),
+        "per_kind": {lts.KIND_NAMES[k]: {"ms_per_step": float(ms_kind[k]),
+                                          "bytes_per_step": float(bytes_kind[k]),
+                                          "launches_per_step": int(launches_kind[k]),
+                                          "GB_per_s": float(gbs[k])} for k in range(lts.LTS_NKINDS)},
+    }
+    # ---- the GPU's own FP64 global SSP-RK3 at the fine step (same simulated time)
+    ref = lts.Model(w.mesh, w.fine_mask, w.M, w.h0, w.u0, w.dt / w.M, w.g, precision=lts.LTS_FP64,
+                    mode=lts.LTS_MODE_SSPRK3, stream=stream.cuda_stream)
+    ref.step(w.M)
+    torch.cuda.synchronize()
+    ncmp = max(2, min(50, args.steps // 20))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ref.step(ncmp * w.M)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ref_ms = e0.elapsed_time(e1) / ncmp
+    ref.close()
+    out["fp64_ssprk3_fine_dt"] = {"ms_per_coarse_interval": ref_ms,
+                                  "sim_seconds_per_wall_second": w.dt / (ref_ms * 1e-3),
+                                  "note": f"FP64 SSPRK3 on the whole mesh at dt/M = {w.dt / w.M:.3f} s"}
+    # ---- CPU baseline (oracle on the host cores) and the error of this run's
+    #      first coarse step against it
+    cells_per_s, n_or, t_or, cores, (rh, ru) = oracle_sample(w, nsteps_cap=1)
+    one = lts.Model(w.mesh, w.fine_mask, w.M, w.h0, w.u0, w.dt, w.g, precision=prec,
+                    compensated=True, stream=stream.cuda_stream)
+    one.step(1)
+    h1, u1, _ = one.read()
+    one.close()
+    out["cpu_baseline"] = {"value": cells_per_s, "unit": UNIT, "cores": cores, "kind": "oracle",
+                           "sample": f"{n_or} LTS3 coarse step(s) of the full mesh by the FP64 C "
+                                     f"oracle ({t_or:.1f} s)", "cpu": cpu_model()}
+    out["error_vs_oracle_1step"] = {
+        "h_rel_maxnorm": float(np.max(np.abs(h1 - rh)) / np.max(np.abs(rh))),
+        "u_rel_maxnorm": float(np.max(np.abs(u1 - ru)) / np.max(np.abs(ru)))}
+    out["mass"] = diag["mass"]
+    return out
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_lts(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

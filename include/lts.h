@@ -177,7 +177,11 @@ typedef struct lts_params {
                                for FP64                                                */
     int32_t use_graph;      /* 1: capture one coarse step as a CUDA graph (default)    */
     int32_t block_size;     /* threads per block, 0 = library default                 */
-    int32_t profile;        /* 1: time every launch with CUDA events (no graph)        */
+    int32_t profile;        /* 1: CUDA events around every direct launch (no graph);
+                               2: event-record nodes around every kernel node of the
+                               graph (per-kernel times of the last lts_step call)      */
+    int32_t pdl;            /* 1: programmatic dependent launch between consecutive
+                               kernels (each launch overlaps its predecessor's tail)   */
     void* stream;           /* cudaStream_t to enqueue on; NULL = a library stream     */
 } lts_params;
 

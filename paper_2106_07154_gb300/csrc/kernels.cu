@@ -116,6 +116,16 @@ __device__ __forceinline__ bool finite_pos(float x) { return x > 0.0f && x < 3.0
 __device__ __forceinline__ bool finite_val(double x) { return fabs(x) < 1e300; }
 __device__ __forceinline__ bool finite_val(float x) { return fabsf(x) < 3.0e38f; }
 
+// Programmatic dependent launch: let the next kernel of the stream start
+// launching now, and wait until the previous kernel's results are visible.
+// Both are no-ops without PDL.  Every kernel loads its static mesh tables
+// before griddep_wait, so those loads overlap the previous kernel's tail; no
+// state is read or written before the wait.
+__device__ __forceinline__ void griddep_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // ------------------------------------------------------------- kind 0: vertex
 
 // q_v = (zeta_v + f_v) / h_v with zeta_v = sum t_{e,v} (d_e/A_v) u_e and
@@ -123,15 +133,21 @@ __device__ __forceinline__ bool finite_val(float x) { return fabsf(x) < 3.0e38f;
 template <class T>
 __device__ __forceinline__ void vertex_pv(const DevArgs<T>& a, int v) {
     const Tables<T>& t = a.t;
-    T zeta = t.vd0[v] * a.in_u[t.ve0[v]] + t.vd1[v] * a.in_u[t.ve1[v]] + t.vd2[v] * a.in_u[t.ve2[v]];
-    T hv = t.vk0[v] * a.in_h[t.vc0[v]] + t.vk1[v] * a.in_h[t.vc1[v]] + t.vk2[v] * a.in_h[t.vc2[v]];
-    a.q[v] = (zeta + t.f[v]) / hv;
+    const int e0 = t.ve0[v], e1 = t.ve1[v], e2 = t.ve2[v];
+    const int c0 = t.vc0[v], c1 = t.vc1[v], c2 = t.vc2[v];
+    const T d0 = t.vd0[v], d1 = t.vd1[v], d2 = t.vd2[v];
+    const T k0 = t.vk0[v], k1 = t.vk1[v], k2 = t.vk2[v];
+    const T f = t.f[v];
+    griddep_wait();
+    T zeta = d0 * a.in_u[e0] + d1 * a.in_u[e1] + d2 * a.in_u[e2];
+    T hv = k0 * a.in_h[c0] + k1 * a.in_h[c1] + k2 * a.in_h[c2];
+    a.q[v] = (zeta + f) / hv;
 }
 
 // --------------------------------------------------------------- kind 1: ring
 //
-// For cell c with slots j = 0..n-1 (edge e_j, neighbour across it, vertex
-// v_j between e_j and e_{j+1}, kite fraction R_j = A_{c,v_j}/A_c):
+// One thread per cell c, slots j = 0..n-1 (edge e_j, neighbour across it,
+// vertex v_j between e_j and e_{j+1}, kite fraction R_j = A_{c,v_j}/A_c):
 //   F_j  = (h_c + h_nb)/2 u_j,   G_j = n_{e_j,c} l_j F_j,   qt_j = (q_{v_{j-1}} + q_{v_j})/2
 //   K_c  = sum_j l_j d_j u_j^2 / (4 A_c),      H_c = -(1/A_c) sum_j G_j
 // and for every slot p the share of the PV flux of edge e_p,
@@ -139,55 +155,83 @@ __device__ __forceinline__ void vertex_pv(const DevArgs<T>& a, int v) {
 // where S_{j->p} = sum of R_m over the vertices met going counter-clockwise
 // from e_j to e_p (so w_{e_p,e_j} = n_{e_j,c} (-n_{e_p,c}) (S_{j->p} - 1/2),
 // t_{e_p,v_{p-1}} = -n_{e_p,c} on a counter-clockwise ring).  With prefix sums
-// P_m = R_0 + ... + R_{m-1}, S_{j->p} = P_p - P_j + [j > p] P_n, so
+// P_p = R_0 + ... + R_{p-1}, S_{j->p} = P_p - P_j + [j > p] P_n, so
 //   C_p = qt_p [(P_p - 1/2) A_p + P_n Asuf_p - A'_p] + [(P_p - 1/2) B_p + P_n Bsuf_p - B'_p]
 // with A_p = sum_{j!=p} G_j, A'_p = sum_{j!=p} P_j G_j, Asuf_p = sum_{j>p} G_j
 // and B the same with G_j qt_j: the weight sum regrouped into O(n) work.
+// The first UNCOND slots are loaded without waiting for the cell's degree
+// (padding slots are valid copies of slot 0), so the table loads and the
+// state gathers of a thread are issued as two independent waves.
+constexpr int UNCOND = 6;
+
 template <class T, bool COMP, int MAXR>
 __device__ __forceinline__ T ring_pass(const DevArgs<T>& a, int c) {
     const Tables<T>& t = a.t;
     const int N = t.nC;
     const int n = t.cn[c];
+    // static ring tables of the first UNCOND slots, before the wait
+    int E0[UNCOND], NB0[UNCOND], V0[UNCOND];
+    T SNL0[UNCOND], R0[UNCOND], SK0[UNCOND];
+#pragma unroll
+    for (int j = 0; j < UNCOND; ++j) {
+        E0[j] = __ldg(t.se + j * N + c);
+        NB0[j] = __ldg(t.sn + j * N + c);
+        V0[j] = __ldg(t.sv + j * N + c);
+        SNL0[j] = __ldg(t.snl + j * N + c);
+        R0[j] = __ldg(t.sR + j * N + c);
+        SK0[j] = __ldg(t.sK + j * N + c);
+    }
+    griddep_wait();
     const T hc = a.in_h[c];
-    T G[MAXR], qt[MAXR], P[MAXR];
-    T qprev = a.q[__ldg(t.sv + (n - 1) * N + c)];   // q at v_{n-1} (closes the ring)
+    T G[MAXR], qv[MAXR], R[MAXR];
     T Kc = T(0), s = T(0), comp = T(0);
-    T Pacc = T(0);
 #pragma unroll
     for (int j = 0; j < MAXR; ++j) {
-        if (j < n) {
-            const int e = __ldg(t.se + j * N + c);
-            const int nb = __ldg(t.sn + j * N + c);
-            const int v = __ldg(t.sv + j * N + c);
-            const T snl = __ldg(t.snl + j * N + c);
-            const T R = __ldg(t.sR + j * N + c);
-            const T sK = __ldg(t.sK + j * N + c);
+        if (j < UNCOND || j < n) {
+            const int e = j < UNCOND ? E0[j % UNCOND] : __ldg(t.se + j * N + c);
+            const int nb = j < UNCOND ? NB0[j % UNCOND] : __ldg(t.sn + j * N + c);
+            const int v = j < UNCOND ? V0[j % UNCOND] : __ldg(t.sv + j * N + c);
+            const T snl = j < UNCOND ? SNL0[j % UNCOND] : __ldg(t.snl + j * N + c);
+            const T Rj = j < UNCOND ? R0[j % UNCOND] : __ldg(t.sR + j * N + c);
+            const T sK = j < UNCOND ? SK0[j % UNCOND] : __ldg(t.sK + j * N + c);
             const T uj = a.in_u[e];
             const T hnb = a.in_h[nb];
-            const T qj = a.q[v];
+            qv[j] = a.q[v];
+            const bool in = j < n;
             const T F = T(0.5) * (hc + hnb) * uj;
-            const T g = mul_rn(snl, F);
+            const T g = in ? mul_rn(snl, F) : T(0);
             G[j] = g;
-            qt[j] = T(0.5) * (qprev + qj);
-            qprev = qj;
-            P[j] = Pacc;
-            Pacc += R;
-            Kc += sK * uj * uj;
-            if (COMP) {
-                T ss, ee;
-                two_sum(s, g, ss, ee);
-                s = ss;
-                comp += ee;
-            } else {
-                s += g;
+            R[j] = in ? Rj : T(0);
+            if (in) {
+                Kc += sK * uj * uj;
+                if (COMP) {
+                    T ss, ee;
+                    two_sum(s, g, ss, ee);
+                    s = ss;
+                    comp += ee;
+                } else {
+                    s += g;
+                }
             }
+        } else {
+            G[j] = T(0);
+            R[j] = T(0);
+            qv[j] = T(0);
         }
     }
-    const T Pn = Pacc;
-    T Atot = T(0), Btot = T(0), A1 = T(0), B1 = T(0);
+    // q at v_{n-1} closes the ring for slot 0
+    T qlast = qv[0];
+#pragma unroll
+    for (int j = 1; j < MAXR; ++j)
+        if (j == n - 1) qlast = qv[j];
+    T qt[MAXR], P[MAXR];
+    T Pacc = T(0), Atot = T(0), Btot = T(0), A1 = T(0), B1 = T(0);
 #pragma unroll
     for (int j = 0; j < MAXR; ++j) {
+        qt[j] = T(0.5) * ((j == 0 ? qlast : qv[j - 1]) + qv[j]);
+        P[j] = Pacc;
         if (j < n) {
+            Pacc += R[j];
             const T gq = G[j] * qt[j];
             Atot += G[j];
             Btot += gq;
@@ -195,17 +239,15 @@ __device__ __forceinline__ T ring_pass(const DevArgs<T>& a, int c) {
             B1 += P[j] * gq;
         }
     }
+    const T Pn = Pacc;
     T Asuf = T(0), Bsuf = T(0);
 #pragma unroll
     for (int p = MAXR - 1; p >= 0; --p) {
         if (p < n) {
             const T gq = G[p] * qt[p];
-            const T Ap = Atot - G[p];
-            const T Bp = Btot - gq;
-            const T A1p = A1 - P[p] * G[p];
-            const T B1p = B1 - P[p] * gq;
             const T w = P[p] - T(0.5);
-            const T C = qt[p] * (w * Ap + Pn * Asuf - A1p) + (w * Bp + Pn * Bsuf - B1p);
+            const T C = qt[p] * (w * (Atot - G[p]) + Pn * Asuf - (A1 - P[p] * G[p])) +
+                        (w * (Btot - gq) + Pn * Bsuf - (B1 - P[p] * gq));
             a.ring_c[p * N + c] = C;
             Asuf += G[p];
             Bsuf += gq;
@@ -225,13 +267,16 @@ __device__ __forceinline__ T edge_tendency(const DevArgs<T>& a, int e) {
     const int c0 = t.ec0[e], c1 = t.ec1[e];
     const uint32_t pp = t.ep[e];
     const int p0 = pp & 0xff, p1 = (pp >> 8) & 0xff;
+    const T rdc = t.rdc[e];
+    const T db = t.b[c1] - t.b[c0];
+    griddep_wait();
     const T C0 = a.ring_c[p0 * N + c0], C1 = a.ring_c[p1 * N + c1];
     // h1 - h0 is exact for nearby thicknesses (Sterbenz); with COMP the
     // compensation words restore the digits the FP32 thickness dropped.
     T dh = a.in_h[c1] - a.in_h[c0];
     if (COMP) dh += a.in_hl[c1] - a.in_hl[c0];
-    const T grad = a.g * (dh + (t.b[c1] - t.b[c0])) + (a.ring_k[c1] - a.ring_k[c0]);
-    return -t.rdc[e] * (T(0.5) * (C1 - C0) + grad);
+    const T grad = a.g * (dh + db) + (a.ring_k[c1] - a.ring_k[c0]);
+    return -rdc * (T(0.5) * (C1 - C0) + grad);
 }
 
 // ------------------------------------------------------------ pointwise parts
@@ -313,28 +358,51 @@ __device__ __forceinline__ int find_seg(const DevArgs<T>& a, int blk) {
     return s;
 }
 
+
+__device__ __forceinline__ bool is_ring(int type) {
+    return type == SEG_RING || type == SEG_RING_UPD || type == SEG_RING_ACC;
+}
+
 template <class T, bool COMP, int MAXR, int KIND>
 __global__ void __launch_bounds__(256) kernel_phase(const __grid_constant__ DevArgs<T> a) {
+    griddep_launch_dependents();
     const int sidx = find_seg(a, blockIdx.x);
     const DevSeg<T>& s = a.seg[sidx];
-    const int i = s.begin + (blockIdx.x - s.block0) * blockDim.x + threadIdx.x;
-    if (i >= s.end) return;
     const int type = s.type;
+    const int local = (blockIdx.x - s.block0) * blockDim.x + threadIdx.x;
+    const int i = s.begin + local;
+    if (i >= s.end) return;
     if (KIND == 0 && type == SEG_VERT) {
         vertex_pv(a, i);
-    } else if (KIND == 1 && (type == SEG_RING || type == SEG_RING_UPD || type == SEG_RING_ACC)) {
+    } else if (KIND == 1 && is_ring(type)) {
         const T H = ring_pass<T, COMP, MAXR>(a, i);
         if (type != SEG_RING) epilogue<T, COMP, true>(a, s, type == SEG_RING_ACC, i, H, a.in_h);
     } else if (KIND == 2 && (type == SEG_EDGE_UPD || type == SEG_EDGE_ACC)) {
         const T U = edge_tendency<T, COMP>(a, i);
         epilogue<T, COMP, false>(a, s, type == SEG_EDGE_ACC, i, U, a.in_u);
     } else {
+        griddep_wait();
         pointwise<T, COMP>(s, i);
     }
 }
 
+template <class K, class A>
+cudaError_t launch_kernel(K kernel, int blocks, int block, bool pdl, cudaStream_t st, const A& a) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, a);
+}
+
 template <class T, bool COMP, int MAXR>
-cudaError_t launch_t(const LaunchDesc& d, const void* tables, int block, int* flag,
+cudaError_t launch_t(const LaunchDesc& d, const void* tables, int block, bool pdl, int* flag,
                      cudaStream_t st) {
     DevArgs<T> a;
     a.t = *static_cast<const Tables<T>*>(tables);
@@ -374,11 +442,10 @@ cudaError_t launch_t(const LaunchDesc& d, const void* tables, int block, int* fl
     }
     if (blocks == 0) return cudaSuccess;
     switch (d.kind) {
-        case 0: kernel_phase<T, COMP, MAXR, 0><<<blocks, block, 0, st>>>(a); break;
-        case 1: kernel_phase<T, COMP, MAXR, 1><<<blocks, block, 0, st>>>(a); break;
-        default: kernel_phase<T, COMP, MAXR, 2><<<blocks, block, 0, st>>>(a); break;
+        case 0: return launch_kernel(kernel_phase<T, COMP, MAXR, 0>, blocks, block, pdl, st, a);
+        case 1: return launch_kernel(kernel_phase<T, COMP, MAXR, 1>, blocks, block, pdl, st, a);
+        default: return launch_kernel(kernel_phase<T, COMP, MAXR, 2>, blocks, block, pdl, st, a);
     }
-    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------ state I/O
@@ -469,8 +536,8 @@ __global__ void __launch_bounds__(DIAG_THREADS) diag_final(const double* partial
 template <class T, bool COMP>
 cudaError_t launch_any(const LaunchDesc& d, const void* tables, const KernelConfig& kc, int* flag,
                        cudaStream_t s) {
-    if (kc.maxdeg <= 8) return launch_t<T, COMP, 8>(d, tables, kc.block, flag, s);
-    return launch_t<T, COMP, MAX_DEGREE>(d, tables, kc.block, flag, s);
+    if (kc.maxdeg <= 8) return launch_t<T, COMP, 8>(d, tables, kc.block, kc.pdl, flag, s);
+    return launch_t<T, COMP, MAX_DEGREE>(d, tables, kc.block, kc.pdl, flag, s);
 }
 
 }  // namespace

@@ -78,6 +78,9 @@ struct lts_state_s {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     cudaStream_t capture_stream = nullptr;
+    cudaStream_t side_stream = nullptr;          // concurrent branch (direct launches)
+    cudaStream_t capture_side = nullptr;         // concurrent branch during capture
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     DeviceArena arena;
     const void* tables = nullptr;
     SV buf[4];            // [parity] = x_old, [1-parity] = x_new, [2] = x_1st, [3] = x_2nd
@@ -103,6 +106,7 @@ struct lts_state_s {
     int launches[NKINDS] = {0, 0, 0};
     double prof_ms[NKINDS] = {0, 0, 0};
     std::vector<cudaEvent_t> events;
+    std::vector<cudaEvent_t> gevents[2];   // profile == 2: per kernel node, per parity
     ~lts_state_s();
 };
 
@@ -420,6 +424,7 @@ void plan_lts3(lts_state_s* S, int parity, std::vector<LaunchDesc>& out) {
     out.push_back(P.launch(1, X1, {P.upd(true, B_I1, B_CREST, X0, X1, X2, A2, dt / 4.0)}));
     out.push_back(P.launch(2, X1, {P.upd(false, B_I1, B_CREST, X0, X1, X2, A2, dt / 4.0),
                                    P.copy(true, B_I1, B_I1, X2, S->P2c, I1)}));
+    const size_t after_step2 = out.size();
     // Step 3: M fine substeps on F, correction terms on I1 u I2, I1 predicted
     for (int k = 0; k < M; ++k) {
         const SV& old = (k == 0) ? X0 : XN;
@@ -448,13 +453,48 @@ void plan_lts3(lts_state_s* S, int parity, std::vector<LaunchDesc>& out) {
                                            P.acc(false, s - 1, k == 0), pe}));
         }
     }
-    // Step 4 (third stage on C) and Step 5 (interface correction)
-    out.push_back(P.launch(0, X2, {P.vert(B_I2, B_CREST)}));
-    out.push_back(P.launch(1, X2, {P.upd(true, B_C1, B_CREST, X0, X2, XN, A3, 2.0 * dt / 3.0),
-                                   P.replay(true, X0, XN, dtM)}));
-    out.push_back(P.launch(2, X2, {P.upd(false, B_C1, B_CREST, X0, X2, XN, A3, 2.0 * dt / 3.0),
-                                   P.replay(false, X0, XN, dtM)}));
-    out.erase(std::remove_if(out.begin(), out.end(), [](const LaunchDesc& d) { return d.nseg == 0; }),
+    // Step 4 (third stage on C, reading R2) and Step 5 (interface correction).
+    // Step 4 depends only on Step 2 (reading A7 of the design notes): its part
+    // on the far coarse band C rest runs as a side branch concurrently with
+    // Step 3 (it reads x_2nd on bands C2..C rest and writes x_new on C rest,
+    // which Step 3 neither reads nor writes; its q / ring entries are disjoint
+    // from Step 3's).  The C1, C2 part, whose cells Step 3 still reads in
+    // x_new, follows Step 3 together with Step 5.
+    std::vector<LaunchDesc> side;
+    side.push_back(P.launch(0, X2, {P.vert(B_C2, B_CREST)}));
+    side.push_back(P.launch(1, X2, {P.upd(true, B_CREST, B_CREST, X0, X2, XN, A3, 2.0 * dt / 3.0)}));
+    side.push_back(P.launch(2, X2, {P.upd(false, B_CREST, B_CREST, X0, X2, XN, A3, 2.0 * dt / 3.0)}));
+    std::vector<LaunchDesc> tail;
+    tail.push_back(P.launch(0, X2, {P.vert(B_I2, B_C2)}));
+    tail.push_back(P.launch(1, X2, {P.upd(true, B_C1, B_C2, X0, X2, XN, A3, 2.0 * dt / 3.0),
+                                    P.replay(true, X0, XN, dtM)}));
+    tail.push_back(P.launch(2, X2, {P.upd(false, B_C1, B_C2, X0, X2, XN, A3, 2.0 * dt / 3.0),
+                                    P.replay(false, X0, XN, dtM)}));
+    auto drop = [](std::vector<LaunchDesc>& v) {
+        v.erase(std::remove_if(v.begin(), v.end(), [](const LaunchDesc& d) { return d.nseg == 0; }),
+                v.end());
+    };
+    drop(side);
+    drop(tail);
+    const bool concurrent = S->p.profile == 0 && !side.empty();
+    if (concurrent) {
+        // the side branch forks right after Step 2
+        for (auto& d : side) d.branch = 1;
+        side.front().fork = true;
+        if (!tail.empty()) tail.front().join = true;
+        out.insert(out.begin() + static_cast<long>(after_step2), side.begin(), side.end());
+    } else {
+        out.insert(out.end(), side.begin(), side.end());
+    }
+    out.insert(out.end(), tail.begin(), tail.end());
+    if (concurrent && tail.empty()) {
+        LaunchDesc j;   // nothing after Step 3: still join before the step ends
+        j.join = true;
+        out.push_back(j);
+    }
+    // empty launches (bands without cells) are dropped, markers are kept
+    out.erase(std::remove_if(out.begin(), out.end(),
+                             [](const LaunchDesc& d) { return d.nseg == 0 && !d.fork && !d.join; }),
               out.end());
 }
 
@@ -478,19 +518,57 @@ void plan_ssprk3(lts_state_s* S, int parity, std::vector<LaunchDesc>& out) {
     }
 }
 
-int enqueue_plan(lts_state_s* S, const std::vector<LaunchDesc>& plan, cudaStream_t st) {
+// Enqueues one coarse step: main-stream launches on `st`, side-branch
+// launches on `side`, with an event fork before the branch and a join before
+// the first launch that needs it.  A launch that follows a fork or join is
+// not a programmatic dependent of its stream predecessor.
+int enqueue_plan(lts_state_s* S, const std::vector<LaunchDesc>& plan, cudaStream_t st,
+                 cudaStream_t side) {
+    bool after_event[2] = {false, false};
     for (const LaunchDesc& d : plan) {
-        cudaError_t e = launch_phase(d, S->tables, S->kc, S->flag, st);
+        if (d.fork) {
+            CUDA_TRY(cudaEventRecord(S->ev_fork, st));
+            CUDA_TRY(cudaStreamWaitEvent(side, S->ev_fork, 0));
+            after_event[1] = true;
+        }
+        if (d.join) {
+            CUDA_TRY(cudaEventRecord(S->ev_join, side));
+            CUDA_TRY(cudaStreamWaitEvent(st, S->ev_join, 0));
+            after_event[0] = true;
+        }
+        if (d.nseg == 0) continue;
+        KernelConfig kc = S->kc;
+        if (after_event[d.branch]) kc.pdl = false;
+        after_event[d.branch] = false;
+        cudaError_t e = launch_phase(d, S->tables, kc, S->flag, d.branch ? side : st);
         if (e != cudaSuccess) return set_error(LTS_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
+    }
+    return LTS_OK;
+}
+
+// profile == 2: an external event-record node before and after every kernel
+// node, so per-kernel times can be read after each graph launch.
+int enqueue_plan_timed(lts_state_s* S, const std::vector<LaunchDesc>& plan, cudaStream_t st, int p) {
+    for (size_t k = 0; k < plan.size(); ++k) {
+        cudaEvent_t* ev = &S->gevents[p][2 * k];
+        cudaError_t e = cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal);
+        if (e == cudaSuccess) e = launch_phase(plan[k], S->tables, S->kc, S->flag, st);
+        if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal);
+        if (e != cudaSuccess) return set_error(LTS_ECUDA, "timed capture: %s", cudaGetErrorString(e));
     }
     return LTS_OK;
 }
 
 int capture_graphs(lts_state_s* S) {
     for (int p = 0; p < 2; ++p) {
+        if (S->p.profile == 2) {
+            S->gevents[p].resize(2 * S->plan[p].size());
+            for (auto& ev : S->gevents[p]) CUDA_TRY(cudaEventCreate(&ev));
+        }
         cudaGraph_t g = nullptr;
         CUDA_TRY(cudaStreamBeginCapture(S->capture_stream, cudaStreamCaptureModeThreadLocal));
-        int rc = enqueue_plan(S, S->plan[p], S->capture_stream);
+        int rc = S->p.profile == 2 ? enqueue_plan_timed(S, S->plan[p], S->capture_stream, p)
+                                   : enqueue_plan(S, S->plan[p], S->capture_stream, S->capture_side);
         cudaError_t e = cudaStreamEndCapture(S->capture_stream, &g);
         if (rc != LTS_OK) {
             if (g) cudaGraphDestroy(g);
@@ -566,8 +644,14 @@ lts_state_s::~lts_state_s() {
     for (auto& e : exec)
         if (e) cudaGraphExecDestroy(e);
     for (auto ev : events) cudaEventDestroy(ev);
+    for (auto& v : gevents)
+        for (auto ev : v) cudaEventDestroy(ev);
     if (own_stream && stream) cudaStreamDestroy(stream);
     if (capture_stream) cudaStreamDestroy(capture_stream);
+    if (side_stream) cudaStreamDestroy(side_stream);
+    if (capture_side) cudaStreamDestroy(capture_side);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
 }
 
 // ---------------------------------------------------------------- the C ABI
@@ -784,6 +868,8 @@ int lts_state_create(lts_mesh mesh, lts_regions reg, const double* h0, const dou
     S->kc.comp = (which == 0) && p->compensated;
     S->kc.block = bs;
     S->kc.maxdeg = mesh->m.maxE <= 8 ? 8 : MAX_DEGREE;
+    S->kc.mindeg = *std::min_element(mesh->m.nEoC.begin(), mesh->m.nEoC.end());
+    S->kc.pdl = p->pdl != 0 && p->profile == 0;
     S->tsz = which ? 8 : 4;
     S->tables = which ? static_cast<const void*>(&reg->t64) : static_cast<const void*>(&reg->t32);
     if (p->stream) {
@@ -793,6 +879,10 @@ int lts_state_create(lts_mesh mesh, lts_regions reg, const double* h0, const dou
         S->own_stream = true;
     }
     CUDA_TRY(cudaStreamCreateWithFlags(&S->capture_stream, cudaStreamNonBlocking));
+    CUDA_TRY(cudaStreamCreateWithFlags(&S->capture_side, cudaStreamNonBlocking));
+    CUDA_TRY(cudaStreamCreateWithFlags(&S->side_stream, cudaStreamNonBlocking));
+    CUDA_TRY(cudaEventCreateWithFlags(&S->ev_fork, cudaEventDisableTiming));
+    CUDA_TRY(cudaEventCreateWithFlags(&S->ev_join, cudaEventDisableTiming));
     reg->ref++;
     S->reg = reg;
     rc = state_alloc(S.get());
@@ -808,12 +898,13 @@ int lts_state_create(lts_mesh mesh, lts_regions reg, const double* h0, const dou
     // launch statistics of one step (both parities have the same sizes)
     const HostMesh& m = mesh->m;
     for (LaunchDesc& d : S->plan[0]) {
+        if (d.nseg == 0) continue;
         d.bytes = launch_bytes(d, reg->r, m.nC, m.nE, m.nV, S->tsz, S->kc.comp);
         S->bytes[d.kind] += d.bytes;
         S->launches[d.kind] += 1;
     }
     rc = write_state(S.get(), h0, u0);
-    if (rc == LTS_OK && p->use_graph && !p->profile) rc = capture_graphs(S.get());
+    if (rc == LTS_OK && ((p->use_graph && p->profile != 1) || p->profile == 2)) rc = capture_graphs(S.get());
     if (rc == LTS_OK) {
         cudaError_t e = cudaStreamSynchronize(S->stream);
         if (e != cudaSuccess) rc = set_error(LTS_ECUDA, "state upload: %s", cudaGetErrorString(e));
@@ -839,7 +930,26 @@ void lts_state_destroy(lts_state s) {
 int lts_step(lts_state s, int32_t n) {
     if (!s) return set_error(LTS_EINVAL, "null state");
     if (n < 0) return set_error(LTS_EINVAL, "n_coarse must be >= 0");
-    if (s->p.profile) {
+    if (s->p.profile == 2) {
+        // graph launches with event nodes; per-kernel times summed over the call
+        for (double& x : s->prof_ms) x = 0.0;
+        for (int i = 0; i < n; ++i) {
+            const int par = s->parity;
+            CUDA_TRY(cudaGraphLaunch(s->exec[par], s->stream));
+            CUDA_TRY(cudaStreamSynchronize(s->stream));
+            const auto& plan = s->plan[par];
+            for (size_t k = 0; k < plan.size(); ++k) {
+                float ms = 0.f;
+                CUDA_TRY(cudaEventElapsedTime(&ms, s->gevents[par][2 * k], s->gevents[par][2 * k + 1]));
+                s->prof_ms[plan[k].kind] += ms;
+            }
+            s->parity ^= 1;
+            s->steps++;
+            s->time += s->p.dt;
+        }
+        return LTS_OK;
+    }
+    if (s->p.profile == 1) {
         const size_t L = s->plan[0].size();
         if (s->events.size() < 2 * L) {
             for (size_t k = s->events.size(); k < 2 * L; ++k) {
@@ -873,7 +983,7 @@ int lts_step(lts_state s, int32_t n) {
         if (s->exec[s->parity]) {
             CUDA_TRY(cudaGraphLaunch(s->exec[s->parity], s->stream));
         } else {
-            int rc = enqueue_plan(s, s->plan[s->parity], s->stream);
+            int rc = enqueue_plan(s, s->plan[s->parity], s->stream, s->side_stream);
             if (rc != LTS_OK) return rc;
         }
         s->parity ^= 1;

@@ -18,7 +18,8 @@ enum Band : int {
 // Device tables in band order.  Cell "slot" arrays are slot-major:
 // element (slot j, cell c) is at [j * nC + c]; slot j of cell c holds the
 // j-th edge of c counter-clockwise, the neighbour across it, and the vertex
-// between slot j and slot j+1.
+// between slot j and slot j+1.  Slots j >= nEdgesOnCell repeat slot 0 (valid
+// indices, never used in a sum), so they may be loaded unconditionally.
 template <class T>
 struct Tables {
     int nC, nE, nV, maxE;
@@ -96,6 +97,9 @@ struct LaunchDesc {
     void* ring_k = nullptr;       // [nC] kinetic energy K_i
     double g = 9.81;
     double bytes = 0.0;           // algorithmic bytes (filled by the planner)
+    int branch = 0;               // 0 = main stream, 1 = side branch (concurrent work)
+    bool fork = false;            // side branch starts here (waits for the main stream)
+    bool join = false;            // main stream waits for the side branch before this launch
 };
 
 struct KernelConfig {
@@ -103,6 +107,8 @@ struct KernelConfig {
     bool comp;       // FP32 compensated
     int block;       // threads per block
     int maxdeg;      // ring kernel variant: 8 or 16
+    int mindeg;      // smallest cell degree of the mesh (slots loaded unconditionally)
+    bool pdl;        // programmatic dependent launch
 };
 
 // kernels.cu

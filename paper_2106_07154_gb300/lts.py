@@ -70,7 +70,8 @@ class lts_density(C.Structure):
 class lts_params(C.Structure):
     _fields_ = [("g", C.c_double), ("dt", C.c_double), ("precision", C.c_int32),
                 ("mode", C.c_int32), ("compensated", C.c_int32), ("use_graph", C.c_int32),
-                ("block_size", C.c_int32), ("profile", C.c_int32), ("stream", C.c_void_p)]
+                ("block_size", C.c_int32), ("profile", C.c_int32), ("pdl", C.c_int32),
+                ("stream", C.c_void_p)]
 
 
 class lts_diag(C.Structure):
@@ -268,9 +269,10 @@ def lts_regions_permutation(reg_h, nCells: int, nEdges: int, nVertices: int):
 
 def lts_state_create(mesh_h, reg_h, h0, u0, g: float, dt: float, precision: int = LTS_FP32,
                      mode: int = LTS_MODE_LTS3, compensated: bool = True, use_graph: bool = True,
-                     block_size: int = 0, profile: bool = False, stream: int | None = None):
+                     block_size: int = 0, profile: int = 0, stream: int | None = None,
+                     pdl: bool = True):
     p = lts_params(g, dt, precision, mode, int(compensated), int(use_graph), block_size,
-                   int(profile), stream)
+                   int(profile), int(pdl), stream)
     h = C.c_void_p()
     _check(lib().lts_state_create(mesh_h, reg_h, _f64(h0).ctypes.data, _f64(u0).ctypes.data,
                                   C.byref(p), C.byref(h)))
@@ -316,8 +318,8 @@ class Model:
 
     def __init__(self, mesh: dict, fine_mask, M: int, h0, u0, dt: float, g: float = 9.81,
                  precision: int = LTS_FP32, mode: int = LTS_MODE_LTS3, compensated: bool = True,
-                 use_graph: bool = True, block_size: int = 0, profile: bool = False,
-                 interface_layers: int = 1, stream: int | None = None):
+                 use_graph: bool = True, block_size: int = 0, profile: int = 0,
+                 interface_layers: int = 1, stream: int | None = None, pdl: bool = True):
         self.nC = int(mesh["nCells"])
         self.nE = int(mesh["nEdges"])
         self.nV = int(mesh["nVertices"])
@@ -325,7 +327,7 @@ class Model:
         self.mesh_h = lts_mesh_create(mesh)
         self.reg_h = lts_regions_set(self.mesh_h, fine_mask, 3, M, interface_layers)
         self.state_h = lts_state_create(self.mesh_h, self.reg_h, h0, u0, g, dt, precision, mode,
-                                        compensated, use_graph, block_size, profile, stream)
+                                        compensated, use_graph, block_size, profile, stream, pdl)
 
     def step(self, n: int):
         lts_step(self.state_h, n)
