@@ -155,6 +155,11 @@ void lts_regions_destroy(lts_regions r);
  * Either pointer may be NULL. */
 int lts_regions_labels(lts_regions r, int8_t* cell_label, int8_t* edge_label);
 
+/* Re-tiles the regions for the fused kernel (kernel_path = 1): tiles of at
+ * most tile_cells consecutive band-order cells (32..4096; default 256).
+ * Only while no state uses the regions.  Errors: LTS_EINVAL. */
+int lts_regions_tiling(lts_regions r, int32_t tile_cells);
+
 /* Number of cells, edges and vertices per band (arrays of 9). */
 int lts_regions_counts(lts_regions r, int64_t* cells, int64_t* edges, int64_t* vertices);
 
@@ -182,6 +187,9 @@ typedef struct lts_params {
                                graph (per-kernel times of the last lts_step call)      */
     int32_t pdl;            /* 1: programmatic dependent launch between consecutive
                                kernels (each launch overlaps its predecessor's tail)   */
+    int32_t kernel_path;    /* 0: three launches per right-hand side (vertex PV, cell
+                               ring, edge; default); 1: one fused tile kernel per
+                               right-hand side (shared-memory staging per tile)        */
     void* stream;           /* cudaStream_t to enqueue on; NULL = a library stream     */
 } lts_params;
 
@@ -217,11 +225,12 @@ int lts_write(lts_state s, const double* h, const double* u, double time, int64_
 
 /* Launch statistics of one coarse step: number of kernel launches, and per
  * launch kind k (0 = vertex PV, 1 = cell ring pass with the thickness
- * update, 2 = edge pass with the velocity update) the algorithmic bytes
+ * update, 2 = edge pass with the velocity update, 3 = fused tile kernel
+ * doing all three for a tile) the algorithmic bytes
  * summed over the step (each array element a launch touches counted once).
  * With profile = 1, ms[k] is the summed event time of those launches in the
  * last lts_step call (0 otherwise).  Arrays of LTS_NKINDS. */
-#define LTS_NKINDS 3
+#define LTS_NKINDS 4
 int lts_step_stats(lts_state s, int32_t* launches_per_step, double* bytes, double* ms,
                    int32_t* launches_per_kind);
 

@@ -39,11 +39,65 @@ struct DevArgs {
     const T* in_h;
     const T* in_hl;   // compensation words of the input thickness (COMP only)
     const T* in_u;
+    const T* in_ul;   // compensation words of the input velocity (COMP only)
     T* q;
     T* ring_c;        // [maxE*nC] per-slot PV contributions
     T* ring_k;        // [nC] K_i
     T g;
     int* flag;
+    int l2;           // 0 no hint, 1 keep in L2 (evict_last), 2 stream (evict_first)
+    int smem;         // dynamic shared memory of the launch (fused tiles)
+};
+
+// ------------------------------------------------------------- L2 residency
+// The fine substeps revisit the same ~100 MB (fine-region tables and state)
+// 3M times per coarse step while the coarse-band launches stream the rest of
+// the mesh once; read-only loads carry an L2 eviction-priority policy so the
+// streamed data leaves L2 first.  Hints only: results do not depend on them.
+__device__ __forceinline__ uint64_t l2_policy(int mode) {
+    uint64_t p;
+    if (mode == 1)
+        asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    else if (mode == 2)
+        asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    else
+        asm("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+// Loads of mesh tables (never written by any kernel): free to be scheduled.
+#define LTS_LD_HINT(TY, PTXT, CONS)                                                      \
+    __device__ __forceinline__ TY ld_static(const TY* q, uint64_t p) {                   \
+        TY x;                                                                            \
+        asm("ld.global.nc.L2::cache_hint." PTXT " %0, [%1], %2;" : CONS(x) : "l"(q), "l"(p)); \
+        return x;                                                                        \
+    }                                                                                    \
+    __device__ __forceinline__ TY ld_state(const TY* q, uint64_t p) {                    \
+        TY x;                                                                            \
+        asm volatile("ld.global.nc.L2::cache_hint." PTXT " %0, [%1], %2;"                \
+                     : CONS(x) : "l"(q), "l"(p) : "memory");                             \
+        return x;                                                                        \
+    }
+#define LTS_R(x) "=r"(x)
+#define LTS_F(x) "=f"(x)
+#define LTS_D(x) "=d"(x)
+LTS_LD_HINT(int, "b32", LTS_R)
+LTS_LD_HINT(uint32_t, "b32", LTS_R)
+LTS_LD_HINT(float, "f32", LTS_F)
+LTS_LD_HINT(double, "f64", LTS_D)
+__device__ __forceinline__ uint8_t ld_static(const uint8_t* q, uint64_t p) {
+    uint32_t x;
+    asm("ld.global.nc.L2::cache_hint.u8 %0, [%1], %2;" : "=r"(x) : "l"(q), "l"(p));
+    return static_cast<uint8_t>(x);
+}
+// Read-only loads with the launch's L2 policy: `stat` for mesh tables, `operator()`
+// for state written by earlier kernels (ordered after griddep_wait).
+struct Ld {
+    uint64_t pol;
+    __device__ __forceinline__ explicit Ld(int m) : pol(l2_policy(m)) {}
+    template <class V>
+    __device__ __forceinline__ V stat(const V* q) const { return ld_static(q, pol); }
+    template <class V>
+    __device__ __forceinline__ V operator()(const V* q) const { return ld_state(q, pol); }
 };
 
 // ---------------------------------------------------------------- arithmetic
@@ -133,14 +187,15 @@ __device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wa
 template <class T>
 __device__ __forceinline__ void vertex_pv(const DevArgs<T>& a, int v) {
     const Tables<T>& t = a.t;
-    const int e0 = t.ve0[v], e1 = t.ve1[v], e2 = t.ve2[v];
-    const int c0 = t.vc0[v], c1 = t.vc1[v], c2 = t.vc2[v];
-    const T d0 = t.vd0[v], d1 = t.vd1[v], d2 = t.vd2[v];
-    const T k0 = t.vk0[v], k1 = t.vk1[v], k2 = t.vk2[v];
-    const T f = t.f[v];
+    const Ld ld(a.l2);
+    const int e0 = ld.stat(t.ve0 + v), e1 = ld.stat(t.ve1 + v), e2 = ld.stat(t.ve2 + v);
+    const int c0 = ld.stat(t.vc0 + v), c1 = ld.stat(t.vc1 + v), c2 = ld.stat(t.vc2 + v);
+    const T d0 = ld.stat(t.vd0 + v), d1 = ld.stat(t.vd1 + v), d2 = ld.stat(t.vd2 + v);
+    const T k0 = ld.stat(t.vk0 + v), k1 = ld.stat(t.vk1 + v), k2 = ld.stat(t.vk2 + v);
+    const T f = ld.stat(t.f + v);
     griddep_wait();
-    T zeta = d0 * a.in_u[e0] + d1 * a.in_u[e1] + d2 * a.in_u[e2];
-    T hv = k0 * a.in_h[c0] + k1 * a.in_h[c1] + k2 * a.in_h[c2];
+    T zeta = d0 * ld(a.in_u + e0) + d1 * ld(a.in_u + e1) + d2 * ld(a.in_u + e2);
+    T hv = k0 * ld(a.in_h + c0) + k1 * ld(a.in_h + c1) + k2 * ld(a.in_h + c2);
     a.q[v] = (zeta + f) / hv;
 }
 
@@ -167,36 +222,38 @@ constexpr int UNCOND = 6;
 template <class T, bool COMP, int MAXR>
 __device__ __forceinline__ T ring_pass(const DevArgs<T>& a, int c) {
     const Tables<T>& t = a.t;
+    const Ld ld(a.l2);
     const int N = t.nC;
-    const int n = t.cn[c];
+    const int n = ld.stat(t.cn + c);
     // static ring tables of the first UNCOND slots, before the wait
     int E0[UNCOND], NB0[UNCOND], V0[UNCOND];
     T SNL0[UNCOND], R0[UNCOND], SK0[UNCOND];
 #pragma unroll
     for (int j = 0; j < UNCOND; ++j) {
-        E0[j] = __ldg(t.se + j * N + c);
-        NB0[j] = __ldg(t.sn + j * N + c);
-        V0[j] = __ldg(t.sv + j * N + c);
-        SNL0[j] = __ldg(t.snl + j * N + c);
-        R0[j] = __ldg(t.sR + j * N + c);
-        SK0[j] = __ldg(t.sK + j * N + c);
+        E0[j] = ld.stat(t.se + j * N + c);
+        NB0[j] = ld.stat(t.sn + j * N + c);
+        V0[j] = ld.stat(t.sv + j * N + c);
+        SNL0[j] = ld.stat(t.snl + j * N + c);
+        R0[j] = ld.stat(t.sR + j * N + c);
+        SK0[j] = ld.stat(t.sK + j * N + c);
     }
+    const T rA = ld.stat(t.rA + c);
     griddep_wait();
-    const T hc = a.in_h[c];
+    const T hc = ld(a.in_h + c);
     T G[MAXR], qv[MAXR], R[MAXR];
     T Kc = T(0), s = T(0), comp = T(0);
 #pragma unroll
     for (int j = 0; j < MAXR; ++j) {
         if (j < UNCOND || j < n) {
-            const int e = j < UNCOND ? E0[j % UNCOND] : __ldg(t.se + j * N + c);
-            const int nb = j < UNCOND ? NB0[j % UNCOND] : __ldg(t.sn + j * N + c);
-            const int v = j < UNCOND ? V0[j % UNCOND] : __ldg(t.sv + j * N + c);
-            const T snl = j < UNCOND ? SNL0[j % UNCOND] : __ldg(t.snl + j * N + c);
-            const T Rj = j < UNCOND ? R0[j % UNCOND] : __ldg(t.sR + j * N + c);
-            const T sK = j < UNCOND ? SK0[j % UNCOND] : __ldg(t.sK + j * N + c);
-            const T uj = a.in_u[e];
-            const T hnb = a.in_h[nb];
-            qv[j] = a.q[v];
+            const int e = j < UNCOND ? E0[j % UNCOND] : ld.stat(t.se + j * N + c);
+            const int nb = j < UNCOND ? NB0[j % UNCOND] : ld.stat(t.sn + j * N + c);
+            const int v = j < UNCOND ? V0[j % UNCOND] : ld.stat(t.sv + j * N + c);
+            const T snl = j < UNCOND ? SNL0[j % UNCOND] : ld.stat(t.snl + j * N + c);
+            const T Rj = j < UNCOND ? R0[j % UNCOND] : ld.stat(t.sR + j * N + c);
+            const T sK = j < UNCOND ? SK0[j % UNCOND] : ld.stat(t.sK + j * N + c);
+            const T uj = ld(a.in_u + e);
+            const T hnb = ld(a.in_h + nb);
+            qv[j] = ld(a.q + v);
             const bool in = j < n;
             const T F = T(0.5) * (hc + hnb) * uj;
             const T g = in ? mul_rn(snl, F) : T(0);
@@ -254,7 +311,7 @@ __device__ __forceinline__ T ring_pass(const DevArgs<T>& a, int c) {
         }
     }
     a.ring_k[c] = Kc;
-    return -(s + comp) * t.rA[c];
+    return -(s + comp) * rA;
 }
 
 // --------------------------------------------------------------- kind 2: edge
@@ -263,20 +320,229 @@ __device__ __forceinline__ T ring_pass(const DevArgs<T>& a, int c) {
 template <class T, bool COMP>
 __device__ __forceinline__ T edge_tendency(const DevArgs<T>& a, int e) {
     const Tables<T>& t = a.t;
+    const Ld ld(a.l2);
     const int N = t.nC;
-    const int c0 = t.ec0[e], c1 = t.ec1[e];
-    const uint32_t pp = t.ep[e];
+    const int c0 = ld.stat(t.ec0 + e), c1 = ld.stat(t.ec1 + e);
+    const uint32_t pp = ld.stat(t.ep + e);
     const int p0 = pp & 0xff, p1 = (pp >> 8) & 0xff;
-    const T rdc = t.rdc[e];
-    const T db = t.b[c1] - t.b[c0];
+    const T rdc = ld.stat(t.rdc + e);
+    const T db = ld.stat(t.b + c1) - ld.stat(t.b + c0);
     griddep_wait();
-    const T C0 = a.ring_c[p0 * N + c0], C1 = a.ring_c[p1 * N + c1];
+    const T C0 = ld(a.ring_c + p0 * N + c0), C1 = ld(a.ring_c + p1 * N + c1);
     // h1 - h0 is exact for nearby thicknesses (Sterbenz); with COMP the
     // compensation words restore the digits the FP32 thickness dropped.
-    T dh = a.in_h[c1] - a.in_h[c0];
-    if (COMP) dh += a.in_hl[c1] - a.in_hl[c0];
-    const T grad = a.g * (dh + db) + (a.ring_k[c1] - a.ring_k[c0]);
+    T dh = ld(a.in_h + c1) - ld(a.in_h + c0);
+    if (COMP) dh += ld(a.in_hl + c1) - ld(a.in_hl + c0);
+    const T grad = a.g * (dh + db) + (ld(a.ring_k + c1) - ld(a.ring_k + c0));
     return -rdc * (T(0.5) * (C1 - C0) + grad);
+}
+
+template <class T, bool COMP>
+__device__ __forceinline__ void pointwise(const DevSeg<T>& s, int i);
+template <class T>
+__device__ __forceinline__ int find_seg(const DevArgs<T>& a, int blk);
+
+// ----------------------------------------------------------- kind 3: tiles
+//
+// The fused right-hand side: one block per tile (a band-order range of
+// cells inside one band, the edges whose lower cell it owns, a halo of the
+// other cells of those edges, and every ring vertex of those cells).
+//   pass 1: q_v of the tile's vertices            -> shared memory
+//   pass 2: ring pass of own + halo cells         -> C_p, K_c in shared memory;
+//           H_c with the stage update / accumulation for own cells
+//   pass 3: U_e of the owned edges from shared C and K -> stage update / accumulation
+// A vertex or halo cell shared by two tiles is evaluated by both from the
+// same inputs with the same code, so the results are bit-identical to the
+// three-launch path's.  No intermediate leaves the block.
+
+template <class T>
+__device__ __forceinline__ T vertex_value(const DevArgs<T>& a, const Ld& ld, int v) {
+    const Tables<T>& t = a.t;
+    const int e0 = ld.stat(t.ve0 + v), e1 = ld.stat(t.ve1 + v), e2 = ld.stat(t.ve2 + v);
+    const int c0 = ld.stat(t.vc0 + v), c1 = ld.stat(t.vc1 + v), c2 = ld.stat(t.vc2 + v);
+    const T d0 = ld.stat(t.vd0 + v), d1 = ld.stat(t.vd1 + v), d2 = ld.stat(t.vd2 + v);
+    const T k0 = ld.stat(t.vk0 + v), k1 = ld.stat(t.vk1 + v), k2 = ld.stat(t.vk2 + v);
+    const T f = ld.stat(t.f + v);
+    T zeta = d0 * ld(a.in_u + e0) + d1 * ld(a.in_u + e1) + d2 * ld(a.in_u + e2);
+    T hv = k0 * ld(a.in_h + c0) + k1 * ld(a.in_h + c1) + k2 * ld(a.in_h + c2);
+    return (zeta + f) / hv;
+}
+
+// The ring pass of kind 1 with q read from shared memory (local vertex ids
+// lsv) and C, K written to shared memory (slot-major over the local cells).
+template <class T, bool COMP, int MAXR>
+__device__ __forceinline__ T ring_local(const DevArgs<T>& a, const Ld& ld, int c, int k, int nl,
+                                        const uint16_t* lsv, const T* q_s, T* rc_s, T* K_s) {
+    const Tables<T>& t = a.t;
+    const int N = t.nC;
+    const int n = ld.stat(t.cn + c);
+    const T hc = ld(a.in_h + c);
+    T G[MAXR], qv[MAXR], R[MAXR];
+    T Kc = T(0), s = T(0), comp = T(0);
+#pragma unroll
+    for (int j = 0; j < MAXR; ++j) {
+        if (j < UNCOND || j < n) {
+            const int e = ld.stat(t.se + j * N + c);
+            const int nb = ld.stat(t.sn + j * N + c);
+            const int lv = lsv[j * nl + k];
+            const T snl = ld.stat(t.snl + j * N + c);
+            const T Rj = ld.stat(t.sR + j * N + c);
+            const T sK = ld.stat(t.sK + j * N + c);
+            const T uj = ld(a.in_u + e);
+            const T hnb = ld(a.in_h + nb);
+            qv[j] = q_s[lv];
+            const bool in = j < n;
+            const T F = T(0.5) * (hc + hnb) * uj;
+            const T g = in ? mul_rn(snl, F) : T(0);
+            G[j] = g;
+            R[j] = in ? Rj : T(0);
+            if (in) {
+                Kc += sK * uj * uj;
+                if (COMP) {
+                    T ss, ee;
+                    two_sum(s, g, ss, ee);
+                    s = ss;
+                    comp += ee;
+                } else {
+                    s += g;
+                }
+            }
+        } else {
+            G[j] = T(0);
+            R[j] = T(0);
+            qv[j] = T(0);
+        }
+    }
+    T qlast = qv[0];
+#pragma unroll
+    for (int j = 1; j < MAXR; ++j)
+        if (j == n - 1) qlast = qv[j];
+    T qt[MAXR], P[MAXR];
+    T Pacc = T(0), Atot = T(0), Btot = T(0), A1 = T(0), B1 = T(0);
+#pragma unroll
+    for (int j = 0; j < MAXR; ++j) {
+        qt[j] = T(0.5) * ((j == 0 ? qlast : qv[j - 1]) + qv[j]);
+        P[j] = Pacc;
+        if (j < n) {
+            Pacc += R[j];
+            const T gq = G[j] * qt[j];
+            Atot += G[j];
+            Btot += gq;
+            A1 += P[j] * G[j];
+            B1 += P[j] * gq;
+        }
+    }
+    const T Pn = Pacc;
+    T Asuf = T(0), Bsuf = T(0);
+#pragma unroll
+    for (int p = MAXR - 1; p >= 0; --p) {
+        if (p < n) {
+            const T gq = G[p] * qt[p];
+            const T w = P[p] - T(0.5);
+            const T C = qt[p] * (w * (Atot - G[p]) + Pn * Asuf - (A1 - P[p] * G[p])) +
+                        (w * (Btot - gq) + Pn * Bsuf - (B1 - P[p] * gq));
+            rc_s[p * nl + k] = C;
+            Asuf += G[p];
+            Bsuf += gq;
+        }
+    }
+    K_s[k] = Kc;
+    return -(s + comp) * ld.stat(t.rA + c);
+}
+
+// Stage update or accumulation with explicit arrays (fused kernel epilogue).
+template <class T, bool COMP>
+__device__ __forceinline__ void store_update(const T* oh, const T* ol, const T* xh, const T* xl,
+                                             T* outh, T* outl, int i, T a_, T D, T R, bool cell,
+                                             int* flag) {
+    T yh, yl;
+    combine<T, COMP>(oh[i], COMP ? ol[i] : T(0), xh[i], COMP ? xl[i] : T(0), a_, D, R, yh, yl);
+    outh[i] = yh;
+    if (COMP) outl[i] = yl;
+    const bool ok = cell ? finite_pos(yh) : finite_val(yh);
+    if (!ok) atomicOr(flag, cell ? 1 : 2);
+}
+
+template <class T, bool COMP, int MAXR>
+__device__ __forceinline__ void tile_pass(const DevArgs<T>& a, const DevSeg<T>& s, int tile) {
+    const Tables<T>& t = a.t;
+    const Ld ld(a.l2);
+    const int4 ta = t.ta[tile];
+    const int4 tb = t.tbk[tile];
+    const int c_begin = ta.x, nown = ta.y, halo_begin = ta.z, nl = ta.w;
+    const int e_begin = tb.x, e_end = tb.y, v_begin = tb.z, nv = tb.w;
+    const uint16_t* lsv = t.lsv + t.tlsv[tile];
+    const bool acc = tile >= s.pad;   // tiles from s.pad on accumulate (Steps 3.x.2)
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    // guard: a tile that would not fit the launch's shared memory is skipped
+    // and reported (flag bit 4) instead of touching memory it does not own
+    const long need = static_cast<long>(sizeof(T)) * (((nv + 3) & ~3) + (MAXR + 1) * static_cast<long>(nl));
+    if (need > a.smem) {
+        if (threadIdx.x == 0) atomicOr(a.flag, 4);
+        return;
+    }
+    T* q_s = reinterpret_cast<T*>(smem_raw);
+    T* rc_s = q_s + ((nv + 3) & ~3);
+    T* K_s = rc_s + MAXR * nl;
+    griddep_wait();
+    // pass 1: potential vorticity of the tile's vertices
+    for (int k = threadIdx.x; k < nv; k += blockDim.x) q_s[k] = vertex_value(a, ld, t.tverts[v_begin + k]);
+    __syncthreads();
+    // pass 2: rings of own and halo cells; own cells get their update
+    for (int k = threadIdx.x; k < nl; k += blockDim.x) {
+        const int c = k < nown ? c_begin + k : t.halo[halo_begin + (k - nown)];
+        const T H = ring_local<T, COMP, MAXR>(a, ld, c, k, nl, lsv, q_s, rc_s, K_s);
+        if (k < nown) {
+            if (acc) {
+                T* ac = static_cast<T*>(s.p[8]);
+                const int q = c - s.base;
+                ac[q] = s.flag ? H : ac[q] + H;
+            } else {
+                store_update<T, COMP>((const T*)s.p[0], (const T*)s.p[1], a.in_h, a.in_hl, (T*)s.p[2],
+                                      (T*)s.p[3], c, s.c[0], s.c[1], H, true, a.flag);
+            }
+        }
+    }
+    __syncthreads();
+    // pass 3: owned edges
+    const int N = t.nC;
+    for (int e = e_begin + threadIdx.x; e < e_end; e += blockDim.x) {
+        const uint32_t l = t.lec[e];
+        const int l0 = l & 0xffff, l1 = l >> 16;
+        const uint32_t pp = ld.stat(t.ep + e);
+        const int p0 = pp & 0xff, p1 = (pp >> 8) & 0xff;
+        const int c0 = ld.stat(t.ec0 + e), c1 = ld.stat(t.ec1 + e);
+        const T C0 = rc_s[p0 * nl + l0], C1 = rc_s[p1 * nl + l1];
+        T dh = ld(a.in_h + c1) - ld(a.in_h + c0);
+        if (COMP) dh += ld(a.in_hl + c1) - ld(a.in_hl + c0);
+        const T db = ld.stat(t.b + c1) - ld.stat(t.b + c0);
+        const T grad = a.g * (dh + db) + (K_s[l1] - K_s[l0]);
+        const T U = -ld.stat(t.rdc + e) * (T(0.5) * (C1 - C0) + grad);
+        if (acc) {
+            T* ac = static_cast<T*>(s.p[9]);
+            const int q = e - s.base2;
+            ac[q] = s.flag ? U : ac[q] + U;
+        } else {
+            store_update<T, COMP>((const T*)s.p[4], (const T*)s.p[5], a.in_u, a.in_ul, (T*)s.p[6],
+                                  (T*)s.p[7], e, s.c[0], s.c[1], U, false, a.flag);
+        }
+    }
+    (void)N;
+}
+
+template <class T, bool COMP, int MAXR>
+__global__ void __launch_bounds__(256) kernel_tiles(const __grid_constant__ DevArgs<T> a) {
+    griddep_launch_dependents();
+    const int sidx = find_seg(a, blockIdx.x);
+    const DevSeg<T>& s = a.seg[sidx];
+    if (s.type == SEG_TILE) {
+        tile_pass<T, COMP, MAXR>(a, s, s.begin + (blockIdx.x - s.block0));
+        return;
+    }
+    const int i = s.begin + (blockIdx.x - s.block0) * blockDim.x + threadIdx.x;
+    if (i >= s.end) return;
+    griddep_wait();
+    pointwise<T, COMP>(s, i);
 }
 
 // ------------------------------------------------------------ pointwise parts
@@ -292,10 +558,10 @@ __device__ __forceinline__ void pointwise(const DevSeg<T>& s, int i) {
         const T* x2l = (const T*)s.p[5];
         T* outh = (T*)s.p[6];
         T* outl = (T*)s.p[7];
-        const int k = i - s.base;
+        const int k = i - s.base, k2 = i - s.base2;
         T yh, yl;
-        predict<T, COMP>(oh[i], COMP ? ol[i] : T(0), x1h[k], COMP ? x1l[k] : T(0), x2h[k],
-                         COMP ? x2l[k] : T(0), s.c[0], s.c[1], s.flag, yh, yl);
+        predict<T, COMP>(oh[i], COMP ? ol[i] : T(0), x1h[k], COMP ? x1l[k] : T(0), x2h[k2],
+                         COMP ? x2l[k2] : T(0), s.c[0], s.c[1], s.flag, yh, yl);
         outh[i] = yh;
         if (COMP) outl[i] = yl;
     } else if (s.type == SEG_COPY) {
@@ -387,11 +653,12 @@ __global__ void __launch_bounds__(256) kernel_phase(const __grid_constant__ DevA
 }
 
 template <class K, class A>
-cudaError_t launch_kernel(K kernel, int blocks, int block, bool pdl, cudaStream_t st, const A& a) {
+cudaError_t launch_kernel(K kernel, int blocks, int block, bool pdl, cudaStream_t st, const A& a,
+                          int smem = 0) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(blocks);
     cfg.blockDim = dim3(block);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -402,18 +669,21 @@ cudaError_t launch_kernel(K kernel, int blocks, int block, bool pdl, cudaStream_
 }
 
 template <class T, bool COMP, int MAXR>
-cudaError_t launch_t(const LaunchDesc& d, const void* tables, int block, bool pdl, int* flag,
+cudaError_t launch_t(const LaunchDesc& d, const void* tables, int block, bool pdl, int smem, int* flag,
                      cudaStream_t st) {
     DevArgs<T> a;
     a.t = *static_cast<const Tables<T>*>(tables);
     a.in_h = static_cast<const T*>(d.in_h);
     a.in_hl = static_cast<const T*>(d.in_hl);
     a.in_u = static_cast<const T*>(d.in_u);
+    a.in_ul = static_cast<const T*>(d.in_ul);
     a.q = static_cast<T*>(d.q);
     a.ring_c = static_cast<T*>(d.ring_c);
     a.ring_k = static_cast<T*>(d.ring_k);
     a.g = static_cast<T>(d.g);
     a.flag = flag;
+    a.l2 = d.l2;
+    a.smem = smem;
     int blocks = 0, ns = 0;
     for (int k = 0; k < d.nseg; ++k) {
         const SegDesc& s = d.seg[k];
@@ -433,7 +703,12 @@ cudaError_t launch_t(const LaunchDesc& d, const void* tables, int block, bool pd
             o.c[4] = static_cast<T>(1.0 / 3.0);
         }
         for (int m = 0; m < 10; ++m) o.p[m] = s.p[m];
-        blocks += (s.end - s.begin + block - 1) / block;
+        if (s.type == SEG_TILE) {
+            o.pad = s.flag2;
+            blocks += s.end - s.begin;            // one block per tile
+        } else {
+            blocks += (s.end - s.begin + block - 1) / block;
+        }
     }
     a.nseg = ns;
     for (int k = ns; k < MAXSEG; ++k) {
@@ -441,6 +716,14 @@ cudaError_t launch_t(const LaunchDesc& d, const void* tables, int block, bool pd
         a.seg[k].block0 = 0x7fffffff;
     }
     if (blocks == 0) return cudaSuccess;
+    if (d.kind == 3) {
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(kernel_tiles<T, COMP, MAXR>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e != cudaSuccess) return e;
+        }
+        return launch_kernel(kernel_tiles<T, COMP, MAXR>, blocks, block, pdl, st, a, smem);
+    }
     switch (d.kind) {
         case 0: return launch_kernel(kernel_phase<T, COMP, MAXR, 0>, blocks, block, pdl, st, a);
         case 1: return launch_kernel(kernel_phase<T, COMP, MAXR, 1>, blocks, block, pdl, st, a);
@@ -536,8 +819,8 @@ __global__ void __launch_bounds__(DIAG_THREADS) diag_final(const double* partial
 template <class T, bool COMP>
 cudaError_t launch_any(const LaunchDesc& d, const void* tables, const KernelConfig& kc, int* flag,
                        cudaStream_t s) {
-    if (kc.maxdeg <= 8) return launch_t<T, COMP, 8>(d, tables, kc.block, kc.pdl, flag, s);
-    return launch_t<T, COMP, MAX_DEGREE>(d, tables, kc.block, kc.pdl, flag, s);
+    if (kc.maxdeg <= 8) return launch_t<T, COMP, 8>(d, tables, kc.block, kc.pdl, kc.tile_smem, flag, s);
+    return launch_t<T, COMP, MAX_DEGREE>(d, tables, kc.block, kc.pdl, kc.tile_smem, flag, s);
 }
 
 }  // namespace

@@ -18,6 +18,10 @@
 
 using namespace lts;
 
+namespace {
+constexpr int kDefaultTileCells = 256;   // cells per tile of the fused kernel
+}
+
 // ------------------------------------------------------------------ objects
 
 struct DeviceArena {
@@ -182,6 +186,13 @@ int build_tables(lts_regions_s* R, int which, Tables<T>& t) {
     t.vk0 = vk; t.vk1 = vk + nV; t.vk2 = vk + 2 * nV;
     t.vd0 = vd; t.vd1 = vd + nV; t.vd2 = vd + 2 * nV;
     t.f = up(co.f);
+    t.ta = up(r.tile_a);
+    t.tbk = up(r.tile_b);
+    t.tlsv = up(r.tile_lsv_off);
+    t.halo = up(r.halo);
+    t.tverts = up(r.tverts);
+    t.lsv = up(r.lsv);
+    t.lec = up(r.lec);
     t.area = up(co.area);
     t.bd = up(co.bd);
     t.sK64 = up(co.sK64);
@@ -200,6 +211,7 @@ int build_tables(lts_regions_s* R, int which, Tables<T>& t) {
 double launch_bytes(const LaunchDesc& d, const RegionsHost& r, int nC, int nE, int nV, size_t T,
                     bool comp) {
     std::vector<char> mh(nC, 0), mhl(nC, 0), mu(nE, 0), mq(nV, 0), mk(nC, 0), mb(nC, 0);
+    std::vector<char> mrow(nC, 0), mvert(nV, 0);   // fused tiles: ring rows and vertices read
     double bytes = 0.0;
     const double c = comp ? 1.0 : 0.0;
     for (int s = 0; s < d.nseg; ++s) {
@@ -243,6 +255,29 @@ double launch_bytes(const LaunchDesc& d, const RegionsHost& r, int nC, int nE, i
                 bytes += n * 2.0 * T;                        // the two ring shares C (one per edge end)
                 bytes += g.type == SEG_EDGE_UPD ? n * T * (2.0 + 3.0 * c) : n * T * (g.flag ? 1 : 2);
                 break;
+            case SEG_TILE:
+                for (int tl = g.begin; tl < g.end; ++tl) {
+                    const int4 ta = r.tile_a[tl], tb = r.tile_b[tl];
+                    const bool acc = tl >= g.flag2;
+                    // own cells: epilogue; all local cells: ring tables; vertices; edges
+                    bytes += ta.y * T * (acc ? (g.flag ? 1.0 : 2.0) : (2.0 + 3.0 * c));
+                    bytes += static_cast<double>(tb.y - tb.x) *
+                             (12.0 + T + 4.0 + (acc ? T * (g.flag ? 1.0 : 2.0) : T * (2.0 + 3.0 * c)));
+                    bytes += 8.0 * 4 + 8.0 * 4;   // tile descriptors
+                    for (int k = 0; k < ta.w; ++k) {
+                        const int cc = k < ta.y ? ta.x + k : r.halo[ta.z + (k - ta.y)];
+                        mrow[cc] = 1;
+                    }
+                    for (int k = 0; k < tb.w; ++k) mvert[r.tverts[tb.z + k]] = 1;
+                    for (int e = tb.x; e < tb.y; ++e) {
+                        mu[e] = 1;
+                        for (int cc : {r.ec0[e], r.ec1[e]}) {
+                            mh[cc] = mb[cc] = 1;
+                            if (comp) mhl[cc] = 1;
+                        }
+                    }
+                }
+                break;
             case SEG_PRED:
                 bytes += n * T * (g.flag ? 2.0 * (1 + c) : 4.0 * (1 + c));
                 break;
@@ -252,6 +287,25 @@ double launch_bytes(const LaunchDesc& d, const RegionsHost& r, int nC, int nE, i
             case SEG_REPLAY:
                 bytes += n * T * (5.0 + 2.0 * c);
                 break;
+        }
+    }
+    // fused tiles: ring tables (cn, rA, per slot se, sn, lsv, snl, sR, sK) of every
+    // local cell, and the state the rings gather; vertex tables and their gathers
+    for (int k = 0; k < nC; ++k) {
+        if (!mrow[k]) continue;
+        bytes += 1.0 + T + r.cn[k] * (10.0 + 3.0 * T);
+        mh[k] = 1;
+        for (int j = 0; j < r.cn[k]; ++j) {
+            mu[r.se[static_cast<size_t>(j) * nC + k]] = 1;
+            mh[r.sn[static_cast<size_t>(j) * nC + k]] = 1;
+        }
+    }
+    for (int v = 0; v < nV; ++v) {
+        if (!mvert[v]) continue;
+        bytes += 24.0 + 7.0 * T;
+        for (int q = 0; q < 3; ++q) {
+            mh[r.vc[static_cast<size_t>(q) * nV + v]] = 1;
+            mu[r.ve[static_cast<size_t>(q) * nV + v]] = 1;
         }
     }
     double cnt = 0.0;
@@ -276,6 +330,26 @@ struct Planner {
         s.type = SEG_VERT;
         s.begin = vb[lo];
         s.end = vb[hi + 1];
+        return s;
+    }
+    // fused right-hand side over the tiles of bands lo..hi; tiles of bands
+    // >= acc_lo accumulate (Steps 3.x.2) instead of updating
+    SegDesc tiles(int lo, int hi, int acc_lo, const SV& old, const SV& out, double a, double D,
+                  int stage, bool first) const {
+        SegDesc s;
+        s.type = SEG_TILE;
+        s.begin = r.tb[lo];
+        s.end = r.tb[hi + 1];
+        s.flag2 = acc_lo <= hi ? r.tb[acc_lo] : s.end;
+        s.flag = first ? 1 : 0;
+        s.base = cb[B_I1];
+        s.base2 = eb[B_I1];
+        s.p[0] = old.hh; s.p[1] = old.hl; s.p[2] = out.hh; s.p[3] = out.hl;
+        s.p[4] = old.uh; s.p[5] = old.ul; s.p[6] = out.uh; s.p[7] = out.ul;
+        s.p[8] = stage >= 0 ? S->acc_c[stage] : nullptr;
+        s.p[9] = stage >= 0 ? S->acc_e[stage] : nullptr;
+        s.c[0] = a;
+        s.c[1] = D;
         return s;
     }
     SegDesc ring(int lo, int hi) const {   // ring results only, cell bands lo..hi
@@ -313,7 +387,8 @@ struct Planner {
         return s;
     }
     // x[I1] = prediction (Steps 3.x.1) from x_old (full), P1, P2 (compact)
-    SegDesc pred(bool cell, const SV& old, const SV& out, int k, int M, int which) const {
+    SegDesc pred(bool cell, const SV& old, const SV& out, int k, int M, int which,
+                 const SV* x2full = nullptr) const {
         double a, at;
         const double kk = k, MM = M;
         if (which == 1) {          // alpha
@@ -342,6 +417,12 @@ struct Planner {
         s.p[3] = cell ? p1.hl : p1.ul;
         s.p[4] = cell ? p2.hh : p2.uh;
         s.p[5] = cell ? p2.hl : p2.ul;
+        s.base2 = s.base;
+        if (x2full) {   // x_2nd read from its stage array (before Step 3 overwrites I1)
+            s.p[4] = cell ? x2full->hh : x2full->uh;
+            s.p[5] = cell ? x2full->hl : x2full->ul;
+            s.base2 = 0;
+        }
         s.p[6] = cell ? out.hh : out.uh;
         s.p[7] = cell ? out.hl : out.ul;
         s.c[0] = c1;
@@ -385,6 +466,7 @@ struct Planner {
         d.in_h = in.hh;
         d.in_hl = in.hl;
         d.in_u = in.uh;
+        d.in_ul = in.ul;
         d.q = S->q;
         d.ring_c = S->ring_c;
         d.ring_k = S->ring_k;
@@ -425,6 +507,7 @@ void plan_lts3(lts_state_s* S, int parity, std::vector<LaunchDesc>& out) {
     out.push_back(P.launch(2, X1, {P.upd(false, B_I1, B_CREST, X0, X1, X2, A2, dt / 4.0),
                                    P.copy(true, B_I1, B_I1, X2, S->P2c, I1)}));
     const size_t after_step2 = out.size();
+    for (auto& d : out) d.l2 = 2;   // Steps 1 and 2 stream the coarse region
     // Step 3: M fine substeps on F, correction terms on I1 u I2, I1 predicted
     for (int k = 0; k < M; ++k) {
         const SV& old = (k == 0) ? X0 : XN;
@@ -460,6 +543,7 @@ void plan_lts3(lts_state_s* S, int parity, std::vector<LaunchDesc>& out) {
     // which Step 3 neither reads nor writes; its q / ring entries are disjoint
     // from Step 3's).  The C1, C2 part, whose cells Step 3 still reads in
     // x_new, follows Step 3 together with Step 5.
+    for (size_t k = after_step2; k < out.size(); ++k) out[k].l2 = 1;   // fine substeps stay in L2
     std::vector<LaunchDesc> side;
     side.push_back(P.launch(0, X2, {P.vert(B_C2, B_CREST)}));
     side.push_back(P.launch(1, X2, {P.upd(true, B_CREST, B_CREST, X0, X2, XN, A3, 2.0 * dt / 3.0)}));
@@ -470,6 +554,8 @@ void plan_lts3(lts_state_s* S, int parity, std::vector<LaunchDesc>& out) {
                                     P.replay(true, X0, XN, dtM)}));
     tail.push_back(P.launch(2, X2, {P.upd(false, B_C1, B_C2, X0, X2, XN, A3, 2.0 * dt / 3.0),
                                     P.replay(false, X0, XN, dtM)}));
+    for (auto& d : side) d.l2 = 2;
+    for (auto& d : tail) d.l2 = 2;
     auto drop = [](std::vector<LaunchDesc>& v) {
         v.erase(std::remove_if(v.begin(), v.end(), [](const LaunchDesc& d) { return d.nseg == 0; }),
                 v.end());
@@ -496,6 +582,116 @@ void plan_lts3(lts_state_s* S, int parity, std::vector<LaunchDesc>& out) {
     out.erase(std::remove_if(out.begin(), out.end(),
                              [](const LaunchDesc& d) { return d.nseg == 0 && !d.fork && !d.join; }),
               out.end());
+}
+
+// The same plan with one fused tile launch per right-hand side.
+void plan_lts3_fused(lts_state_s* S, int parity, std::vector<LaunchDesc>& out) {
+    const RegionsHost& r = S->reg->r;
+    Planner P{S, r, r.cb, r.eb, r.vb, S->kc.comp};
+    const SV& X0 = S->buf[parity];
+    const SV& XN = S->buf[1 - parity];
+    const SV& X1 = S->buf[2];
+    const SV& X2 = S->buf[3];
+    const double dt = S->p.dt;
+    const int M = r.M;
+    const double dtM = dt / M;
+    const int I1 = r.cb[B_I1];
+    const int I1e = r.eb[B_I1];
+    const SegDesc none;
+    const int NOACC = NBANDS;   // acc_lo past every band: all tiles update
+    out.clear();
+    // Step 1 on Fbar u I1 u I2 u C; x_new on I2..C2 prefilled with x_old
+    out.push_back(P.launch(3, X0, {P.tiles(B_F2, B_CREST, NOACC, X0, X1, A1, dt, -1, false),
+                                   P.copy(true, B_I2, B_C2, X0, XN, 0),
+                                   P.copy(false, B_I2, B_C2, X0, XN, 0)}));
+    // Step 2 on I1 u I2 u C; snapshots of x_1st on I1
+    out.push_back(P.launch(3, X1, {P.tiles(B_I1, B_CREST, NOACC, X0, X2, A2, dt / 4.0, -1, false),
+                                   P.copy(true, B_I1, B_I1, X1, S->P1c, I1),
+                                   P.copy(false, B_I1, B_I1, X1, S->P1e, I1e)}));
+    const size_t after_step2 = out.size();
+    for (auto& d : out) d.l2 = 2;
+    // Step 3
+    for (int k = 0; k < M; ++k) {
+        const SV& old = (k == 0) ? X0 : XN;
+        for (int s = 1; s <= 3; ++s) {
+            const SV& in = (s == 1) ? old : (s == 2 ? X1 : X2);
+            const SV& o = (s == 1) ? X1 : (s == 2 ? X2 : XN);
+            const double a = (s == 1) ? A1 : (s == 2 ? A2 : A3);
+            const double D = (s == 1) ? dtM : (s == 2 ? dtM / 4.0 : 2.0 * dtM / 3.0);
+            SegDesc pc, pe, sc, se;
+            if (s == 1) {
+                // x_2nd on I1 still holds the coarse stage here: read it in place,
+                // and take the snapshot for the later predictions
+                const bool first = (k == 0);
+                pc = P.pred(true, X0, X1, k, M, 2, first ? &X2 : nullptr);
+                pe = P.pred(false, X0, X1, k, M, 2, first ? &X2 : nullptr);
+                if (first) {
+                    sc = P.copy(true, B_I1, B_I1, X2, S->P2c, I1);
+                    se = P.copy(false, B_I1, B_I1, X2, S->P2e, I1e);
+                }
+            } else if (s == 2) {
+                pc = P.pred(true, X0, X2, k, M, 3);
+                pe = P.pred(false, X0, X2, k, M, 3);
+            } else if (k + 1 < M) {
+                pc = P.pred(true, X0, XN, k + 1, M, 1);
+                pe = P.pred(false, X0, XN, k + 1, M, 1);
+            }
+            LaunchDesc d = P.launch(3, in, {P.tiles(B_FDEEP, B_I2, B_I1, old, o, a, D, s - 1, k == 0),
+                                            pc, pe, sc, se});
+            d.l2 = 1;
+            out.push_back(d);
+        }
+    }
+    (void)none;
+    // Step 4 on C rest concurrently with Step 3; C1, C2 and Step 5 after it
+    std::vector<LaunchDesc> side, tail;
+    side.push_back(P.launch(3, X2, {P.tiles(B_CREST, B_CREST, NOACC, X0, XN, A3, 2.0 * dt / 3.0, -1, false)}));
+    tail.push_back(P.launch(3, X2, {P.tiles(B_C1, B_C2, NOACC, X0, XN, A3, 2.0 * dt / 3.0, -1, false),
+                                    P.replay(true, X0, XN, dtM), P.replay(false, X0, XN, dtM)}));
+    for (auto& d : side) d.l2 = 2;
+    for (auto& d : tail) d.l2 = 2;
+    auto drop = [](std::vector<LaunchDesc>& v) {
+        v.erase(std::remove_if(v.begin(), v.end(), [](const LaunchDesc& d) { return d.nseg == 0; }),
+                v.end());
+    };
+    drop(side);
+    drop(tail);
+    const bool concurrent = S->p.profile == 0 && !side.empty();
+    size_t at = after_step2;
+    if (concurrent) {
+        for (auto& d : side) d.branch = 1;
+        side.front().fork = true;
+        if (!tail.empty()) tail.front().join = true;
+        out.insert(out.begin() + static_cast<long>(at), side.begin(), side.end());
+    } else {
+        out.insert(out.end(), side.begin(), side.end());
+    }
+    out.insert(out.end(), tail.begin(), tail.end());
+    if (concurrent && tail.empty()) {
+        LaunchDesc j;
+        j.join = true;
+        out.push_back(j);
+    }
+    out.erase(std::remove_if(out.begin(), out.end(),
+                             [](const LaunchDesc& d) { return d.nseg == 0 && !d.fork && !d.join; }),
+              out.end());
+}
+
+void plan_ssprk3_fused(lts_state_s* S, int parity, std::vector<LaunchDesc>& out) {
+    const RegionsHost& r = S->reg->r;
+    Planner P{S, r, r.cb, r.eb, r.vb, S->kc.comp};
+    const SV& X0 = S->buf[parity];
+    const SV& XN = S->buf[1 - parity];
+    const SV& X1 = S->buf[2];
+    const SV& X2 = S->buf[3];
+    const double dt = S->p.dt;
+    out.clear();
+    const SV* ins[3] = {&X0, &X1, &X2};
+    const SV* outs[3] = {&X1, &X2, &XN};
+    const double as[3] = {A1, A2, A3};
+    const double Ds[3] = {dt, dt / 4.0, 2.0 * dt / 3.0};
+    for (int s = 0; s < 3; ++s)
+        out.push_back(P.launch(3, *ins[s], {P.tiles(B_FDEEP, B_CREST, NBANDS, X0, *outs[s], as[s], Ds[s], -1, false)}));
 }
 
 void plan_ssprk3(lts_state_s* S, int parity, std::vector<LaunchDesc>& out) {
@@ -796,6 +992,7 @@ int lts_regions_set(lts_mesh m, const int8_t* fine_mask, int32_t order, int32_t 
     int rc;
     try {
         rc = compute_regions(m->m, fine_mask, layers, R->r);
+        if (rc == LTS_OK) rc = build_tiles(m->m, R->r, kDefaultTileCells);
     } catch (const std::bad_alloc&) {
         return set_error(LTS_ENOMEM, "out of host memory");
     }
@@ -817,6 +1014,22 @@ int lts_regions_labels(lts_regions r, int8_t* cl, int8_t* el) {
         for (size_t i = 0; i < r->r.cband.size(); ++i) cl[i] = cmap[r->r.cband[i]];
     if (el)
         for (size_t e = 0; e < r->r.eband.size(); ++e) el[e] = emap[r->r.eband[e]];
+    return LTS_OK;
+}
+
+int lts_regions_tiling(lts_regions r, int32_t tile_cells) {
+    if (!r) return set_error(LTS_EINVAL, "null regions");
+    if (r->ref.load() != 1) return set_error(LTS_EINVAL, "regions are in use by a state");
+    int rc;
+    try {
+        rc = build_tiles(r->mesh->m, r->r, tile_cells);
+    } catch (const std::bad_alloc&) {
+        return set_error(LTS_ENOMEM, "out of host memory");
+    }
+    if (rc != LTS_OK) return rc;
+    r->arena[0].reset();   // device tables are rebuilt on the next state creation
+    r->arena[1].reset();
+    r->d_perm_c = r->d_perm_e = nullptr;
     return LTS_OK;
 }
 
@@ -867,10 +1080,17 @@ int lts_state_create(lts_mesh mesh, lts_regions reg, const double* h0, const dou
     S->kc.precision = which;
     S->kc.comp = (which == 0) && p->compensated;
     S->kc.block = bs;
+    S->tsz = which ? 8 : 4;
     S->kc.maxdeg = mesh->m.maxE <= 8 ? 8 : MAX_DEGREE;
+    if (p->kernel_path != 0 && p->kernel_path != 1)
+        return set_error(LTS_EINVAL, "kernel_path must be 0 (three launches) or 1 (fused tiles)");
+    {
+        const int nv = (reg->r.max_local_verts + 3) & ~3;
+        S->kc.tile_smem = static_cast<int>(S->tsz) * (nv + (S->kc.maxdeg + 1) * reg->r.max_local_cells);
+        if (S->kc.tile_smem > 227 * 1024) return set_error(LTS_EINVAL, "tiles need too much shared memory");
+    }
     S->kc.mindeg = *std::min_element(mesh->m.nEoC.begin(), mesh->m.nEoC.end());
     S->kc.pdl = p->pdl != 0 && p->profile == 0;
-    S->tsz = which ? 8 : 4;
     S->tables = which ? static_cast<const void*>(&reg->t64) : static_cast<const void*>(&reg->t32);
     if (p->stream) {
         S->stream = static_cast<cudaStream_t>(p->stream);
@@ -892,8 +1112,14 @@ int lts_state_create(lts_mesh mesh, lts_regions reg, const double* h0, const dou
         return rc;
     }
     for (int par = 0; par < 2; ++par) {
-        if (p->mode == LTS_MODE_LTS3) plan_lts3(S.get(), par, S->plan[par]);
-        else plan_ssprk3(S.get(), par, S->plan[par]);
+        const bool fused = p->kernel_path == 1;
+        if (p->mode == LTS_MODE_LTS3) {
+            if (fused) plan_lts3_fused(S.get(), par, S->plan[par]);
+            else plan_lts3(S.get(), par, S->plan[par]);
+        } else {
+            if (fused) plan_ssprk3_fused(S.get(), par, S->plan[par]);
+            else plan_ssprk3(S.get(), par, S->plan[par]);
+        }
     }
     // launch statistics of one step (both parities have the same sizes)
     const HostMesh& m = mesh->m;
@@ -1021,6 +1247,7 @@ int lts_read(lts_state s, double* h, double* u, lts_diag* d) {
         d->time = s->time;
         d->steps = s->steps;
     }
+    if (flag & 4) return set_error(LTS_ECUDA, "internal error: a tile exceeded its shared memory (skipped)");
     if (flag) return set_error(LTS_ENONFINITE, "a stage produced %s", (flag & 1) ? "a thickness <= 0 or non-finite" : "a non-finite velocity");
     return LTS_OK;
 }

@@ -44,6 +44,14 @@ struct Tables {
     const T* vk0; const T* vk1; const T* vk2;         // [nV] A_{c,v} / A_v
     const T* vd0; const T* vd1; const T* vd2;         // [nV] t_{e,v} d_e / A_v
     const T* f;                                        // [nV] Coriolis parameter
+    // tiles of the fused kernel (kind 3)
+    const int4* ta;      // [ntiles] {cell begin, own cells, halo begin, local cells}
+    const int4* tbk;     // [ntiles] {edge begin, edge end, vertex-list begin, local vertices}
+    const int* tlsv;     // [ntiles] start of the tile's local-slot-vertex block
+    const int* halo;     // halo cells of all tiles
+    const int* tverts;   // local vertex lists of all tiles
+    const uint16_t* lsv; // local vertex of (slot, local cell), slot-major per tile
+    const uint32_t* lec; // [nE] local cells of the owning tile: c0 | c1 << 16
     // diagnostics
     const double* area;  // [nC] A_c (FP64 master copy)
     const double* bd;    // [nC] b   (FP64 master copy)
@@ -65,6 +73,7 @@ enum SegType : int {
     SEG_PRED = 6,       // out = x_old + c1 (x1 - x_old) + c2 (x2 - x_old)   (I1 prediction)
     SEG_COPY = 7,       // dst[i - base_dst] = src[i - base_src]   (hi and lo)
     SEG_REPLAY = 8,     // Step 5: three stage combinations from the accumulated RHS
+    SEG_TILE = 9,       // fused right-hand side over tiles [begin, end) (one block per tile)
 };
 
 // Largest cell degree the ring kernel is compiled for (variants 8 and 16).
@@ -81,16 +90,18 @@ struct SegDesc {
     int base = 0;             // compact-array offset (acc, snapshots): compact index = i - base
     int base2 = 0;            // second offset (COPY source)
     int flag = 0;             // ACC: 1 = first term (store); PRED: 0 general, 1/2/3 select old/x1/x2
+    int flag2 = 0;            // TILE: first tile that accumulates instead of updating
     double c[4] = {0, 0, 0, 0};  // UPD: a, D; PRED: c1, c2; REPLAY: D1, D2, D3
     void* p[10] = {};         // see kernels.cu for the meaning per type
 };
 
 struct LaunchDesc {
-    int kind = 0;             // 0 = vertex, 1 = ring, 2 = edge
+    int kind = 0;             // 0 = vertex, 1 = ring, 2 = edge, 3 = fused tiles
     int nseg = 0;
     SegDesc seg[MAXSEG];
     const void* in_h = nullptr;   // input state (hi words) of the RHS
     const void* in_hl = nullptr;  // compensation words of the input thickness (or null)
+    const void* in_ul = nullptr;  // compensation words of the input velocity (or null)
     const void* in_u = nullptr;
     void* q = nullptr;            // vertex potential vorticity buffer
     void* ring_c = nullptr;       // [maxE*nC] per-slot PV contributions (slot-major)
@@ -98,6 +109,7 @@ struct LaunchDesc {
     double g = 9.81;
     double bytes = 0.0;           // algorithmic bytes (filled by the planner)
     int branch = 0;               // 0 = main stream, 1 = side branch (concurrent work)
+    int l2 = 0;                   // L2 policy of read-only loads: 0 none, 1 keep, 2 stream
     bool fork = false;            // side branch starts here (waits for the main stream)
     bool join = false;            // main stream waits for the side branch before this launch
 };
@@ -107,6 +119,7 @@ struct KernelConfig {
     bool comp;       // FP32 compensated
     int block;       // threads per block
     int maxdeg;      // ring kernel variant: 8 or 16
+    int tile_smem;   // dynamic shared memory of the fused kernel (bytes)
     int mindeg;      // smallest cell degree of the mesh (slots loaded unconditionally)
     bool pdl;        // programmatic dependent launch
 };
@@ -122,6 +135,6 @@ cudaError_t launch_diagnostics(const KernelConfig& kc, const void* tables, const
                                const void* h_lo, const void* u_hi, const void* u_lo, double g,
                                double* partial, int nblocks, double* out2, cudaStream_t s);
 int kernel_registers(const KernelConfig& kc, int kind);
-constexpr int NKINDS = 3;
+constexpr int NKINDS = 4;
 
 }  // namespace lts

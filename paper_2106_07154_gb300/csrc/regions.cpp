@@ -216,6 +216,7 @@ int compute_regions(const HostMesh& m, const int8_t* fine, int layers, RegionsHo
     }
     r.vc.assign(3 * static_cast<size_t>(nV), 0);
     r.ve.assign(3 * static_cast<size_t>(nV), 0);
+    (void)0;
     for (int k = 0; k < nV; ++k) {
         int v = r.perm_v[k];
         for (int q = 0; q < 3; ++q) {
@@ -223,6 +224,95 @@ int compute_regions(const HostMesh& m, const int8_t* fine, int layers, RegionsHo
             r.ve[static_cast<size_t>(q) * nV + k] = r.inv_e[m.EoV[3 * v + q]];
         }
     }
+    return LTS_OK;
+}
+
+// Tiles for the fused right-hand-side kernel.  Tile cells are a contiguous
+// band-order range inside one band; the tile owns the edges whose lower
+// band-order cell is one of its cells (edges are sorted by that cell, so this
+// is an edge range, and all such edges carry the tile's band).  The tile's
+// local cells are its own cells followed by its halo (the other cell of owned
+// edges); its local vertices are all ring vertices of its local cells.
+int build_tiles(const HostMesh& m, RegionsHost& r, int tile_cells) {
+    const int nC = m.nC, nE = m.nE, W = m.maxE;
+    if (tile_cells < 32 || tile_cells > 4096) return set_error(LTS_EINVAL, "tile size out of range");
+    r.tile_cells = tile_cells;
+    r.tile_a.clear();
+    r.tile_b.clear();
+    r.tile_lsv_off.clear();
+    r.halo.clear();
+    r.tverts.clear();
+    r.lsv.clear();
+    r.lec.assign(nE, 0);
+    r.max_local_cells = r.max_local_verts = 0;
+    // edges are sorted by (band, lower cell): lower cell of every edge
+    std::vector<int> lowc(nE);
+    for (int e = 0; e < nE; ++e) lowc[e] = std::min(r.ec0[e], r.ec1[e]);
+    std::vector<int> stamp_c(nC, -1), local_c(nC, -1), stamp_v(m.nV, -1), local_v(m.nV, -1);
+    int ecur = 0;
+    for (int b = 0; b < NBANDS; ++b) {
+        r.tb[b] = static_cast<int>(r.tile_a.size());
+        for (int c0 = r.cb[b]; c0 < r.cb[b + 1]; c0 += tile_cells) {
+            const int c1 = std::min(c0 + tile_cells, r.cb[b + 1]);
+            const int t = static_cast<int>(r.tile_a.size());
+            // owned edges: lower cell in [c0, c1)
+            while (ecur < nE && lowc[ecur] < c0) ++ecur;
+            const int e0 = ecur;
+            while (ecur < nE && lowc[ecur] < c1) ++ecur;
+            const int e1 = ecur;
+            // local cells: own cells, then halo
+            std::vector<int> cells;
+            for (int c = c0; c < c1; ++c) {
+                stamp_c[c] = t;
+                local_c[c] = static_cast<int>(cells.size());
+                cells.push_back(c);
+            }
+            const int halo_begin = static_cast<int>(r.halo.size());
+            for (int e = e0; e < e1; ++e) {
+                for (int c : {r.ec0[e], r.ec1[e]}) {
+                    if (stamp_c[c] != t) {
+                        stamp_c[c] = t;
+                        local_c[c] = static_cast<int>(cells.size());
+                        cells.push_back(c);
+                        r.halo.push_back(c);
+                    }
+                }
+                r.lec[e] = static_cast<uint32_t>(local_c[r.ec0[e]]) |
+                           (static_cast<uint32_t>(local_c[r.ec1[e]]) << 16);
+            }
+            const int nl = static_cast<int>(cells.size());
+            // local vertices: ring vertices of the local cells, first seen first
+            const int vert_begin = static_cast<int>(r.tverts.size());
+            int nv = 0;
+            for (int c : cells)
+                for (int j = 0; j < r.cn[c]; ++j) {
+                    int v = r.sv[static_cast<size_t>(j) * nC + c];
+                    if (stamp_v[v] != t) {
+                        stamp_v[v] = t;
+                        local_v[v] = nv++;
+                        r.tverts.push_back(v);
+                    }
+                }
+            if (nl > 65535 || nv > 65535) return set_error(LTS_EINVAL, "tile too large");
+            // lsv block, slot-major over the local cells
+            r.tile_lsv_off.push_back(static_cast<int>(r.lsv.size()));
+            const size_t base = r.lsv.size();
+            r.lsv.resize(base + static_cast<size_t>(W) * nl, 0);
+            for (int k = 0; k < nl; ++k) {
+                int c = cells[k];
+                for (int j = 0; j < r.cn[c]; ++j)
+                    r.lsv[base + static_cast<size_t>(j) * nl + k] =
+                        static_cast<uint16_t>(local_v[r.sv[static_cast<size_t>(j) * nC + c]]);
+            }
+            r.tile_a.push_back(make_int4(c0, c1 - c0, halo_begin, nl));
+            r.tile_b.push_back(make_int4(e0, e1, vert_begin, nv));
+            r.max_local_cells = std::max(r.max_local_cells, nl);
+            r.max_local_verts = std::max(r.max_local_verts, nv);
+        }
+    }
+    r.tb[NBANDS] = static_cast<int>(r.tile_a.size());
+    r.ntiles = r.tb[NBANDS];
+    if (ecur != nE) return set_error(LTS_EINVAL, "tiles do not cover the edges");
     return LTS_OK;
 }
 

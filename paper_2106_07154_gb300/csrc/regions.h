@@ -28,7 +28,23 @@ struct RegionsHost {
     std::vector<uint8_t> cn;
     std::vector<int> se, sn, sv, ec0, ec1, vc, ve;
     std::vector<uint32_t> ep;
+    // tiles of the fused kernel (see build_tiles)
+    int tile_cells = 0;
+    int ntiles = 0;
+    int tb[NBANDS + 1];                         // first tile of each band
+    std::vector<int4> tile_a;                   // {cell begin, own cells, halo begin, local cells}
+    std::vector<int4> tile_b;                   // {edge begin, edge end, vert begin, local vertices}
+    std::vector<int> tile_lsv_off;              // [ntiles] start of the tile's lsv block
+    std::vector<int> halo;                      // halo cells of all tiles
+    std::vector<int> tverts;                    // local vertex lists of all tiles
+    std::vector<uint16_t> lsv;                  // per tile, slot-major: local vertex of (slot, local cell)
+    std::vector<uint32_t> lec;                  // [nE] local cells of the owning tile: c0 | c1 << 16
+    int max_local_cells = 0, max_local_verts = 0;
 };
+
+// Tiles of at most `tile_cells` consecutive cells of one band; a tile owns
+// the edges whose lower band-order cell lies in it (a contiguous edge range).
+int build_tiles(const HostMesh& m, RegionsHost& r, int tile_cells);
 
 template <class T>
 struct CoefTables {

@@ -25,8 +25,10 @@ LTS_FP32 = 0
 LTS_FP64 = 1
 LTS_MODE_LTS3 = 0
 LTS_MODE_SSPRK3 = 1
-LTS_NKINDS = 3
-KIND_NAMES = ("vertex", "ring", "edge")
+LTS_NKINDS = 4
+KIND_NAMES = ("vertex", "ring", "edge", "tile")
+PATH_THREE = 0
+PATH_FUSED = 1
 
 NBANDS = 9
 BAND_NAMES = ("F_deep", "F3", "F2", "F1", "I1", "I2", "C1", "C2", "C_rest")
@@ -71,7 +73,7 @@ class lts_params(C.Structure):
     _fields_ = [("g", C.c_double), ("dt", C.c_double), ("precision", C.c_int32),
                 ("mode", C.c_int32), ("compensated", C.c_int32), ("use_graph", C.c_int32),
                 ("block_size", C.c_int32), ("profile", C.c_int32), ("pdl", C.c_int32),
-                ("stream", C.c_void_p)]
+                ("kernel_path", C.c_int32), ("stream", C.c_void_p)]
 
 
 class lts_diag(C.Structure):
@@ -126,6 +128,7 @@ def lib():
             L.lts_regions_destroy.restype = None
             L.lts_regions_labels.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
             L.lts_regions_counts.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+            L.lts_regions_tiling.argtypes = [C.c_void_p, C.c_int32]
             L.lts_regions_permutation.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
             L.lts_state_create.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                            C.POINTER(lts_params), C.POINTER(C.c_void_p)]
@@ -251,6 +254,10 @@ def lts_regions_labels(reg_h, nCells: int, nEdges: int):
     return cl, el
 
 
+def lts_regions_tiling(reg_h, tile_cells: int):
+    _check(lib().lts_regions_tiling(reg_h, int(tile_cells)))
+
+
 def lts_regions_counts(reg_h):
     c = np.zeros(NBANDS, np.int64)
     e = np.zeros(NBANDS, np.int64)
@@ -270,9 +277,9 @@ def lts_regions_permutation(reg_h, nCells: int, nEdges: int, nVertices: int):
 def lts_state_create(mesh_h, reg_h, h0, u0, g: float, dt: float, precision: int = LTS_FP32,
                      mode: int = LTS_MODE_LTS3, compensated: bool = True, use_graph: bool = True,
                      block_size: int = 0, profile: int = 0, stream: int | None = None,
-                     pdl: bool = True):
+                     pdl: bool = True, kernel_path: int = 0):
     p = lts_params(g, dt, precision, mode, int(compensated), int(use_graph), block_size,
-                   int(profile), int(pdl), stream)
+                   int(profile), int(pdl), int(kernel_path), stream)
     h = C.c_void_p()
     _check(lib().lts_state_create(mesh_h, reg_h, _f64(h0).ctypes.data, _f64(u0).ctypes.data,
                                   C.byref(p), C.byref(h)))
@@ -319,15 +326,19 @@ class Model:
     def __init__(self, mesh: dict, fine_mask, M: int, h0, u0, dt: float, g: float = 9.81,
                  precision: int = LTS_FP32, mode: int = LTS_MODE_LTS3, compensated: bool = True,
                  use_graph: bool = True, block_size: int = 0, profile: int = 0,
-                 interface_layers: int = 1, stream: int | None = None, pdl: bool = True):
+                 interface_layers: int = 1, stream: int | None = None, pdl: bool = True,
+                 kernel_path: int = 0, tile_cells: int = 0):
         self.nC = int(mesh["nCells"])
         self.nE = int(mesh["nEdges"])
         self.nV = int(mesh["nVertices"])
         self.mesh_h = self.reg_h = self.state_h = None
         self.mesh_h = lts_mesh_create(mesh)
         self.reg_h = lts_regions_set(self.mesh_h, fine_mask, 3, M, interface_layers)
+        if tile_cells:
+            lts_regions_tiling(self.reg_h, tile_cells)
         self.state_h = lts_state_create(self.mesh_h, self.reg_h, h0, u0, g, dt, precision, mode,
-                                        compensated, use_graph, block_size, profile, stream, pdl)
+                                        compensated, use_graph, block_size, profile, stream, pdl,
+                                        kernel_path)
 
     def step(self, n: int):
         lts_step(self.state_h, n)

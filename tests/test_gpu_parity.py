@@ -37,11 +37,11 @@ def rel(a, b):
 
 
 def run_gpu(w, n, precision, M=None, mode=lts.LTS_MODE_LTS3, dt=None, use_graph=True,
-            compensated=True, fine=None, layers=1, block_size=0, profile=False):
+            compensated=True, fine=None, layers=1, block_size=0, profile=0, kernel_path=0):
     with lts.Model(w.mesh, w.fine_mask if fine is None else fine, M or w.M, w.h0, w.u0,
                    dt or w.dt, w.g, precision=precision, mode=mode, compensated=compensated,
                    use_graph=use_graph, interface_layers=layers, block_size=block_size,
-                   profile=profile) as m:
+                   profile=profile, kernel_path=kernel_path) as m:
         m.step(n)
         h, u, d = m.read()
     return h, u, d
@@ -141,6 +141,17 @@ def test_graph_and_direct_launches_identical(sphw):
     d = run_gpu(sphw, 7, lts.LTS_FP32, profile=2)
     for x in (b, c, d):
         assert np.array_equal(a[0], x[0]) and np.array_equal(a[1], x[1])
+
+
+@pytest.mark.parametrize("precision", [lts.LTS_FP64, lts.LTS_FP32])
+@pytest.mark.parametrize("mode", [lts.LTS_MODE_LTS3, lts.LTS_MODE_SSPRK3])
+def test_fused_tiles_equal_three_launches(sphw, precision, mode):
+    """The fused tile kernel and the three-launch path do the same per-element
+    arithmetic, so they agree bit for bit."""
+    dt = sphw.dt if mode == lts.LTS_MODE_LTS3 else sphw.dt / sphw.M
+    a = run_gpu(sphw, 6, precision, mode=mode, dt=dt, kernel_path=lts.PATH_FUSED)
+    b = run_gpu(sphw, 6, precision, mode=mode, dt=dt, kernel_path=lts.PATH_THREE)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
 
 
 def test_block_size_does_not_change_results(sphw):
