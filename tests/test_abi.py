@@ -1,0 +1,94 @@
+"""The C ABI: liblts.so loads without a GPU and exports every function that
+include/lts.h declares; host-only entry points work without a GPU."""
+import ctypes
+import re
+from pathlib import Path
+
+import numpy as np
+
+from paper_2106_07154_gb300 import lts
+
+HEADER = Path(__file__).resolve().parent.parent / "include" / "lts.h"
+
+
+def declared_functions():
+    text = HEADER.read_text()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*(lts_[a-z0-9_]+)\s*\(", text, re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("lts_mesh_create", "lts_regions_set", "lts_state_create", "lts_step", "lts_read",
+                     "lts_build_scvt", "lts_build_hex_periodic", "lts_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_function():
+    L = ctypes.CDLL(str(lts.LIB_PATH))
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_errors_without_gpu_are_reported_not_raised():
+    mesh = lts.lts_build_hex_periodic(8, 8, 10e3, 1e-4)
+    mh = lts.lts_mesh_create(mesh)
+    rh = lts.lts_regions_set(mh, np.zeros(mesh["nCells"], np.int8), 3, 2)
+    try:
+        # bad arguments are rejected before any device work
+        try:
+            lts.lts_regions_set(mh, np.zeros(mesh["nCells"], np.int8), 2, 2)
+            assert False, "order 2 should be rejected"
+        except lts.LtsError as e:
+            assert e.code == lts.LTS_EINVAL and "order" in str(e)
+        try:
+            lts.lts_regions_set(mh, np.zeros(mesh["nCells"], np.int8), 3, 0)
+            assert False, "M = 0 should be rejected"
+        except lts.LtsError as e:
+            assert e.code == lts.LTS_EINVAL
+    finally:
+        lts.lts_regions_destroy(rh)
+        lts.lts_mesh_destroy(mh)
+
+
+def test_mesh_validation_rejects_clockwise_rings():
+    mesh = lts.lts_build_hex_periodic(8, 8, 10e3, 1e-4)
+    bad = dict(mesh)
+    # reverse the ring of cell 0 (edges, neighbours and vertices)
+    n = int(bad["nEdgesOnCell"][0])
+    for k in ("edgesOnCell", "cellsOnCell"):
+        a = bad[k].copy()
+        a[0, :n] = a[0, :n][::-1]
+        bad[k] = a
+    v = bad["verticesOnCell"].copy()
+    v[0, :n] = np.roll(v[0, :n][::-1], -1)
+    bad["verticesOnCell"] = v
+    try:
+        lts.lts_mesh_create(bad)
+        assert False, "a clockwise ring should be rejected"
+    except lts.LtsError as e:
+        assert e.code == lts.LTS_EINVAL and "counter-clockwise" in str(e)
+
+
+def test_regions_labels_match_band_counts():
+    mesh = lts.lts_build_hex_periodic(16, 16, 10e3, 1e-4)
+    fine = np.zeros(mesh["nCells"], np.int8)
+    fine[:40] = 1
+    mh = lts.lts_mesh_create(mesh)
+    rh = lts.lts_regions_set(mh, fine, 3, 2)
+    try:
+        cl, el = lts.lts_regions_labels(rh, mesh["nCells"], mesh["nEdges"])
+        c, e, v = lts.lts_regions_counts(rh)
+        assert c.sum() == mesh["nCells"] and e.sum() == mesh["nEdges"] and v.sum() == mesh["nVertices"]
+        # label 5 (coarse) = bands C1, C2, C rest; label 3 = I1; 4 = I2
+        assert (cl == 3).sum() == c[4] and (cl == 4).sum() == c[5] and (cl == 5).sum() == c[6:].sum()
+        pc, pe, pv = lts.lts_regions_permutation(rh, mesh["nCells"], mesh["nEdges"], mesh["nVertices"])
+        assert sorted(pc.tolist()) == list(range(mesh["nCells"]))
+        assert sorted(pe.tolist()) == list(range(mesh["nEdges"]))
+        assert sorted(pv.tolist()) == list(range(mesh["nVertices"]))
+        # band order: labels are non-decreasing along the permutation
+        assert np.all(np.diff(np.minimum(cl[pc], 5)) >= 0)
+    finally:
+        lts.lts_regions_destroy(rh)
+        lts.lts_mesh_destroy(mh)
