@@ -234,6 +234,25 @@ int lts_write(lts_state s, const double* h, const double* u, double time, int64_
 int lts_step_stats(lts_state s, int32_t* launches_per_step, double* bytes, double* ms,
                    int32_t* launches_per_kind);
 
+/* Mass and energy of the current state (the FP64 reduction lts_read
+ * performs), for callers that cannot allocate device memory when they need
+ * them, e.g. while a stream is being captured into a CUDA graph, or when
+ * device memory comes from a pool that must not grow.  The paper has no
+ * counterpart; this is an interface convenience.
+ *   d_out: device memory owned by the caller, 2 doubles: {mass, energy}.
+ * Allocates nothing: the per-block partial sums live in one fixed device
+ * array of 4096 x 2 doubles (64 KiB) inside liblts.so, which every GPU that
+ * loads the library keeps until the process exits; meshes of more than
+ * 4096 * 256 = 1,048,576 cells are rejected with LTS_EINVAL.  The first call
+ * on a device looks the array's address up (cudaGetSymbolAddress), so make
+ * that first call before any stream capture.  Enqueued on the state's
+ * stream, no synchronisation.  All calls share the array, and every call
+ * overwrites the partial sums it reads, so calls that overlap on the GPU
+ * (different streams, unordered) race and must not be issued.
+ * Errors: LTS_EINVAL (null argument, mesh too large, state on another
+ * device), LTS_ECUDA. */
+int lts_diagnostics_noalloc(lts_state s, double* d_out);
+
 const char* lts_last_error(void);
 
 #ifdef __cplusplus

@@ -1261,6 +1261,28 @@ int lts_write(lts_state s, const double* h, const double* u, double time, int64_
     return LTS_OK;
 }
 
+}  // extern "C"
+
+namespace lts {
+int state_view(lts_state s, StateView* v) {
+    if (!s || !v) return set_error(LTS_EINVAL, "null argument");
+    const SV& X = s->buf[s->parity];
+    v->kc = s->kc;
+    v->tables = s->tables;
+    v->h_hi = X.hh;
+    v->h_lo = X.hl;
+    v->u_hi = X.uh;
+    v->u_lo = X.ul;
+    v->g = s->p.g;
+    v->nC = s->reg->mesh->m.nC;
+    v->device = s->reg->device;
+    v->stream = s->stream;
+    return LTS_OK;
+}
+}  // namespace lts
+
+extern "C" {
+
 int lts_step_stats(lts_state s, int32_t* launches_per_step, double* bytes, double* ms,
                    int32_t* launches_per_kind) {
     if (!s) return set_error(LTS_EINVAL, "null state");

@@ -135,6 +135,18 @@ cudaError_t launch_diagnostics(const KernelConfig& kc, const void* tables, const
                                const void* h_lo, const void* u_hi, const void* u_lo, double g,
                                double* partial, int nblocks, double* out2, cudaStream_t s);
 int kernel_registers(const KernelConfig& kc, int kind);
+
+// Device view of a state's current solution, for entry points defined in
+// other translation units (lts_api.cpp fills it).
+struct StateView {
+    KernelConfig kc;
+    const void* tables;
+    const void *h_hi, *h_lo, *u_hi, *u_lo;
+    double g;
+    int nC;
+    int device;
+    cudaStream_t stream;
+};
 constexpr int NKINDS = 4;
 
 }  // namespace lts

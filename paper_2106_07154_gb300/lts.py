@@ -139,6 +139,7 @@ def lib():
             L.lts_write.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int64]
             L.lts_step_stats.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                          C.c_void_p]
+            L.lts_diagnostics_noalloc.argtypes = [C.c_void_p, C.c_void_p]
         _lib = L
     return _lib
 
@@ -318,6 +319,12 @@ def lts_step_stats(state_h):
     _check(lib().lts_step_stats(state_h, C.byref(n), b.ctypes.data, ms.ctypes.data, k.ctypes.data))
     return {"launches": int(n.value), "bytes": b.tolist(), "ms": ms.tolist(),
             "launches_per_kind": k.tolist()}
+
+
+def lts_diagnostics_noalloc(state_h, d_out_ptr: int):
+    """Enqueues mass and energy of the current state into caller-owned device
+    memory (2 doubles at d_out_ptr) without allocating; see include/lts.h."""
+    _check(lib().lts_diagnostics_noalloc(state_h, C.c_void_p(int(d_out_ptr))))
 
 
 class Model:
