@@ -10,6 +10,12 @@ events on the state's stream over exactly K steps after W warm-up steps,
 max over ranks.  Under torchrun every rank advances its own replica (the path
 has no exchange step on one GPU), so the aggregate is weak scaling.
 
+--workload ensemble64 times the batched ensemble instead: 64 uneven
+spherical SCVT members (2,562 to 163,842 cells, ratios and M in {2, 4, 8})
+advanced together, one launch per phase for all members; under torchrun the
+members are partitioned over the ranks (strong scaling, no collective on
+the data path).
+
 --impl reference times the FP64 CPU oracle (the reference arm of this
 build) on the host cores on a bounded sample of the same workload.
 """
@@ -52,6 +58,9 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip e2e/roofline/baselines")
     ap.add_argument("--no-graph", action="store_true", help="direct launches instead of the graph")
     ap.add_argument("--no-pdl", action="store_true", help="no programmatic dependent launch")
+    ap.add_argument("--autotune", type=int, default=0,
+                    help="time the run with the configuration the library's autotuner picks "
+                         "(coarse steps per candidate; 0 = library defaults)")
     return ap.parse_args()
 
 
@@ -182,6 +191,8 @@ def run_reference(args):
         return 0
     from paper_2106_07154_gb300 import workloads as W
 
+    if args.workload == "ensemble64":
+        return run_reference_ensemble(args)
     w = W.workload(args.workload)
     import oracle
 
@@ -212,6 +223,40 @@ def run_reference(args):
             "config": workload_config(w, "fp64-oracle"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample, "cpu": cpu_model()},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_reference_ensemble(args):
+    """The oracle on the ensemble's members in order, one coarse step each,
+    until 90 s of oracle time (the members' meshes are built untimed)."""
+    import oracle
+    from paper_2106_07154_gb300 import workloads as W
+
+    recipes = W.ensemble_recipes()
+    cells, t_or, done = 0, 0.0, 0
+    for r in recipes:
+        w = W.sphere_cap(**r)
+        o = oracle.Oracle(w.mesh)
+        cl, el = o.regions(w.fine_mask)
+        t0 = time.perf_counter()
+        o.lts3(w.h0, w.u0, cl, el, w.M, w.dt, 1, g=w.g)
+        t_or += time.perf_counter() - t0
+        cells += w.nCells
+        done += 1
+        if t_or > 90.0:
+            break
+    value = cells / t_or
+    cfg = ensemble_config(recipes, recipes, 1)
+    cfg["nCells_total"] = sum(r["n"] for r in recipes)
+    sample = f"one LTS3 coarse step of the first {done} members ({cells} cells) by the FP64 C oracle"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+            "steps": 1, "warmup": 0, "ms_per_step": 1e3 * t_or * cfg["nCells_total"] / cells,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
+                             "kind": "oracle", "sample": sample, "cpu": cpu_model()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -249,9 +294,10 @@ def run_lts(args):
         torch.distributed.barrier()
     prec = lts.LTS_FP32 if args.precision == "fp32" else lts.LTS_FP64
     stream = torch.cuda.Stream()
+    tune = args.autotune if (args.autotune and not args.no_graph and not args.no_pdl) else 0
     model = lts.Model(w.mesh, w.fine_mask, w.M, w.h0, w.u0, w.dt, w.g, precision=prec,
                       compensated=True, use_graph=not args.no_graph, stream=stream.cuda_stream,
-                      pdl=not args.no_pdl)
+                      pdl=not args.no_pdl, autotune=tune, tune_ordering=bool(tune))
     stats = model.stats()
     model.step(args.warmup)
     torch.cuda.synchronize()
@@ -278,6 +324,8 @@ def run_lts(args):
     value = world * w.nCells * args.steps / (ms * 1e-3)
     launch_cfg = ("direct launches" if args.no_graph else "one CUDA graph per coarse step") + \
         ("" if args.no_pdl else ", programmatic dependent launch")
+    if model.tuned:
+        launch_cfg += ", configuration chosen by the library's autotuner"
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
@@ -285,6 +333,8 @@ def run_lts(args):
             "config": workload_config(w, args.precision + ("+compensation" if prec == 0 else "")),
             "gpu_launches": stats["launches"] * args.steps, "clocks": clk, "launch": launch_cfg,
             "sim_seconds_per_wall_second": w.dt * args.steps / (ms * 1e-3)}
+    if model.tuned:
+        line["config"]["tuned"] = model.tuned
     if not args.no_extras and rank == 0:
         line.update(extras(args, w, model, stats, stream, h_gpu, u_gpu, diag))
     model.close()
@@ -322,8 +372,12 @@ def extras(args, w, model, stats, stream, h_gpu, u_gpu, diag):
                           "mass/energy), pinned host buffers, wall clock"}
     # ---- per-kernel timing: the same coarse-step graph with an event-record
     #      node before and after every kernel node, on the state's stream
+    tuned = model.tuned or {}
+    knobs = {k: tuned[k] for k in ("block_size", "kernel_path", "l2_hints", "serial_step4") if k in tuned}
+    if "ordering" in tuned:
+        knobs["ordering"] = tuned["ordering"]
     prof = lts.Model(w.mesh, w.fine_mask, w.M, w.h0, w.u0, w.dt, w.g, precision=prec,
-                     compensated=True, profile=2, stream=stream.cuda_stream)
+                     compensated=True, profile=2, stream=stream.cuda_stream, **knobs)
     nprof = 20
     prof.step(2)
     ms_sum = np.zeros(lts.LTS_NKINDS)
@@ -332,10 +386,22 @@ def extras(args, w, model, stats, stream, h_gpu, u_gpu, diag):
         ms_sum += np.array(prof.stats()["ms"])
     prof.close()
     ms_kind = ms_sum / nprof
+    # the same launches issued directly on the stream with an event pair
+    # around each (no graph, no programmatic overlap)
+    prof1 = lts.Model(w.mesh, w.fine_mask, w.M, w.h0, w.u0, w.dt, w.g, precision=prec,
+                      compensated=True, profile=1, stream=stream.cuda_stream, **knobs)
+    prof1.step(2)
+    ms1 = np.zeros(lts.LTS_NKINDS)
+    for _ in range(nprof):
+        prof1.step(1)
+        ms1 += np.array(prof1.stats()["ms"])
+    prof1.close()
+    ms1 /= nprof
     bytes_kind = np.array(stats["bytes"])
     launches_kind = np.array(stats["launches_per_kind"])
-    gbs = bytes_kind / (ms_kind * 1e-3) / 1e9
-    dom = int(np.argmax(ms_kind))
+    has = launches_kind > 0
+    gbs = np.where(has, bytes_kind / np.maximum(ms_kind, 1e-12) / 1e6, 0.0)
+    dom = int(np.argmax(np.where(has, ms_kind, -1.0)))
     peak, peak_src = hbm_peak()
     traffic = dram_traffic_per_launch() if dom == 1 else None
     out["roofline"] = {
@@ -348,8 +414,24 @@ def extras(args, w, model, stats, stream, h_gpu, u_gpu, diag):
         "per_kind": {lts.KIND_NAMES[k]: {"ms_per_step": float(ms_kind[k]),
                                           "bytes_per_step": float(bytes_kind[k]),
                                           "launches_per_step": int(launches_kind[k]),
-                                          "GB_per_s": float(gbs[k])} for k in range(lts.LTS_NKINDS)},
+                                          "GB_per_s": float(gbs[k])}
+                     for k in range(lts.LTS_NKINDS) if has[k]},
+        "timing": "per-kernel CUDA events: an event-record node before and after every kernel "
+                  "node of the coarse-step graph (20 steps after the timed region)",
+        "per_kind_direct_launch_events": {
+            lts.KIND_NAMES[k]: {"ms_per_step": float(ms1[k]),
+                                "GB_per_s": float(bytes_kind[k] / (ms1[k] * 1e-3) / 1e9) if ms1[k] > 0 else None}
+            for k in range(lts.LTS_NKINDS) if has[k]},
     }
+    # ---- the library's autotuner on this workload (report only)
+    if not model.tuned:
+        base = lts.make_params(w.g, w.dt, prec, lts.LTS_MODE_LTS3, True, True)
+        mh = lts.lts_mesh_create(w.mesh)
+        rh = lts.lts_regions_set(mh, w.fine_mask, 3, w.M)
+        best, rep = lts.lts_autotune(mh, rh, w.h0, w.u0, base, 20, tune_ordering=True)
+        lts.lts_regions_destroy(rh)
+        lts.lts_mesh_destroy(mh)
+        out["autotune"] = dict(lts.params_dict(best), **rep)
     # ---- the GPU's own FP64 global SSP-RK3 at the fine step (same simulated time)
     ref = lts.Model(w.mesh, w.fine_mask, w.M, w.h0, w.u0, w.dt / w.M, w.g, precision=lts.LTS_FP64,
                     mode=lts.LTS_MODE_SSPRK3, stream=stream.cuda_stream)
@@ -385,10 +467,166 @@ def extras(args, w, model, stats, stream, h_gpu, u_gpu, diag):
     return out
 
 
+# ------------------------------------------------------------------ ensemble
+
+def ensemble_config(recipes, mine, world):
+    return {"workload": f"ensemble64: {len(recipes)} spherical SCVT members, "
+                        f"{min(r['n'] for r in recipes)}..{max(r['n'] for r in recipes)} cells, "
+                        "ratio = M in {2,4,8}, 200 Lloyd iterations, one launch per phase",
+            "members": len(recipes), "members_rank0": len(mine),
+            "nCells_total": None, "precision": "fp32+compensation",
+            "l2": "inputs larger than L2 (each coarse step streams every member's mesh)",
+            "parallelism": f"members partitioned over {world} rank(s)" if world > 1 else "1 GPU"}
+
+
+def run_ensemble(args):
+    import torch
+    from paper_2106_07154_gb300 import lts, shard
+    from paper_2106_07154_gb300 import workloads as W
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU for --impl lts")
+    torch.cuda.set_device(local)
+    recipes = W.ensemble_recipes()
+    weights = [r["n"] * r["M"] for r in recipes]
+    parts = shard.greedy_partition(weights, world)
+    mine = parts[rank]
+    ws = [W.sphere_cap(**recipes[i]) for i in mine]
+    cells_all = None
+    stream = torch.cuda.Stream()
+    models = [lts.Model(w.mesh, w.fine_mask, w.M, w.h0, w.u0, w.dt, w.g, precision=lts.LTS_FP32,
+                        compensated=True) for w in ws]
+    ens = lts.Ensemble(models, stream=stream.cuda_stream)
+    st = ens.stats()
+    my_cells = st["cells"]
+    if world > 1:
+        t = torch.tensor([my_cells], dtype=torch.int64, device="cuda")
+        torch.distributed.all_reduce(t)
+        cells_all = int(t.item())
+    else:
+        cells_all = my_cells
+    ens.step(args.warmup)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    e0.record(stream)
+    ens.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        torch.distributed.barrier()
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    cfg = ensemble_config(recipes, mine, world)
+    cfg["nCells_total"] = cells_all
+    peak, peak_src = hbm_peak()
+    bytes_step = float(sum(st["bytes"]))
+    line = {"metric": METRIC, "value": cells_all * args.steps / (ms * 1e-3), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "strong" if world > 1 else "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": cfg,
+            "gpu_launches": st["launches"] * args.steps, "clocks": clk,
+            "launch": "one CUDA graph per ensemble coarse step, persistent segment-table kernels, "
+                      "programmatic dependent launch",
+            "segments_per_step": st["segments"]}
+    if rank == 0 and not args.no_extras:
+        achieved = bytes_step / (ms / args.steps * 1e-3) / 1e9
+        line["roofline"] = {"bound": "hbm", "kernel": "whole ensemble step (all kinds)",
+                            "achieved": achieved, "peak": peak, "unit": "GB/s",
+                            "frac": achieved / peak, "traffic": None,
+                            "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
+                            "algorithmic_bytes_per_step": bytes_step}
+        # the same members as separate states, one after another on one stream
+        sep = [lts.Model(w.mesh, w.fine_mask, w.M, w.h0, w.u0, w.dt, w.g, precision=lts.LTS_FP32,
+                         compensated=True, stream=stream.cuda_stream) for w in ws]
+        nsep = max(3, min(50, args.steps // 10))
+        for m in sep:
+            m.step(2)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(nsep):
+            for m in sep:
+                m.step(1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sep_ms = e0.elapsed_time(e1) / nsep
+        for m in sep:
+            m.close()
+        line["separate_states"] = {"ms_per_step": sep_ms,
+                                   "value": my_cells / (sep_ms * 1e-3),
+                                   "note": "each member its own state and graph, stepped one "
+                                           "after another on the same stream"}
+        # end to end: every member written from and read back to pinned host memory
+        n_e2e = 5
+        bufs = []
+        for w in ws:
+            hb = torch.empty(w.nCells, dtype=torch.float64, pin_memory=True).numpy()
+            ub = torch.empty(int(w.mesh["nEdges"]), dtype=torch.float64, pin_memory=True).numpy()
+            hb[:] = w.h0
+            ub[:] = w.u0
+            bufs.append((hb, ub))
+        h2d = sum(8 * (b[0].size + b[1].size) for b in bufs)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            for i, (hb, ub) in enumerate(bufs):
+                ens.write(i, hb, ub)
+            ens.step(1)
+            for i, (hb, ub) in enumerate(bufs):
+                ens.read(i, hb, ub)
+        e2e_s = time.perf_counter() - t0
+        line["e2e"] = {"value": my_cells * n_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                       "d2h_bytes_per_step": h2d + 36 * len(bufs), "steps": n_e2e,
+                       "note": "per step: lts_ensemble_write of every member, one ensemble step, "
+                               "lts_ensemble_read of every member (pinned host buffers, wall clock)"}
+        # CPU baseline: the oracle on the two smallest members, one coarse step each
+        import oracle
+
+        small = sorted(range(len(ws)), key=lambda i: ws[i].nCells)[:2]
+        t0 = time.perf_counter()
+        cells = 0
+        for i in small:
+            w = ws[i]
+            o = oracle.Oracle(w.mesh)
+            cl, el = o.regions(w.fine_mask)
+            o.lts3(w.h0, w.u0, cl, el, w.M, w.dt, 1, g=w.g)
+            cells += w.nCells
+        t_or = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": cells / t_or, "unit": UNIT, "cores": oracle.num_threads(),
+                                "kind": "oracle", "cpu": cpu_model(),
+                                "sample": f"one LTS3 coarse step of the two smallest members "
+                                          f"({cells} cells) by the FP64 C oracle ({t_or:.1f} s)"}
+    ens.close()
+    for m in models:
+        m.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "ensemble64":
+        return run_ensemble(args)
     return run_lts(args)
 
 

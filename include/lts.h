@@ -138,13 +138,14 @@ void lts_mesh_destroy(lts_mesh m);
  * band; an edge takes the smaller band of its two cells (the fine-to-coarse
  * assignment of Eq. (5)), a vertex the smallest band of its three cells.
  * Every restricted phase then reads and writes contiguous index ranges.
- * Uploads the band-ordered device tables (FP64 master geometry, FP32/FP64
- * coefficient copies derived in FP64 and rounded once).
+ * Host only: the first lts_state_create of each precision uploads the
+ * band-ordered device tables (FP64 master geometry, FP32/FP64 coefficient
+ * copies derived in FP64 and rounded once).
  *   order:            3 (LTS3); other values -> LTS_EINVAL.
  *   M:                fine substeps per coarse step, >= 1.
  *   interface_layers: cells per interface layer (>= 1): I1 = cells at
  *                     edge-distance 1..L from F, I2 = distance L+1..2L.
- * Needs a CUDA device.  Errors: LTS_EINVAL, LTS_ENOMEM, LTS_ECUDA, LTS_ENODEV. */
+ * Errors: LTS_EINVAL, LTS_ENOMEM. */
 int lts_regions_set(lts_mesh m, const int8_t* fine_mask, int32_t order, int32_t M,
                     int32_t interface_layers, lts_regions* out);
 void lts_regions_destroy(lts_regions r);
@@ -159,6 +160,19 @@ int lts_regions_labels(lts_regions r, int8_t* cell_label, int8_t* edge_label);
  * most tile_cells consecutive band-order cells (32..4096; default 256).
  * Only while no state uses the regions.  Errors: LTS_EINVAL. */
 int lts_regions_tiling(lts_regions r, int32_t tile_cells);
+
+/* Order of the cells inside each band (the bands themselves are fixed):
+ *   LTS_ORDER_HILBERT (default): along a Hilbert curve through the cell
+ *     centres, so neighbours sit close in memory;
+ *   LTS_ORDER_INDEX: the mesh's own index order (the naive layout, for
+ *     comparison).
+ * Edges and vertices follow their cells.  Only while no state uses the
+ * regions.  Every element's arithmetic is the same in either order, so
+ * results are identical; only the memory access pattern changes.
+ * Errors: LTS_EINVAL, LTS_ENOMEM. */
+#define LTS_ORDER_HILBERT 0
+#define LTS_ORDER_INDEX   1
+int lts_regions_ordering(lts_regions r, int32_t ordering);
 
 /* Number of cells, edges and vertices per band (arrays of 9). */
 int lts_regions_counts(lts_regions r, int64_t* cells, int64_t* edges, int64_t* vertices);
@@ -191,6 +205,10 @@ typedef struct lts_params {
                                ring, edge; default); 1: one fused tile kernel per
                                right-hand side (shared-memory staging per tile)        */
     void* stream;           /* cudaStream_t to enqueue on; NULL = a library stream     */
+    int32_t no_l2_hints;    /* 1: table loads without L2 eviction priorities (default:
+                               keep the fine region, stream the coarse one)            */
+    int32_t serial_step4;   /* 1: Step 4 on the far coarse band after Step 3 instead of
+                               as a concurrent branch (results are identical)          */
 } lts_params;
 
 /* Allocates the device state (band order) and uploads (h0, u0), given in the
@@ -205,6 +223,31 @@ void lts_state_destroy(lts_state s);
 /* Enqueues n_coarse coarse steps (LTS3) or steps (SSPRK3) on the state's
  * stream.  Asynchronous: returns after enqueueing.  n_coarse >= 0. */
 int lts_step(lts_state s, int32_t n_coarse);
+
+/* Autotuner: times candidate launch configurations of one coarse step on
+ * scratch states built from (m, r, h0, u0) and *base, and returns the
+ * fastest as *best (base's g, dt, precision, mode, compensation and stream
+ * kept; use_graph = 1).  Candidates: block_size 128 or 256, kernel_path 0
+ * or 1, pdl on or off, L2 hints on or off, Step 4 concurrent or serial
+ * (LTS3).  Each is timed over `steps` coarse steps after 3 warm-up steps;
+ * the three fastest are timed twice more and the best of three wins.  With
+ * flags & LTS_TUNE_ORDERING and no state using r, the other cell ordering
+ * (lts_regions_ordering) is tried with the winner and r keeps the faster.
+ * No configuration changes a result bit; the tuner only chooses speed.  The
+ * paper has no counterpart (it runs with MPI defaults).  Needs a CUDA
+ * device; synchronises.  rep may be NULL.
+ * Errors: LTS_EINVAL (bad arguments, nothing buildable), LTS_ENOMEM,
+ * LTS_ECUDA. */
+#define LTS_TUNE_ORDERING 1
+typedef struct lts_tune_report {
+    int32_t candidates;     /* configurations timed                              */
+    int32_t ordering;       /* cell ordering r has afterwards (LTS_ORDER_*)      */
+    double best_ms;         /* ms per coarse step of *best                       */
+    double default_ms;      /* ms per coarse step of the library defaults        */
+} lts_tune_report;
+int lts_autotune(lts_mesh m, lts_regions r, const double* h0, const double* u0,
+                 const lts_params* base, int32_t steps, int32_t flags, lts_params* best,
+                 lts_tune_report* rep);
 
 typedef struct lts_diag {
     double mass;            /* sum_i A_i h_i (FP64 reduction of the FP64 or FP32+compensation state) */
@@ -252,6 +295,62 @@ int lts_step_stats(lts_state s, int32_t* launches_per_step, double* bytes, doubl
  * Errors: LTS_EINVAL (null argument, mesh too large, state on another
  * device), LTS_ECUDA. */
 int lts_diagnostics_noalloc(lts_state s, double* d_out);
+
+/* ------------------------------------------------------------------------
+ * Ensembles: several independent states (each its own mesh, regions, M and
+ * dt) advanced together, one launch per phase of the coarse step for all
+ * members (the phases of Algorithm 2.2, or of 2.1 for SSPRK3 members).
+ * The paper runs one mesh per job; batching independent meshes is an
+ * interface of this library.  The members' tables and states are copied
+ * into one packed index space; each launch carries the segments (band
+ * ranges) of every member in a device table walked by a persistent grid,
+ * and a member with a smaller M has no segments in the later substeps.
+ * Every member's cells see the same arithmetic as its stand-alone
+ * lts_step, so results equal the members' own steps bit for bit.
+ * ------------------------------------------------------------------------ */
+typedef struct lts_ensemble_s* lts_ensemble;
+
+typedef struct lts_ensemble_params {
+    int32_t use_graph;      /* 1: capture one ensemble coarse step as a CUDA graph     */
+    int32_t pdl;            /* 1: programmatic dependent launch between launches       */
+    int32_t persistent;     /* 1: grid = resident blocks (persistent, default);
+                               0: one block per 256-element piece of a segment         */
+    void* stream;           /* cudaStream_t to enqueue on; NULL = a library stream     */
+} lts_ensemble_params;
+
+/* Builds an ensemble of n >= 1 distinct states that live on the current
+ * device and share precision, compensation, mode, g, block size and
+ * kernel_path 0.  Copies each member's current state in (the members'
+ * streams are synchronised first).  p may be NULL (graph, PDL, persistent).
+ * The members must outlive the ensemble and must not be stepped, written
+ * or destroyed while it exists; lts_ensemble_read brings a member's own
+ * state up to date.  Needs at most 2^31 - 1 cells x maxEdges in total.
+ * Errors: LTS_EINVAL, LTS_ENOMEM, LTS_ECUDA, LTS_ENODEV. */
+int lts_ensemble_create(const lts_state* members, int32_t n, const lts_ensemble_params* p,
+                        lts_ensemble* out);
+void lts_ensemble_destroy(lts_ensemble e);
+
+/* Enqueues n_coarse coarse steps of every member (each with its own dt and
+ * M) on the ensemble's stream; asynchronous.  n_coarse >= 0. */
+int lts_ensemble_step(lts_ensemble e, int32_t n_coarse);
+
+/* Copies member i's packed state into the member (its clock advanced by
+ * the ensemble's steps), then behaves as lts_read on that member.  Returns
+ * LTS_ENONFINITE if any member produced a thickness <= 0 or a non-finite
+ * value since the last ensemble read (the flag is shared by all members). */
+int lts_ensemble_read(lts_ensemble e, int32_t i, double* h, double* u, lts_diag* d);
+
+/* Replaces member i's state (original order, FP64 host arrays, as
+ * lts_write) inside the ensemble, e.g. to restart one member; `time` and
+ * `steps` set that member's clock.  Synchronises the member's stream. */
+int lts_ensemble_write(lts_ensemble e, int32_t i, const double* h, const double* u, double time,
+                       int64_t steps);
+
+/* Launches and segment records per ensemble coarse step, algorithmic bytes
+ * per launch kind (array of LTS_NKINDS, summed over members), and the total
+ * number of cells.  Any pointer may be NULL. */
+int lts_ensemble_stats(lts_ensemble e, int32_t* launches_per_step, double* bytes, int64_t* cells,
+                       int32_t* segments_per_step);
 
 const char* lts_last_error(void);
 

@@ -1,0 +1,142 @@
+// autotune.cpp -- chooses the launch configuration of the coarse step by
+// timing candidates on scratch states of the caller's mesh, regions and
+// initial state.
+//
+// Knobs: threads per block, the kernel path (three launches per right-hand
+// side or fused tiles), programmatic dependent launch, the L2
+// eviction-priority hints, whether Step 4 on the far coarse band runs as a
+// concurrent branch, and (optionally) the cell ordering inside the bands.
+// None of them changes a result bit (each element's arithmetic is the same
+// in every configuration), so the choice is purely a matter of time.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "../../include/lts.h"
+#include "lts_error.h"
+#include "lts_internal.h"
+#include "lts_objects.h"
+
+using namespace lts;
+
+namespace {
+
+struct Candidate {
+    int block, path, pdl, no_l2, serial;
+    double ms = INFINITY;
+};
+
+lts_params apply(const lts_params& base, const Candidate& c) {
+    lts_params p = base;
+    p.block_size = c.block;
+    p.kernel_path = c.path;
+    p.pdl = c.pdl;
+    p.no_l2_hints = c.no_l2;
+    p.serial_step4 = c.serial;
+    p.use_graph = 1;
+    p.profile = 0;
+    p.stream = nullptr;
+    return p;
+}
+
+// Milliseconds per coarse step of one configuration (3 warm-up steps, then
+// `steps` steps between two events on the state's stream); INFINITY when the
+// configuration cannot be built for this mesh (e.g. tiles that do not fit).
+int time_config(lts_mesh m, lts_regions r, const double* h0, const double* u0, const lts_params& p,
+                int steps, double* ms) {
+    *ms = INFINITY;
+    lts_state s = nullptr;
+    int rc = lts_state_create(m, r, h0, u0, &p, &s);
+    if (rc == LTS_EINVAL) return LTS_OK;   // not available for this mesh: skipped
+    if (rc != LTS_OK) return rc;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t err = cudaEventCreate(&e0);
+    if (err == cudaSuccess) err = cudaEventCreate(&e1);
+    if (err == cudaSuccess) {
+        rc = lts_step(s, 3);
+        if (rc == LTS_OK) err = cudaEventRecord(e0, s->stream);
+        if (rc == LTS_OK && err == cudaSuccess) rc = lts_step(s, steps);
+        if (rc == LTS_OK && err == cudaSuccess) err = cudaEventRecord(e1, s->stream);
+        if (rc == LTS_OK && err == cudaSuccess) err = cudaEventSynchronize(e1);
+        float t = 0.f;
+        if (rc == LTS_OK && err == cudaSuccess) err = cudaEventElapsedTime(&t, e0, e1);
+        if (rc == LTS_OK && err == cudaSuccess) *ms = t / steps;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    lts_state_destroy(s);
+    if (rc != LTS_OK) return rc;
+    if (err != cudaSuccess) return set_error(LTS_ECUDA, "autotune timing: %s", cudaGetErrorString(err));
+    return LTS_OK;
+}
+
+}  // namespace
+
+extern "C" int lts_autotune(lts_mesh m, lts_regions r, const double* h0, const double* u0,
+                            const lts_params* base, int32_t steps, int32_t flags, lts_params* best,
+                            lts_tune_report* rep) {
+    if (!m || !r || !h0 || !u0 || !base || !best) return set_error(LTS_EINVAL, "null argument");
+    if (steps < 1 || steps > 100000) return set_error(LTS_EINVAL, "steps must be in [1, 100000]");
+    std::vector<Candidate> cands;
+    const bool lts3 = base->mode == LTS_MODE_LTS3;
+    for (int path = 0; path <= 1; ++path)
+        for (int block : {128, 256}) {
+            if (path == 1 && block != 256) continue;   // one block per 256-cell tile
+            for (int pdl = 1; pdl >= 0; --pdl)
+                for (int no_l2 = 0; no_l2 <= 1; ++no_l2)
+                    for (int serial = 0; serial <= (lts3 ? 1 : 0); ++serial)
+                        cands.push_back({block, path, pdl, no_l2, serial});
+        }
+    // every candidate once, then the three fastest twice more (best of three)
+    for (Candidate& c : cands) {
+        int rc = time_config(m, r, h0, u0, apply(*base, c), steps, &c.ms);
+        if (rc != LTS_OK) return rc;
+    }
+    std::vector<size_t> order(cands.size());
+    for (size_t k = 0; k < order.size(); ++k) order[k] = k;
+    std::sort(order.begin(), order.end(), [&](size_t a, size_t b) { return cands[a].ms < cands[b].ms; });
+    const size_t top = std::min<size_t>(3, order.size());
+    for (int rep_k = 0; rep_k < 2; ++rep_k)
+        for (size_t k = 0; k < top; ++k) {
+            Candidate& c = cands[order[k]];
+            double ms = INFINITY;
+            int rc = time_config(m, r, h0, u0, apply(*base, c), steps, &ms);
+            if (rc != LTS_OK) return rc;
+            c.ms = std::min(c.ms, ms);
+        }
+    const Candidate* win = &cands[order[0]];
+    for (size_t k = 0; k < top; ++k)
+        if (cands[order[k]].ms < win->ms) win = &cands[order[k]];
+    if (!std::isfinite(win->ms)) return set_error(LTS_EINVAL, "no configuration could be built");
+    double default_ms = INFINITY;
+    for (const Candidate& c : cands)
+        if (c.block == 256 && c.path == 0 && c.pdl == 1 && c.no_l2 == 0 && c.serial == 0) default_ms = c.ms;
+    *best = apply(*base, *win);
+    best->stream = base->stream;
+    double best_ms = win->ms;
+    int ordering = r->r.ordering, tried_orderings = 1;
+    if ((flags & LTS_TUNE_ORDERING) && r->ref.load() == 1) {
+        // the other cell ordering with the winning launch configuration
+        const int other = 1 - ordering;
+        int rc = lts_regions_ordering(r, other);
+        if (rc != LTS_OK) return rc;
+        double ms = INFINITY;
+        rc = time_config(m, r, h0, u0, apply(*base, *win), steps, &ms);
+        if (rc != LTS_OK) return rc;
+        tried_orderings = 2;
+        if (ms < best_ms) {
+            best_ms = ms;
+            ordering = other;
+        } else {
+            rc = lts_regions_ordering(r, ordering);
+            if (rc != LTS_OK) return rc;
+        }
+    }
+    if (rep) {
+        rep->candidates = static_cast<int32_t>(cands.size()) + (tried_orderings - 1);
+        rep->best_ms = best_ms;
+        rep->default_ms = default_ms;
+        rep->ordering = ordering;
+    }
+    return LTS_OK;
+}

@@ -17,7 +17,10 @@
 // Step 5) ride in these launches.  Every restricted phase is a set of
 // contiguous band ranges; the path is a sparse gather stencil, so no tensor
 // cores are used.
+#include <algorithm>
 #include <cstdint>
+#include <cstring>
+#include <vector>
 
 #include "lts_internal.h"
 
@@ -47,6 +50,10 @@ struct DevArgs {
     int* flag;
     int l2;           // 0 no hint, 1 keep in L2 (evict_last), 2 stream (evict_first)
     int smem;         // dynamic shared memory of the launch (fused tiles)
+    // segment-table launches (ensembles): segments in device memory
+    const DevSeg<T>* gseg;
+    int ngseg;
+    int vblocks;      // virtual blocks over all segments
 };
 
 // ------------------------------------------------------------- L2 residency
@@ -629,13 +636,11 @@ __device__ __forceinline__ bool is_ring(int type) {
     return type == SEG_RING || type == SEG_RING_UPD || type == SEG_RING_ACC;
 }
 
+// The work of (virtual) block `vblk` of segment s.
 template <class T, bool COMP, int MAXR, int KIND>
-__global__ void __launch_bounds__(256) kernel_phase(const __grid_constant__ DevArgs<T> a) {
-    griddep_launch_dependents();
-    const int sidx = find_seg(a, blockIdx.x);
-    const DevSeg<T>& s = a.seg[sidx];
+__device__ __forceinline__ void phase_block(const DevArgs<T>& a, const DevSeg<T>& s, int vblk) {
     const int type = s.type;
-    const int local = (blockIdx.x - s.block0) * blockDim.x + threadIdx.x;
+    const int local = (vblk - s.block0) * blockDim.x + threadIdx.x;
     const int i = s.begin + local;
     if (i >= s.end) return;
     if (KIND == 0 && type == SEG_VERT) {
@@ -650,6 +655,35 @@ __global__ void __launch_bounds__(256) kernel_phase(const __grid_constant__ DevA
         griddep_wait();
         pointwise<T, COMP>(s, i);
     }
+}
+
+template <class T, bool COMP, int MAXR, int KIND>
+__global__ void __launch_bounds__(256) kernel_phase(const __grid_constant__ DevArgs<T> a) {
+    griddep_launch_dependents();
+    const int sidx = find_seg(a, blockIdx.x);
+    phase_block<T, COMP, MAXR, KIND>(a, a.seg[sidx], blockIdx.x);
+}
+
+// Segment-table variant (ensembles of meshes: one launch carries the
+// segments of every member, more than fit in the kernel parameters).  A
+// persistent grid walks the virtual blocks; each finds its segment by a
+// binary search over the segments' first virtual block.
+template <class T>
+__device__ __forceinline__ int find_gseg(const DevArgs<T>& a, int vblk) {
+    int lo = 0, hi = a.ngseg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.gseg[mid].block0 <= vblk) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <class T, bool COMP, int MAXR, int KIND>
+__global__ void __launch_bounds__(256) kernel_phase_table(const __grid_constant__ DevArgs<T> a) {
+    griddep_launch_dependents();
+    for (int vb = blockIdx.x; vb < a.vblocks; vb += gridDim.x)
+        phase_block<T, COMP, MAXR, KIND>(a, a.gseg[find_gseg(a, vb)], vb);
 }
 
 template <class K, class A>
@@ -668,10 +702,33 @@ cudaError_t launch_kernel(K kernel, int blocks, int block, bool pdl, cudaStream_
     return cudaLaunchKernelEx(&cfg, kernel, a);
 }
 
-template <class T, bool COMP, int MAXR>
-cudaError_t launch_t(const LaunchDesc& d, const void* tables, int block, bool pdl, int smem, int* flag,
-                     cudaStream_t st) {
-    DevArgs<T> a;
+template <class T>
+DevSeg<T> to_dev(const SegDesc& s, int block0) {
+    DevSeg<T> o;
+    o.type = s.type;
+    o.begin = s.begin;
+    o.end = s.end;
+    o.base = s.base;
+    o.base2 = s.base2;
+    o.flag = s.flag;
+    o.block0 = block0;
+    o.pad = s.type == SEG_TILE ? s.flag2 : 0;
+    for (int m = 0; m < 6; ++m) o.c[m] = static_cast<T>(m < 4 ? s.c[m] : 0.0);
+    if (s.type == SEG_REPLAY) {
+        o.c[3] = static_cast<T>(0.75);
+        o.c[4] = static_cast<T>(1.0 / 3.0);
+    }
+    for (int m = 0; m < 10; ++m) o.p[m] = s.p[m];
+    return o;
+}
+
+inline int seg_blocks(const SegDesc& s, int block) {
+    return s.type == SEG_TILE ? s.end - s.begin              // one block per tile
+                              : (s.end - s.begin + block - 1) / block;
+}
+
+template <class T>
+void fill_args(DevArgs<T>& a, const LaunchDesc& d, const void* tables, int smem, int* flag) {
     a.t = *static_cast<const Tables<T>*>(tables);
     a.in_h = static_cast<const T*>(d.in_h);
     a.in_hl = static_cast<const T*>(d.in_hl);
@@ -684,31 +741,22 @@ cudaError_t launch_t(const LaunchDesc& d, const void* tables, int block, bool pd
     a.flag = flag;
     a.l2 = d.l2;
     a.smem = smem;
+    a.gseg = nullptr;
+    a.ngseg = 0;
+    a.vblocks = 0;
+}
+
+template <class T, bool COMP, int MAXR>
+cudaError_t launch_t(const LaunchDesc& d, const void* tables, int block, bool pdl, int smem, int* flag,
+                     cudaStream_t st) {
+    DevArgs<T> a;
+    fill_args(a, d, tables, smem, flag);
     int blocks = 0, ns = 0;
     for (int k = 0; k < d.nseg; ++k) {
         const SegDesc& s = d.seg[k];
         if (s.end <= s.begin) continue;
-        DevSeg<T>& o = a.seg[ns++];
-        o.type = s.type;
-        o.begin = s.begin;
-        o.end = s.end;
-        o.base = s.base;
-        o.base2 = s.base2;
-        o.flag = s.flag;
-        o.block0 = blocks;
-        o.pad = 0;
-        for (int m = 0; m < 6; ++m) o.c[m] = static_cast<T>(m < 4 ? s.c[m] : 0.0);
-        if (s.type == SEG_REPLAY) {
-            o.c[3] = static_cast<T>(0.75);
-            o.c[4] = static_cast<T>(1.0 / 3.0);
-        }
-        for (int m = 0; m < 10; ++m) o.p[m] = s.p[m];
-        if (s.type == SEG_TILE) {
-            o.pad = s.flag2;
-            blocks += s.end - s.begin;            // one block per tile
-        } else {
-            blocks += (s.end - s.begin + block - 1) / block;
-        }
+        a.seg[ns++] = to_dev<T>(s, blocks);
+        blocks += seg_blocks(s, block);
     }
     a.nseg = ns;
     for (int k = ns; k < MAXSEG; ++k) {
@@ -728,6 +776,26 @@ cudaError_t launch_t(const LaunchDesc& d, const void* tables, int block, bool pd
         case 0: return launch_kernel(kernel_phase<T, COMP, MAXR, 0>, blocks, block, pdl, st, a);
         case 1: return launch_kernel(kernel_phase<T, COMP, MAXR, 1>, blocks, block, pdl, st, a);
         default: return launch_kernel(kernel_phase<T, COMP, MAXR, 2>, blocks, block, pdl, st, a);
+    }
+}
+
+template <class T, bool COMP, int MAXR>
+cudaError_t launch_table_t(const LaunchDesc& d, const void* dsegs, int nseg, int vblocks, int grid,
+                           const void* tables, int block, bool pdl, int* flag, cudaStream_t st) {
+    DevArgs<T> a;
+    fill_args(a, d, tables, 0, flag);
+    a.nseg = 0;
+    for (int k = 0; k < MAXSEG; ++k) a.seg[k] = DevSeg<T>{};
+    a.gseg = static_cast<const DevSeg<T>*>(dsegs);
+    a.ngseg = nseg;
+    a.vblocks = vblocks;
+    if (vblocks == 0 || nseg == 0) return cudaSuccess;
+    grid = grid > 0 ? std::min(grid, vblocks) : vblocks;
+    switch (d.kind) {
+        case 0: return launch_kernel(kernel_phase_table<T, COMP, MAXR, 0>, grid, block, pdl, st, a);
+        case 1: return launch_kernel(kernel_phase_table<T, COMP, MAXR, 1>, grid, block, pdl, st, a);
+        case 2: return launch_kernel(kernel_phase_table<T, COMP, MAXR, 2>, grid, block, pdl, st, a);
+        default: return cudaErrorInvalidValue;
     }
 }
 
@@ -830,6 +898,65 @@ cudaError_t launch_phase(const LaunchDesc& d, const void* tables, const KernelCo
     if (kc.precision == 1) return launch_any<double, false>(d, tables, kc, flag, s);
     if (kc.comp) return launch_any<float, true>(d, tables, kc, flag, s);
     return launch_any<float, false>(d, tables, kc, flag, s);
+}
+
+namespace {
+template <class T, bool COMP>
+cudaError_t launch_table_any(const LaunchDesc& d, const void* dsegs, int nseg, int vblocks, int grid,
+                             const void* tables, const KernelConfig& kc, int* flag, cudaStream_t s) {
+    if (kc.maxdeg <= 8)
+        return launch_table_t<T, COMP, 8>(d, dsegs, nseg, vblocks, grid, tables, kc.block, kc.pdl, flag, s);
+    return launch_table_t<T, COMP, MAX_DEGREE>(d, dsegs, nseg, vblocks, grid, tables, kc.block, kc.pdl,
+                                               flag, s);
+}
+
+template <class T>
+int encode_t(const SegDesc* segs, int n, int block, std::vector<unsigned char>& out, int* nout) {
+    std::vector<DevSeg<T>> v;
+    int blocks = 0;
+    for (int k = 0; k < n; ++k) {
+        const SegDesc& s = segs[k];
+        if (s.end <= s.begin) continue;
+        if (s.type == SEG_TILE) return -1;
+        v.push_back(to_dev<T>(s, blocks));
+        blocks += seg_blocks(s, block);
+    }
+    out.resize(v.size() * sizeof(DevSeg<T>));
+    if (!v.empty()) std::memcpy(out.data(), v.data(), out.size());
+    *nout = static_cast<int>(v.size());
+    return blocks;
+}
+
+template <class T, bool COMP, int MAXR>
+int table_occupancy_t(int kind, int block) {
+    int nb = 0;
+    cudaError_t e = kind == 0   ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel_phase_table<T, COMP, MAXR, 0>, block, 0)
+                    : kind == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel_phase_table<T, COMP, MAXR, 1>, block, 0)
+                                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel_phase_table<T, COMP, MAXR, 2>, block, 0);
+    return e == cudaSuccess ? nb : -1;
+}
+}  // namespace
+
+int encode_segment_table(const KernelConfig& kc, const SegDesc* segs, int n,
+                         std::vector<unsigned char>& out, int* nseg_out) {
+    if (kc.precision == 1) return encode_t<double>(segs, n, kc.block, out, nseg_out);
+    return encode_t<float>(segs, n, kc.block, out, nseg_out);
+}
+
+cudaError_t launch_phase_table(const LaunchDesc& d, const void* dsegs, int nseg, int vblocks, int grid,
+                               const void* tables, const KernelConfig& kc, int* flag, cudaStream_t s) {
+    if (kc.precision == 1) return launch_table_any<double, false>(d, dsegs, nseg, vblocks, grid, tables, kc, flag, s);
+    if (kc.comp) return launch_table_any<float, true>(d, dsegs, nseg, vblocks, grid, tables, kc, flag, s);
+    return launch_table_any<float, false>(d, dsegs, nseg, vblocks, grid, tables, kc, flag, s);
+}
+
+int table_blocks_per_sm(const KernelConfig& kc, int kind) {
+    const bool big = kc.maxdeg > 8;
+    if (kc.precision == 1)
+        return big ? table_occupancy_t<double, false, 16>(kind, kc.block) : table_occupancy_t<double, false, 8>(kind, kc.block);
+    if (kc.comp)
+        return big ? table_occupancy_t<float, true, 16>(kind, kc.block) : table_occupancy_t<float, true, 8>(kind, kc.block);
+    return big ? table_occupancy_t<float, false, 16>(kind, kc.block) : table_occupancy_t<float, false, 8>(kind, kc.block);
 }
 
 cudaError_t launch_scatter_state(const KernelConfig& kc, int n, const int* perm, const double* src,

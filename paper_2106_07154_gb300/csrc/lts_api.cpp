@@ -14,6 +14,7 @@
 #include "../../include/lts.h"
 #include "lts_error.h"
 #include "lts_internal.h"
+#include "lts_objects.h"
 #include "regions.h"
 
 using namespace lts;
@@ -22,107 +23,7 @@ namespace {
 constexpr int kDefaultTileCells = 256;   // cells per tile of the fused kernel
 }
 
-// ------------------------------------------------------------------ objects
-
-struct DeviceArena {
-    std::vector<void*> blocks;
-    ~DeviceArena() {
-        for (void* p : blocks) cudaFree(p);
-    }
-    template <class T>
-    T* upload(const std::vector<T>& v, cudaError_t& err) {
-        void* p = nullptr;
-        size_t n = std::max<size_t>(1, v.size()) * sizeof(T);
-        err = cudaMalloc(&p, n);
-        if (err != cudaSuccess) return nullptr;
-        blocks.push_back(p);
-        if (!v.empty()) err = cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
-        return static_cast<T*>(p);
-    }
-    void* alloc(size_t bytes, cudaError_t& err) {
-        void* p = nullptr;
-        err = cudaMalloc(&p, std::max<size_t>(bytes, 16));
-        if (err != cudaSuccess) return nullptr;
-        blocks.push_back(p);
-        err = cudaMemset(p, 0, std::max<size_t>(bytes, 16));
-        return p;
-    }
-};
-
-struct lts_mesh_s {
-    std::atomic<int> ref{1};
-    HostMesh m;
-};
-
-struct lts_regions_s {
-    std::atomic<int> ref{1};
-    lts_mesh_s* mesh = nullptr;
-    RegionsHost r;
-    // device tables per precision (built on first use)
-    std::unique_ptr<DeviceArena> arena[2];
-    Tables<float> t32{};
-    Tables<double> t64{};
-    int* d_perm_c = nullptr;
-    int* d_perm_e = nullptr;
-    int device = -1;
-};
-
-struct SV {   // one state vector (h, u) with optional compensation words
-    void* hh = nullptr;
-    void* hl = nullptr;
-    void* uh = nullptr;
-    void* ul = nullptr;
-};
-
-struct lts_state_s {
-    lts_regions_s* reg = nullptr;
-    lts_params p{};
-    KernelConfig kc{};
-    size_t tsz = 4;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    cudaStream_t capture_stream = nullptr;
-    cudaStream_t side_stream = nullptr;          // concurrent branch (direct launches)
-    cudaStream_t capture_side = nullptr;         // concurrent branch during capture
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-    DeviceArena arena;
-    const void* tables = nullptr;
-    SV buf[4];            // [parity] = x_old, [1-parity] = x_new, [2] = x_1st, [3] = x_2nd
-    SV P1c, P1e, P2c, P2e;   // interface-1 snapshots of the coarse 1st / 2nd stage
-    void* acc_c[3] = {};  // correction terms on I1 u I2 cells (Steps 3.x.2)
-    void* acc_e[3] = {};
-    void* q = nullptr;
-    void* ring_c = nullptr;   // [maxE*nC] per-slot PV contributions
-    void* ring_k = nullptr;   // [nC] K_i
-    int* flag = nullptr;
-    double* stage_c = nullptr;   // FP64 staging for I/O (original order)
-    double* stage_e = nullptr;
-    double* diag_partial = nullptr;
-    double* diag_out = nullptr;
-    int diag_blocks = 0;
-    std::vector<LaunchDesc> plan[2];
-    cudaGraphExec_t exec[2] = {nullptr, nullptr};
-    int parity = 0;
-    int64_t steps = 0;
-    double time = 0.0;
-    // statistics
-    double bytes[NKINDS] = {0, 0, 0};
-    int launches[NKINDS] = {0, 0, 0};
-    double prof_ms[NKINDS] = {0, 0, 0};
-    std::vector<cudaEvent_t> events;
-    std::vector<cudaEvent_t> gevents[2];   // profile == 2: per kernel node, per parity
-    ~lts_state_s();
-};
-
 namespace {
-
-#define CUDA_TRY(expr)                                                                        \
-    do {                                                                                      \
-        cudaError_t _e = (expr);                                                              \
-        if (_e != cudaSuccess)                                                                \
-            return set_error(_e == cudaErrorMemoryAllocation ? LTS_ENOMEM : LTS_ECUDA,        \
-                             "%s: %s (%s:%d)", #expr, cudaGetErrorString(_e), __FILE__, __LINE__); \
-    } while (0)
 
 void release_mesh(lts_mesh_s* m) {
     if (m && --m->ref == 0) delete m;
@@ -328,6 +229,7 @@ struct Planner {
     SegDesc vert(int lo, int hi) const {   // vertex bands lo..hi
         SegDesc s;
         s.type = SEG_VERT;
+        s.elem = ELEM_VERT;
         s.begin = vb[lo];
         s.end = vb[hi + 1];
         return s;
@@ -338,6 +240,7 @@ struct Planner {
                   int stage, bool first) const {
         SegDesc s;
         s.type = SEG_TILE;
+        s.elem = -1;   // tiles: not placeable in an ensemble
         s.begin = r.tb[lo];
         s.end = r.tb[hi + 1];
         s.flag2 = acc_lo <= hi ? r.tb[acc_lo] : s.end;
@@ -355,6 +258,7 @@ struct Planner {
     SegDesc ring(int lo, int hi) const {   // ring results only, cell bands lo..hi
         SegDesc s;
         s.type = SEG_RING;
+        s.elem = ELEM_CELL;
         s.begin = cb[lo];
         s.end = cb[hi + 1];
         return s;
@@ -363,6 +267,7 @@ struct Planner {
                 double D) const {
         SegDesc s;
         s.type = cell ? SEG_RING_UPD : SEG_EDGE_UPD;
+        s.elem = cell ? ELEM_CELL : ELEM_EDGE;
         const int* ofs = cell ? cb : eb;
         s.begin = ofs[lo];
         s.end = ofs[hi + 1];
@@ -378,10 +283,12 @@ struct Planner {
     SegDesc acc(bool cell, int stage, bool first) const {
         SegDesc s;
         s.type = cell ? SEG_RING_ACC : SEG_EDGE_ACC;
+        s.elem = cell ? ELEM_CELL : ELEM_EDGE;
         const int* ofs = cell ? cb : eb;
         s.begin = ofs[B_I1];
         s.end = ofs[B_I2 + 1];
         s.base = ofs[B_I1];
+        s.cfam = FAM_I;
         s.flag = first ? 1 : 0;
         s.p[0] = cell ? S->acc_c[stage] : S->acc_e[stage];
         return s;
@@ -404,10 +311,13 @@ struct Planner {
         const double c1 = a - at, c2 = 2.0 * at;
         SegDesc s;
         s.type = SEG_PRED;
+        s.elem = cell ? ELEM_CELL : ELEM_EDGE;
         const int* ofs = cell ? cb : eb;
         s.begin = ofs[B_I1];
         s.end = ofs[B_I1 + 1];
         s.base = ofs[B_I1];
+        s.cfam = FAM_I1;
+        s.cfam2 = FAM_I1;
         s.flag = (c1 == 0.0 && c2 == 0.0) ? 1 : (c1 == 1.0 && c2 == 0.0) ? 2 : (c1 == 0.0 && c2 == 1.0) ? 3 : 0;
         const SV& p1 = cell ? S->P1c : S->P1e;
         const SV& p2 = cell ? S->P2c : S->P2e;
@@ -422,6 +332,7 @@ struct Planner {
             s.p[4] = cell ? x2full->hh : x2full->uh;
             s.p[5] = cell ? x2full->hl : x2full->ul;
             s.base2 = 0;
+            s.cfam2 = FAM_FULL;
         }
         s.p[6] = cell ? out.hh : out.uh;
         s.p[7] = cell ? out.hl : out.ul;
@@ -429,14 +340,18 @@ struct Planner {
         s.c[1] = c2;
         return s;
     }
+    // dst_base = 0: dst is a full array; otherwise dst is the compact I1 array
+    // starting at element dst_base (interface snapshots)
     SegDesc copy(bool cell, int lo, int hi, const SV& src, const SV& dst, int dst_base) const {
         SegDesc s;
         s.type = SEG_COPY;
+        s.elem = cell ? ELEM_CELL : ELEM_EDGE;
         const int* ofs = cell ? cb : eb;
         s.begin = ofs[lo];
         s.end = ofs[hi + 1];
         s.base = dst_base;
         s.base2 = 0;
+        s.cfam = dst_base != 0 ? FAM_I1 : FAM_FULL;
         s.p[0] = cell ? src.hh : src.uh;
         s.p[1] = cell ? src.hl : src.ul;
         s.p[2] = cell ? dst.hh : dst.uh;
@@ -446,10 +361,12 @@ struct Planner {
     SegDesc replay(bool cell, const SV& old, const SV& out, double dtM) const {
         SegDesc s;
         s.type = SEG_REPLAY;
+        s.elem = cell ? ELEM_CELL : ELEM_EDGE;
         const int* ofs = cell ? cb : eb;
         s.begin = ofs[B_I1];
         s.end = ofs[B_I2 + 1];
         s.base = ofs[B_I1];
+        s.cfam = FAM_I;
         s.p[0] = cell ? old.hh : old.uh;
         s.p[1] = cell ? old.hl : old.ul;
         for (int k = 0; k < 3; ++k) s.p[2 + k] = cell ? S->acc_c[k] : S->acc_e[k];
@@ -460,9 +377,10 @@ struct Planner {
         s.c[2] = 2.0 * dtM / 3.0;
         return s;
     }
-    LaunchDesc launch(int kind, const SV& in, std::initializer_list<SegDesc> segs) const {
+    LaunchDesc launch(int kind, const SV& in, std::initializer_list<SegDesc> segs, int key = -1) const {
         LaunchDesc d;
         d.kind = kind;
+        d.key = key;
         d.in_h = in.hh;
         d.in_hl = in.hl;
         d.in_u = in.uh;
@@ -478,6 +396,7 @@ struct Planner {
 };
 
 constexpr double A1 = 0.0, A2 = 0.75, A3 = 1.0 / 3.0;
+
 
 void plan_lts3(lts_state_s* S, int parity, std::vector<LaunchDesc>& out) {
     const RegionsHost& r = S->reg->r;
@@ -496,16 +415,16 @@ void plan_lts3(lts_state_s* S, int parity, std::vector<LaunchDesc>& out) {
     // Each right-hand side updating bands [lo, hi] is three launches:
     // vertex bands [lo-1, hi+1], ring cells [lo, hi+1], edges [lo, hi].
     // Step 1: first stage on Fbar u I1 u I2 u C (bands F2..C rest)
-    out.push_back(P.launch(0, X0, {P.vert(B_F3, B_CREST), P.copy(true, B_I2, B_C2, X0, XN, 0)}));
-    out.push_back(P.launch(1, X0, {P.upd(true, B_F2, B_CREST, X0, X0, X1, A1, dt)}));
+    out.push_back(P.launch(0, X0, {P.vert(B_F3, B_CREST), P.copy(true, B_I2, B_C2, X0, XN, 0)}, KEY_STEP1 + 0));
+    out.push_back(P.launch(1, X0, {P.upd(true, B_F2, B_CREST, X0, X0, X1, A1, dt)}, KEY_STEP1 + 1));
     out.push_back(P.launch(2, X0, {P.upd(false, B_F2, B_CREST, X0, X0, X1, A1, dt),
                                    P.copy(false, B_I2, B_C2, X0, XN, 0),
-                                   P.copy(true, B_I1, B_I1, X1, S->P1c, I1)}));
+                                   P.copy(true, B_I1, B_I1, X1, S->P1c, I1)}, KEY_STEP1 + 2));
     // Step 2: second stage on I1 u I2 u C
-    out.push_back(P.launch(0, X1, {P.vert(B_F1, B_CREST), P.copy(false, B_I1, B_I1, X1, S->P1e, I1e)}));
-    out.push_back(P.launch(1, X1, {P.upd(true, B_I1, B_CREST, X0, X1, X2, A2, dt / 4.0)}));
+    out.push_back(P.launch(0, X1, {P.vert(B_F1, B_CREST), P.copy(false, B_I1, B_I1, X1, S->P1e, I1e)}, KEY_STEP2 + 0));
+    out.push_back(P.launch(1, X1, {P.upd(true, B_I1, B_CREST, X0, X1, X2, A2, dt / 4.0)}, KEY_STEP2 + 1));
     out.push_back(P.launch(2, X1, {P.upd(false, B_I1, B_CREST, X0, X1, X2, A2, dt / 4.0),
-                                   P.copy(true, B_I1, B_I1, X2, S->P2c, I1)}));
+                                   P.copy(true, B_I1, B_I1, X2, S->P2c, I1)}, KEY_STEP2 + 2));
     const size_t after_step2 = out.size();
     for (auto& d : out) d.l2 = 2;   // Steps 1 and 2 stream the coarse region
     // Step 3: M fine substeps on F, correction terms on I1 u I2, I1 predicted
@@ -529,11 +448,12 @@ void plan_lts3(lts_state_s* S, int parity, std::vector<LaunchDesc>& out) {
                 pe = P.pred(false, X0, XN, k + 1, M, 1);
             }
             const SegDesc snap = (k == 0 && s == 1) ? P.copy(false, B_I1, B_I1, X2, S->P2e, I1e) : none;
-            out.push_back(P.launch(0, in, {P.vert(B_FDEEP, B_C1), snap}));
+            const int key = KEY_STEP3 + 9 * k + 3 * (s - 1);
+            out.push_back(P.launch(0, in, {P.vert(B_FDEEP, B_C1), snap}, key + 0));
             out.push_back(P.launch(1, in, {P.upd(true, B_FDEEP, B_F1, old, in, o, a, D),
-                                           P.acc(true, s - 1, k == 0), P.ring(B_C1, B_C1), pc}));
+                                           P.acc(true, s - 1, k == 0), P.ring(B_C1, B_C1), pc}, key + 1));
             out.push_back(P.launch(2, in, {P.upd(false, B_FDEEP, B_F1, old, in, o, a, D),
-                                           P.acc(false, s - 1, k == 0), pe}));
+                                           P.acc(false, s - 1, k == 0), pe}, key + 2));
         }
     }
     // Step 4 (third stage on C, reading R2) and Step 5 (interface correction).
@@ -545,15 +465,15 @@ void plan_lts3(lts_state_s* S, int parity, std::vector<LaunchDesc>& out) {
     // x_new, follows Step 3 together with Step 5.
     for (size_t k = after_step2; k < out.size(); ++k) out[k].l2 = 1;   // fine substeps stay in L2
     std::vector<LaunchDesc> side;
-    side.push_back(P.launch(0, X2, {P.vert(B_C2, B_CREST)}));
-    side.push_back(P.launch(1, X2, {P.upd(true, B_CREST, B_CREST, X0, X2, XN, A3, 2.0 * dt / 3.0)}));
-    side.push_back(P.launch(2, X2, {P.upd(false, B_CREST, B_CREST, X0, X2, XN, A3, 2.0 * dt / 3.0)}));
+    side.push_back(P.launch(0, X2, {P.vert(B_C2, B_CREST)}, KEY_SIDE + 0));
+    side.push_back(P.launch(1, X2, {P.upd(true, B_CREST, B_CREST, X0, X2, XN, A3, 2.0 * dt / 3.0)}, KEY_SIDE + 1));
+    side.push_back(P.launch(2, X2, {P.upd(false, B_CREST, B_CREST, X0, X2, XN, A3, 2.0 * dt / 3.0)}, KEY_SIDE + 2));
     std::vector<LaunchDesc> tail;
-    tail.push_back(P.launch(0, X2, {P.vert(B_I2, B_C2)}));
+    tail.push_back(P.launch(0, X2, {P.vert(B_I2, B_C2)}, KEY_TAIL + 0));
     tail.push_back(P.launch(1, X2, {P.upd(true, B_C1, B_C2, X0, X2, XN, A3, 2.0 * dt / 3.0),
-                                    P.replay(true, X0, XN, dtM)}));
+                                    P.replay(true, X0, XN, dtM)}, KEY_TAIL + 1));
     tail.push_back(P.launch(2, X2, {P.upd(false, B_C1, B_C2, X0, X2, XN, A3, 2.0 * dt / 3.0),
-                                    P.replay(false, X0, XN, dtM)}));
+                                    P.replay(false, X0, XN, dtM)}, KEY_TAIL + 2));
     for (auto& d : side) d.l2 = 2;
     for (auto& d : tail) d.l2 = 2;
     auto drop = [](std::vector<LaunchDesc>& v) {
@@ -562,7 +482,7 @@ void plan_lts3(lts_state_s* S, int parity, std::vector<LaunchDesc>& out) {
     };
     drop(side);
     drop(tail);
-    const bool concurrent = S->p.profile == 0 && !side.empty();
+    const bool concurrent = S->p.profile == 0 && !S->p.serial_step4 && !side.empty();
     if (concurrent) {
         // the side branch forks right after Step 2
         for (auto& d : side) d.branch = 1;
@@ -576,6 +496,7 @@ void plan_lts3(lts_state_s* S, int parity, std::vector<LaunchDesc>& out) {
     if (concurrent && tail.empty()) {
         LaunchDesc j;   // nothing after Step 3: still join before the step ends
         j.join = true;
+        j.key = KEY_TAIL - 1;
         out.push_back(j);
     }
     // empty launches (bands without cells) are dropped, markers are kept
@@ -656,7 +577,7 @@ void plan_lts3_fused(lts_state_s* S, int parity, std::vector<LaunchDesc>& out) {
     };
     drop(side);
     drop(tail);
-    const bool concurrent = S->p.profile == 0 && !side.empty();
+    const bool concurrent = S->p.profile == 0 && !S->p.serial_step4 && !side.empty();
     size_t at = after_step2;
     if (concurrent) {
         for (auto& d : side) d.branch = 1;
@@ -708,9 +629,9 @@ void plan_ssprk3(lts_state_s* S, int parity, std::vector<LaunchDesc>& out) {
     const double as[3] = {A1, A2, A3};
     const double Ds[3] = {dt, dt / 4.0, 2.0 * dt / 3.0};
     for (int s = 0; s < 3; ++s) {
-        out.push_back(P.launch(0, *ins[s], {P.vert(B_FDEEP, B_CREST)}));
-        out.push_back(P.launch(1, *ins[s], {P.upd(true, B_FDEEP, B_CREST, X0, *ins[s], *outs[s], as[s], Ds[s])}));
-        out.push_back(P.launch(2, *ins[s], {P.upd(false, B_FDEEP, B_CREST, X0, *ins[s], *outs[s], as[s], Ds[s])}));
+        out.push_back(P.launch(0, *ins[s], {P.vert(B_FDEEP, B_CREST)}, 3 * s + 0));
+        out.push_back(P.launch(1, *ins[s], {P.upd(true, B_FDEEP, B_CREST, X0, *ins[s], *outs[s], as[s], Ds[s])}, 3 * s + 1));
+        out.push_back(P.launch(2, *ins[s], {P.upd(false, B_FDEEP, B_CREST, X0, *ins[s], *outs[s], as[s], Ds[s])}, 3 * s + 2));
     }
 }
 
@@ -835,6 +756,18 @@ int write_state(lts_state_s* S, const double* h, const double* u) {
 }
 
 }  // namespace
+
+namespace lts {
+int device_check() { return check_device(); }
+void make_plan(lts_state_s* S, int parity, std::vector<LaunchDesc>& out) {
+    if (S->p.mode == LTS_MODE_LTS3) plan_lts3(S, parity, out);
+    else plan_ssprk3(S, parity, out);
+}
+double plan_launch_bytes(const LaunchDesc& d, const RegionsHost& r, int nC, int nE, int nV, size_t T,
+                         bool comp) {
+    return launch_bytes(d, r, nC, nE, nV, T, comp);
+}
+}  // namespace lts
 
 lts_state_s::~lts_state_s() {
     for (auto& e : exec)
@@ -991,7 +924,7 @@ int lts_regions_set(lts_mesh m, const int8_t* fine_mask, int32_t order, int32_t 
     if (!R) return set_error(LTS_ENOMEM, "out of host memory");
     int rc;
     try {
-        rc = compute_regions(m->m, fine_mask, layers, R->r);
+        rc = compute_regions(m->m, fine_mask, layers, 0, R->r);
         if (rc == LTS_OK) rc = build_tiles(m->m, R->r, kDefaultTileCells);
     } catch (const std::bad_alloc&) {
         return set_error(LTS_ENOMEM, "out of host memory");
@@ -1027,6 +960,28 @@ int lts_regions_tiling(lts_regions r, int32_t tile_cells) {
         return set_error(LTS_ENOMEM, "out of host memory");
     }
     if (rc != LTS_OK) return rc;
+    r->arena[0].reset();   // device tables are rebuilt on the next state creation
+    r->arena[1].reset();
+    r->d_perm_c = r->d_perm_e = nullptr;
+    return LTS_OK;
+}
+
+int lts_regions_ordering(lts_regions r, int32_t ordering) {
+    if (!r) return set_error(LTS_EINVAL, "null regions");
+    if (r->ref.load() != 1) return set_error(LTS_EINVAL, "regions are in use by a state");
+    if (ordering == r->r.ordering) return LTS_OK;
+    RegionsHost nr;
+    int rc;
+    try {
+        const std::vector<int8_t> fine = r->r.fine;
+        rc = compute_regions(r->mesh->m, fine.data(), r->r.layers, ordering, nr);
+        if (rc == LTS_OK) rc = build_tiles(r->mesh->m, nr, r->r.tile_cells);
+    } catch (const std::bad_alloc&) {
+        return set_error(LTS_ENOMEM, "out of host memory");
+    }
+    if (rc != LTS_OK) return rc;
+    nr.M = r->r.M;
+    r->r = std::move(nr);
     r->arena[0].reset();   // device tables are rebuilt on the next state creation
     r->arena[1].reset();
     r->d_perm_c = r->d_perm_e = nullptr;
@@ -1121,6 +1076,9 @@ int lts_state_create(lts_mesh mesh, lts_regions reg, const double* h0, const dou
             else plan_ssprk3(S.get(), par, S->plan[par]);
         }
     }
+    if (p->no_l2_hints)
+        for (auto& plan : S->plan)
+            for (LaunchDesc& d : plan) d.l2 = 0;
     // launch statistics of one step (both parities have the same sizes)
     const HostMesh& m = mesh->m;
     for (LaunchDesc& d : S->plan[0]) {
@@ -1286,7 +1244,10 @@ extern "C" {
 int lts_step_stats(lts_state s, int32_t* launches_per_step, double* bytes, double* ms,
                    int32_t* launches_per_kind) {
     if (!s) return set_error(LTS_EINVAL, "null state");
-    if (launches_per_step) *launches_per_step = s->launches[0] + s->launches[1] + s->launches[2];
+    if (launches_per_step) {
+        *launches_per_step = 0;
+        for (int k = 0; k < NKINDS; ++k) *launches_per_step += s->launches[k];
+    }
     for (int k = 0; k < NKINDS; ++k) {
         if (bytes) bytes[k] = s->bytes[k];
         if (ms) ms[k] = s->prof_ms[k];

@@ -93,7 +93,15 @@ struct SegDesc {
     int flag2 = 0;            // TILE: first tile that accumulates instead of updating
     double c[4] = {0, 0, 0, 0};  // UPD: a, D; PRED: c1, c2; REPLAY: D1, D2, D3
     void* p[10] = {};         // see kernels.cu for the meaning per type
+    // host-only: element kind of [begin, end) and the compact family that
+    // `base` / `base2` index (used to place a member's segments in an ensemble)
+    int elem = 0;             // ELEM_CELL, ELEM_EDGE or ELEM_VERT
+    int cfam = 0, cfam2 = 0;  // FAM_FULL, FAM_I1 or FAM_I
 };
+enum : int { ELEM_CELL = 0, ELEM_EDGE = 1, ELEM_VERT = 2 };
+// Compact arrays: FAM_I1 holds band I1 (interface snapshots), FAM_I holds
+// bands I1..I2 (correction accumulators); FAM_FULL = a full-length array.
+enum : int { FAM_FULL = 0, FAM_I1 = 1, FAM_I = 2 };
 
 struct LaunchDesc {
     int kind = 0;             // 0 = vertex, 1 = ring, 2 = edge, 3 = fused tiles
@@ -112,7 +120,16 @@ struct LaunchDesc {
     int l2 = 0;                   // L2 policy of read-only loads: 0 none, 1 keep, 2 stream
     bool fork = false;            // side branch starts here (waits for the main stream)
     bool join = false;            // main stream waits for the side branch before this launch
+    int key = -1;                 // position in the step's phase structure (same key = same
+                                  // phase, input buffers and kind in every plan)
 };
+
+// Launch keys of the LTS3 plan: the phase of a launch (Step 1, Step 2, the
+// Step 4 side branch, Step 3 substep k stage s, the tail) plus its kind.
+// Plans of different meshes have equal keys for the same phase, so an
+// ensemble merges them launch by launch in key order.  SSPRK3 plans use
+// 3 * stage + kind.
+constexpr int KEY_STEP1 = 0, KEY_STEP2 = 3, KEY_SIDE = 10, KEY_STEP3 = 100, KEY_TAIL = 1000000;
 
 struct KernelConfig {
     int precision;   // 0 FP32, 1 FP64
@@ -135,6 +152,19 @@ cudaError_t launch_diagnostics(const KernelConfig& kc, const void* tables, const
                                const void* h_lo, const void* u_hi, const void* u_lo, double g,
                                double* partial, int nblocks, double* out2, cudaStream_t s);
 int kernel_registers(const KernelConfig& kc, int kind);
+// Segment-table launches (ensembles).  encode_segment_table converts the
+// non-empty segments of `segs` into the device records of kc's precision
+// (bytes in `out`, count in *nseg_out) and returns the number of virtual
+// blocks, or -1 for a segment kind the table kernel does not run (tiles).
+int encode_segment_table(const KernelConfig& kc, const SegDesc* segs, int n,
+                         std::vector<unsigned char>& out, int* nseg_out);
+// One launch of kind d.kind (0..2) over a device segment table; d supplies
+// the input state and intermediate buffers (its own segments are ignored).
+// grid = number of resident blocks (persistent) or <= 0 for one block per
+// virtual block.
+cudaError_t launch_phase_table(const LaunchDesc& d, const void* dsegs, int nseg, int vblocks, int grid,
+                               const void* tables, const KernelConfig& kc, int* flag, cudaStream_t s);
+int table_blocks_per_sm(const KernelConfig& kc, int kind);
 
 // Device view of a state's current solution, for entry points defined in
 // other translation units (lts_api.cpp fills it).

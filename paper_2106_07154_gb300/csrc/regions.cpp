@@ -87,8 +87,11 @@ std::vector<int> bfs(const HostMesh& m, const std::vector<char>& source,
 
 }  // namespace
 
-int compute_regions(const HostMesh& m, const int8_t* fine, int layers, RegionsHost& r) {
+int compute_regions(const HostMesh& m, const int8_t* fine, int layers, int ordering, RegionsHost& r) {
     if (layers < 1) return set_error(LTS_EINVAL, "interface_layers must be >= 1");
+    if (ordering != 0 && ordering != 1) return set_error(LTS_EINVAL, "ordering must be 0 or 1");
+    r.ordering = ordering;
+    r.fine.assign(fine, fine + m.nC);
     const int nC = m.nC, nE = m.nE, nV = m.nV;
     std::vector<char> isF(nC), notF(nC), all(nC, 1);
     for (int i = 0; i < nC; ++i) {
@@ -121,7 +124,7 @@ int compute_regions(const HostMesh& m, const int8_t* fine, int layers, RegionsHo
     for (int v = 0; v < nV; ++v)
         r.vband[v] = std::min({r.cband[m.CoV[3 * v]], r.cband[m.CoV[3 * v + 1]], r.cband[m.CoV[3 * v + 2]]});
 
-    // ---- cells: band, then Hilbert key
+    // ---- cells: band, then Hilbert key (or the mesh's own index)
     std::vector<uint64_t> key(nC);
     double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
     for (int i = 0; i < nC; ++i) {
@@ -135,7 +138,7 @@ int compute_regions(const HostMesh& m, const int8_t* fine, int layers, RegionsHo
         double p[3] = {m.xc[i], m.yc[i], m.zc[i]};
         double s[3];
         for (int k = 0; k < 3; ++k) s[k] = hi[k] > lo[k] ? (p[k] - lo[k]) / (hi[k] - lo[k]) : 0.0;
-        key[i] = hilbert3(s[0], s[1], s[2]);
+        key[i] = ordering == 0 ? hilbert3(s[0], s[1], s[2]) : static_cast<uint64_t>(i);
     }
     r.perm_c.resize(nC);
     std::iota(r.perm_c.begin(), r.perm_c.end(), 0);

@@ -20,6 +20,8 @@ struct HostMesh {
 
 struct RegionsHost {
     int M = 1, layers = 1;
+    int ordering = 0;                              // 0 Hilbert inside a band, 1 mesh index order
+    std::vector<int8_t> fine;                      // the fine-cell mask the labels came from
     std::vector<int8_t> cband, eband, vband;      // original order
     std::vector<int> perm_c, perm_e, perm_v;      // new -> original
     std::vector<int> inv_c, inv_e, inv_v;         // original -> new
@@ -52,7 +54,9 @@ struct CoefTables {
     std::vector<double> sK64, area, bd;
 };
 
-int compute_regions(const HostMesh& m, const int8_t* fine, int layers, RegionsHost& r);
+// Labels, bands and band-ordered connectivity.  ordering 0: Hilbert curve
+// inside each band; 1: the mesh's own index order inside each band.
+int compute_regions(const HostMesh& m, const int8_t* fine, int layers, int ordering, RegionsHost& r);
 template <class T>
 void coefficient_tables(const HostMesh& m, const RegionsHost& r, CoefTables<T>& o);
 double derived_weight(const HostMesh& m, int c, int j, int p);

@@ -29,6 +29,9 @@ LTS_NKINDS = 4
 KIND_NAMES = ("vertex", "ring", "edge", "tile")
 PATH_THREE = 0
 PATH_FUSED = 1
+LTS_ORDER_HILBERT = 0
+LTS_ORDER_INDEX = 1
+LTS_TUNE_ORDERING = 1
 
 NBANDS = 9
 BAND_NAMES = ("F_deep", "F3", "F2", "F1", "I1", "I2", "C1", "C2", "C_rest")
@@ -73,7 +76,18 @@ class lts_params(C.Structure):
     _fields_ = [("g", C.c_double), ("dt", C.c_double), ("precision", C.c_int32),
                 ("mode", C.c_int32), ("compensated", C.c_int32), ("use_graph", C.c_int32),
                 ("block_size", C.c_int32), ("profile", C.c_int32), ("pdl", C.c_int32),
-                ("kernel_path", C.c_int32), ("stream", C.c_void_p)]
+                ("kernel_path", C.c_int32), ("stream", C.c_void_p), ("no_l2_hints", C.c_int32),
+                ("serial_step4", C.c_int32)]
+
+
+class lts_tune_report(C.Structure):
+    _fields_ = [("candidates", C.c_int32), ("ordering", C.c_int32), ("best_ms", C.c_double),
+                ("default_ms", C.c_double)]
+
+
+class lts_ensemble_params(C.Structure):
+    _fields_ = [("use_graph", C.c_int32), ("pdl", C.c_int32), ("persistent", C.c_int32),
+                ("stream", C.c_void_p)]
 
 
 class lts_diag(C.Structure):
@@ -129,6 +143,10 @@ def lib():
             L.lts_regions_labels.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
             L.lts_regions_counts.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
             L.lts_regions_tiling.argtypes = [C.c_void_p, C.c_int32]
+            L.lts_regions_ordering.argtypes = [C.c_void_p, C.c_int32]
+            L.lts_autotune.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                       C.POINTER(lts_params), C.c_int32, C.c_int32,
+                                       C.POINTER(lts_params), C.POINTER(lts_tune_report)]
             L.lts_regions_permutation.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
             L.lts_state_create.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                            C.POINTER(lts_params), C.POINTER(C.c_void_p)]
@@ -140,6 +158,17 @@ def lib():
             L.lts_step_stats.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                          C.c_void_p]
             L.lts_diagnostics_noalloc.argtypes = [C.c_void_p, C.c_void_p]
+            L.lts_ensemble_create.argtypes = [C.c_void_p, C.c_int32, C.POINTER(lts_ensemble_params),
+                                              C.POINTER(C.c_void_p)]
+            L.lts_ensemble_destroy.argtypes = [C.c_void_p]
+            L.lts_ensemble_destroy.restype = None
+            L.lts_ensemble_step.argtypes = [C.c_void_p, C.c_int32]
+            L.lts_ensemble_read.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
+                                            C.POINTER(lts_diag)]
+            L.lts_ensemble_write.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
+                                             C.c_double, C.c_int64]
+            L.lts_ensemble_stats.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                             C.c_void_p]
         _lib = L
     return _lib
 
@@ -259,6 +288,10 @@ def lts_regions_tiling(reg_h, tile_cells: int):
     _check(lib().lts_regions_tiling(reg_h, int(tile_cells)))
 
 
+def lts_regions_ordering(reg_h, ordering: int):
+    _check(lib().lts_regions_ordering(reg_h, int(ordering)))
+
+
 def lts_regions_counts(reg_h):
     c = np.zeros(NBANDS, np.int64)
     e = np.zeros(NBANDS, np.int64)
@@ -275,12 +308,47 @@ def lts_regions_permutation(reg_h, nCells: int, nEdges: int, nVertices: int):
     return pc, pe, pv
 
 
+def make_params(g: float, dt: float, precision: int = LTS_FP32, mode: int = LTS_MODE_LTS3,
+                compensated: bool = True, use_graph: bool = True, block_size: int = 0,
+                profile: int = 0, stream: int | None = None, pdl: bool = True,
+                kernel_path: int = 0, l2_hints: bool = True, serial_step4: bool = False):
+    return lts_params(g, dt, precision, mode, int(compensated), int(use_graph), block_size,
+                      int(profile), int(pdl), int(kernel_path), stream, int(not l2_hints),
+                      int(serial_step4))
+
+
+def params_dict(p: lts_params) -> dict:
+    return {"block_size": p.block_size, "kernel_path": p.kernel_path, "pdl": bool(p.pdl),
+            "l2_hints": not p.no_l2_hints, "serial_step4": bool(p.serial_step4),
+            "use_graph": bool(p.use_graph)}
+
+
+def lts_autotune(mesh_h, reg_h, h0, u0, base: lts_params, steps: int = 20,
+                 tune_ordering: bool = False):
+    """Returns (best lts_params, report dict); see include/lts.h."""
+    best = lts_params()
+    rep = lts_tune_report()
+    _check(lib().lts_autotune(mesh_h, reg_h, _f64(h0).ctypes.data, _f64(u0).ctypes.data,
+                              C.byref(base), int(steps), LTS_TUNE_ORDERING if tune_ordering else 0,
+                              C.byref(best), C.byref(rep)))
+    return best, {"candidates": rep.candidates, "ordering": rep.ordering, "best_ms": rep.best_ms,
+                  "default_ms": rep.default_ms}
+
+
+def lts_state_create_p(mesh_h, reg_h, h0, u0, p: lts_params):
+    h = C.c_void_p()
+    _check(lib().lts_state_create(mesh_h, reg_h, _f64(h0).ctypes.data, _f64(u0).ctypes.data,
+                                  C.byref(p), C.byref(h)))
+    return h
+
+
 def lts_state_create(mesh_h, reg_h, h0, u0, g: float, dt: float, precision: int = LTS_FP32,
                      mode: int = LTS_MODE_LTS3, compensated: bool = True, use_graph: bool = True,
                      block_size: int = 0, profile: int = 0, stream: int | None = None,
-                     pdl: bool = True, kernel_path: int = 0):
-    p = lts_params(g, dt, precision, mode, int(compensated), int(use_graph), block_size,
-                   int(profile), int(pdl), int(kernel_path), stream)
+                     pdl: bool = True, kernel_path: int = 0, l2_hints: bool = True,
+                     serial_step4: bool = False):
+    p = make_params(g, dt, precision, mode, compensated, use_graph, block_size, profile, stream,
+                    pdl, kernel_path, l2_hints, serial_step4)
     h = C.c_void_p()
     _check(lib().lts_state_create(mesh_h, reg_h, _f64(h0).ctypes.data, _f64(u0).ctypes.data,
                                   C.byref(p), C.byref(h)))
@@ -327,6 +395,88 @@ def lts_diagnostics_noalloc(state_h, d_out_ptr: int):
     _check(lib().lts_diagnostics_noalloc(state_h, C.c_void_p(int(d_out_ptr))))
 
 
+def lts_ensemble_create(state_handles, use_graph: bool = True, pdl: bool = True,
+                        persistent: bool = True, stream: int | None = None):
+    arr = (C.c_void_p * len(state_handles))(*[C.c_void_p(h.value if isinstance(h, C.c_void_p) else h)
+                                               for h in state_handles])
+    p = lts_ensemble_params(int(use_graph), int(pdl), int(persistent), stream)
+    out = C.c_void_p()
+    _check(lib().lts_ensemble_create(arr, len(state_handles), C.byref(p), C.byref(out)))
+    return out
+
+
+def lts_ensemble_destroy(h):
+    if h:
+        lib().lts_ensemble_destroy(h)
+
+
+def lts_ensemble_step(ens_h, n_coarse: int):
+    _check(lib().lts_ensemble_step(ens_h, int(n_coarse)))
+
+
+def lts_ensemble_read(ens_h, i: int, nCells: int, nEdges: int, h_out=None, u_out=None):
+    h = np.zeros(nCells) if h_out is None else h_out
+    u = np.zeros(nEdges) if u_out is None else u_out
+    d = lts_diag()
+    _check(lib().lts_ensemble_read(ens_h, int(i), h.ctypes.data, u.ctypes.data, C.byref(d)))
+    return h, u, {"mass": d.mass, "energy": d.energy, "time": d.time, "steps": d.steps}
+
+
+def lts_ensemble_write(ens_h, i: int, h, u, time: float = 0.0, steps: int = 0):
+    _check(lib().lts_ensemble_write(ens_h, int(i), _f64(h).ctypes.data, _f64(u).ctypes.data,
+                                    float(time), int(steps)))
+
+
+def lts_ensemble_stats(ens_h):
+    n = C.c_int32()
+    nseg = C.c_int32()
+    cells = C.c_int64()
+    b = np.zeros(LTS_NKINDS)
+    _check(lib().lts_ensemble_stats(ens_h, C.byref(n), b.ctypes.data, C.byref(cells), C.byref(nseg)))
+    return {"launches": int(n.value), "bytes": b.tolist(), "cells": int(cells.value),
+            "segments": int(nseg.value)}
+
+
+class Ensemble:
+    """Several Models advanced together (one launch per phase for all)."""
+
+    def __init__(self, models, use_graph: bool = True, pdl: bool = True, persistent: bool = True,
+                 stream: int | None = None):
+        self.models = list(models)
+        self.h = None
+        self.h = lts_ensemble_create([m.state_h for m in self.models], use_graph, pdl, persistent,
+                                     stream)
+
+    def step(self, n: int):
+        lts_ensemble_step(self.h, n)
+
+    def read(self, i: int, h_out=None, u_out=None):
+        m = self.models[i]
+        return lts_ensemble_read(self.h, i, m.nC, m.nE, h_out, u_out)
+
+    def write(self, i: int, h, u, time=0.0, steps=0):
+        lts_ensemble_write(self.h, i, h, u, time, steps)
+
+    def stats(self):
+        return lts_ensemble_stats(self.h)
+
+    def close(self):
+        lts_ensemble_destroy(self.h)
+        self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Model:
     """Mesh + regions + state, with the handles released on close()."""
 
@@ -334,18 +484,29 @@ class Model:
                  precision: int = LTS_FP32, mode: int = LTS_MODE_LTS3, compensated: bool = True,
                  use_graph: bool = True, block_size: int = 0, profile: int = 0,
                  interface_layers: int = 1, stream: int | None = None, pdl: bool = True,
-                 kernel_path: int = 0, tile_cells: int = 0):
+                 kernel_path: int = 0, tile_cells: int = 0, l2_hints: bool = True,
+                 serial_step4: bool = False, ordering: int = LTS_ORDER_HILBERT,
+                 autotune: int = 0, tune_ordering: bool = False):
+        """autotune > 0: time that many coarse steps per candidate configuration
+        (lts_autotune) and build the state with the fastest; the choice is in
+        self.tuned."""
         self.nC = int(mesh["nCells"])
         self.nE = int(mesh["nEdges"])
         self.nV = int(mesh["nVertices"])
         self.mesh_h = self.reg_h = self.state_h = None
+        self.tuned = None
         self.mesh_h = lts_mesh_create(mesh)
         self.reg_h = lts_regions_set(self.mesh_h, fine_mask, 3, M, interface_layers)
         if tile_cells:
             lts_regions_tiling(self.reg_h, tile_cells)
-        self.state_h = lts_state_create(self.mesh_h, self.reg_h, h0, u0, g, dt, precision, mode,
-                                        compensated, use_graph, block_size, profile, stream, pdl,
-                                        kernel_path)
+        if ordering != LTS_ORDER_HILBERT:
+            lts_regions_ordering(self.reg_h, ordering)
+        p = make_params(g, dt, precision, mode, compensated, use_graph, block_size, profile, stream,
+                        pdl, kernel_path, l2_hints, serial_step4)
+        if autotune:
+            p, rep = lts_autotune(self.mesh_h, self.reg_h, h0, u0, p, autotune, tune_ordering)
+            self.tuned = dict(params_dict(p), **rep)
+        self.state_h = lts_state_create_p(self.mesh_h, self.reg_h, h0, u0, p)
 
     def step(self, n: int):
         lts_step(self.state_h, n)

@@ -178,12 +178,13 @@ def sphere_cap(n: int, ratio: float, M: int, seed: int = 1, lloyd_iters: int = 2
                nsteps: int = 100, cap_radius: float = math.radians(15.0),
                cap_width: float = math.radians(5.0), fine_threshold: float = 0.9,
                cfl: float = 0.5, u0: float = 20.0, mountain: bool = True,
-               name: str = "sphere_cap", cache: bool = True) -> Workload:
+               name: str = "sphere_cap", cache: bool = True,
+               centre=(1.5 * math.pi, math.pi / 6), bump=None) -> Workload:
     """Spherical SCVT with a refined cap centred on the mountain (Section 3:
     centre (3 pi/2, pi/6)); fine region = cells whose target spacing is below
     `fine_threshold` times the coarse spacing; dt = CFL limit of the coarse,
-    interface and fine-boundary cells."""
-    centre = (1.5 * math.pi, math.pi / 6)
+    interface and fine-boundary cells.  `bump` = (amplitude m, radius rad)
+    adds a Gaussian thickness perturbation at the cap centre."""
     cap = (centre[0], centre[1], cap_radius, cap_width, ratio)
     mesh = scvt_mesh(n, seed, [cap], lloyd_iters, cache=cache)
     h0, uu, b = zonal_state(mesh, u0=u0, mountain_height=2000.0 if mountain else 0.0,
@@ -191,6 +192,8 @@ def sphere_cap(n: int, ratio: float, M: int, seed: int = 1, lloyd_iters: int = 2
     mesh["bottom"] = b
     lonc, latc = _lonlat(mesh["xCell"], mesh["yCell"], mesh["zCell"])
     d = _great_circle(lonc, latc, *centre)
+    if bump is not None:
+        h0 = h0 + bump[0] * np.exp(-(d / bump[1]) ** 2)
     s = 1.0 / ratio + (1.0 - 1.0 / ratio) * 0.5 * (1.0 + np.tanh((d - cap_radius) / cap_width))
     fine = (s < fine_threshold).astype(np.int8)
     dt, mind, c = _cfl_dt(mesh, h0, uu, fine == 0, cfl)
@@ -198,6 +201,34 @@ def sphere_cap(n: int, ratio: float, M: int, seed: int = 1, lloyd_iters: int = 2
     return Workload(name, mesh, h0, uu, fine, M, dt, nsteps,
                     info={"ratio": ratio, "seed": seed, "lloyd_iters": lloyd_iters,
                           "fine_cfl": fine_cfl, "coarse_cfl": cfl, "n_fine": int(fine.sum())})
+
+
+def ensemble(n_members: int = 64, seed: int = 7, min_cells: int = 2562, max_cells: int = 163842,
+             lloyd_iters: int = 200, cache: bool = True):
+    """Uneven ensemble of spherical SCVT members: sizes log-uniform in
+    [min_cells, max_cells], resolution ratio 2, 4 or 8 in a cap at a seeded
+    position with M equal to the ratio, a balanced zonal flow with u0 uniform
+    in [10, 40] m/s over a flat bottom, and a Gaussian thickness perturbation
+    of amplitude uniform in [1, 10] m and radius 10 degrees at the cap centre."""
+    return [sphere_cap(**kw) for kw in ensemble_recipes(n_members, seed, min_cells, max_cells,
+                                                        lloyd_iters, cache)]
+
+
+def ensemble_recipes(n_members: int = 64, seed: int = 7, min_cells: int = 2562,
+                     max_cells: int = 163842, lloyd_iters: int = 200, cache: bool = True):
+    """The sphere_cap arguments of every member of `ensemble` (no mesh built)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n_members):
+        n = int(round(math.exp(rng.uniform(math.log(min_cells), math.log(max_cells)))))
+        ratio = float(rng.choice([2.0, 4.0, 8.0]))
+        centre = (float(rng.uniform(0.0, 2.0 * math.pi)), float(math.asin(rng.uniform(-0.9, 0.9))))
+        u0 = float(rng.uniform(10.0, 40.0))
+        amp = float(rng.uniform(1.0, 10.0))
+        out.append(dict(n=n, ratio=ratio, M=int(ratio), seed=seed * 1000 + k,
+                        lloyd_iters=lloyd_iters, u0=u0, mountain=False, centre=centre,
+                        bump=(amp, math.radians(10.0)), name=f"ens{k}", cache=cache))
+    return out
 
 
 def workload(name: str, **kw) -> Workload:

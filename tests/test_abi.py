@@ -92,3 +92,37 @@ def test_regions_labels_match_band_counts():
     finally:
         lts.lts_regions_destroy(rh)
         lts.lts_mesh_destroy(mh)
+
+
+def test_regions_ordering_index_keeps_mesh_order_inside_bands():
+    mesh = lts.lts_build_hex_periodic(16, 16, 10e3, 1e-4)
+    fine = np.zeros(mesh["nCells"], np.int8)
+    fine[100:140] = 1
+    mh = lts.lts_mesh_create(mesh)
+    rh = lts.lts_regions_set(mh, fine, 3, 2)
+    try:
+        nC, nE, nV = mesh["nCells"], mesh["nEdges"], mesh["nVertices"]
+        c0, _, _ = lts.lts_regions_counts(rh)
+        pc0, _, _ = lts.lts_regions_permutation(rh, nC, nE, nV)
+        lts.lts_regions_ordering(rh, lts.LTS_ORDER_INDEX)
+        c1, _, _ = lts.lts_regions_counts(rh)
+        pc1, pe1, pv1 = lts.lts_regions_permutation(rh, nC, nE, nV)
+        assert np.array_equal(c0, c1)                       # the bands do not move
+        off = np.concatenate([[0], np.cumsum(c1)])
+        for b in range(len(c1)):                            # mesh order inside each band
+            seg = pc1[off[b]:off[b + 1]]
+            assert np.all(np.diff(seg) > 0)
+            assert sorted(seg.tolist()) == sorted(pc0[off[b]:off[b + 1]].tolist())
+        assert not np.array_equal(pc0, pc1)                 # Hilbert order differs
+        assert sorted(pe1.tolist()) == list(range(nE)) and sorted(pv1.tolist()) == list(range(nV))
+        lts.lts_regions_ordering(rh, lts.LTS_ORDER_HILBERT)
+        pc2, _, _ = lts.lts_regions_permutation(rh, nC, nE, nV)
+        assert np.array_equal(pc0, pc2)
+        try:
+            lts.lts_regions_ordering(rh, 5)
+            assert False, "ordering 5 should be rejected"
+        except lts.LtsError as e:
+            assert e.code == lts.LTS_EINVAL
+    finally:
+        lts.lts_regions_destroy(rh)
+        lts.lts_mesh_destroy(mh)

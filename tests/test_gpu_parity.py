@@ -204,3 +204,27 @@ def test_nonfinite_is_reported(sphw):
         with pytest.raises(lts.LtsError) as ei:
             m.read()
         assert ei.value.code == lts.LTS_ENONFINITE
+
+
+def test_options_do_not_change_results(sphw):
+    """Cell ordering, L2 hints and Step-4 placement change only the access
+    pattern and the schedule, never an element's arithmetic."""
+    a = run_gpu(sphw, 6, lts.LTS_FP32)
+    for kw in ({"ordering": lts.LTS_ORDER_INDEX}, {"l2_hints": False}, {"serial_step4": True}):
+        with lts.Model(sphw.mesh, sphw.fine_mask, sphw.M, sphw.h0, sphw.u0, sphw.dt,
+                       precision=lts.LTS_FP32, **kw) as m:
+            m.step(6)
+            h, u, _ = m.read()
+        assert np.array_equal(h, a[0]) and np.array_equal(u, a[1]), kw
+
+
+def test_autotune_picks_a_valid_config(sphw):
+    a = run_gpu(sphw, 4, lts.LTS_FP64)
+    with lts.Model(sphw.mesh, sphw.fine_mask, sphw.M, sphw.h0, sphw.u0, sphw.dt,
+                   precision=lts.LTS_FP64, autotune=3, tune_ordering=True) as m:
+        t = m.tuned
+        assert t["candidates"] >= 20 and t["best_ms"] > 0 and t["best_ms"] <= 1.5 * t["default_ms"]
+        assert t["block_size"] in (128, 256) and t["kernel_path"] in (0, 1)
+        m.step(4)
+        h, u, _ = m.read()
+    assert np.array_equal(h, a[0]) and np.array_equal(u, a[1])
