@@ -336,6 +336,7 @@ def run_lts(args):
     if model.tuned:
         line["config"]["tuned"] = model.tuned
     if not args.no_extras and rank == 0:
+        args._ms = ms
         line.update(extras(args, w, model, stats, stream, h_gpu, u_gpu, diag))
     model.close()
     if rank == 0:
@@ -373,7 +374,7 @@ def extras(args, w, model, stats, stream, h_gpu, u_gpu, diag):
     # ---- per-kernel timing: the same coarse-step graph with an event-record
     #      node before and after every kernel node, on the state's stream
     tuned = model.tuned or {}
-    knobs = {k: tuned[k] for k in ("block_size", "kernel_path", "l2_hints", "serial_step4") if k in tuned}
+    knobs = {k: tuned[k] for k in ("block_size", "kernel_path", "l2_hints", "coarse_schedule") if k in tuned}
     if "ordering" in tuned:
         knobs["ordering"] = tuned["ordering"]
     prof = lts.Model(w.mesh, w.fine_mask, w.M, w.h0, w.u0, w.dt, w.g, precision=prec,
@@ -464,6 +465,49 @@ def extras(args, w, model, stats, stream, h_gpu, u_gpu, diag):
         "h_rel_maxnorm": float(np.max(np.abs(h1 - rh)) / np.max(np.abs(rh))),
         "u_rel_maxnorm": float(np.max(np.abs(u1 - ru)) / np.max(np.abs(ru)))}
     out["mass"] = diag["mass"]
+    # ---- FP64 LTS3 (oracle-matching precision) on the same workload
+    m64 = lts.Model(w.mesh, w.fine_mask, w.M, w.h0, w.u0, w.dt, w.g, precision=lts.LTS_FP64,
+                    stream=stream.cuda_stream)
+    m64.step(1)
+    h64, u64, _ = m64.read()
+    m64.step(3)
+    torch.cuda.synchronize()
+    n64 = max(5, min(200, args.steps // 10))
+    e0.record(stream)
+    m64.step(n64)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = e0.elapsed_time(e1) / n64
+    m64.close()
+    out["fp64_lts3"] = {"ms_per_step": ms64, "value": nC / (ms64 * 1e-3), "unit": UNIT,
+                        "error_vs_oracle_1step": {
+                            "h_rel_maxnorm": float(np.max(np.abs(h64 - rh)) / np.max(np.abs(rh))),
+                            "u_rel_maxnorm": float(np.max(np.abs(u64 - ru)) / np.max(np.abs(ru)))}}
+    # ---- accuracy at equal simulated time: 10 coarse steps of LTS3-FP32 and of
+    #      FP64 SSPRK3 at dt/M, both against FP64 SSPRK3 at dt/(4M)
+    nco = 10
+
+    def run(prec_, mode_, dt_, n_):
+        with lts.Model(w.mesh, w.fine_mask, w.M, w.h0, w.u0, dt_, w.g, precision=prec_, mode=mode_,
+                       stream=stream.cuda_stream) as m_:
+            m_.step(n_)
+            hh, uu, _ = m_.read()
+        return hh, uu
+
+    hr, ur = run(lts.LTS_FP64, lts.LTS_MODE_SSPRK3, w.dt / (4 * w.M), nco * 4 * w.M)
+    hl, ul = run(lts.LTS_FP32, lts.LTS_MODE_LTS3, w.dt, nco)
+    hs, us = run(lts.LTS_FP64, lts.LTS_MODE_SSPRK3, w.dt / w.M, nco * w.M)
+
+    def err(a, b):
+        return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+    out["accuracy_10_coarse_steps"] = {
+        "reference": f"FP64 SSPRK3 at dt/(4M) = {w.dt / (4 * w.M):.3f} s over {nco} coarse steps",
+        "lts3_fp32": {"h": err(hl, hr), "u": err(ul, ur),
+                      "sim_seconds_per_wall_second": w.dt * args.steps / (args._ms * 1e-3)},
+        "ssprk3_fp64_fine_dt": {"h": err(hs, hr), "u": err(us, ur),
+                                "sim_seconds_per_wall_second": w.dt / (ref_ms * 1e-3)},
+        "h_initial_vs_reference": err(w.h0, hr)}
     return out
 
 

@@ -132,9 +132,10 @@ void lts_mesh_destroy(lts_mesh m);
 
 /* Region labelling of Eqs. (3)-(5) from a fine-cell mask ([nCells], nonzero
  * = F^c), then band ordering: cells sorted by band
- *   0 F deep | 1 F3 | 2 F2 | 3 F1 | 4 I1 | 5 I2 | 6 C1 | 7 C2 | 8 C rest
- * (F1,F2 = the two fine layers of Eq. (4); F3 = the next fine layer; C1, C2 =
- * the two coarse layers next to I2) and by a Hilbert curve inside each
+ *   0 F deep | 1 F3 | 2 F2 | 3 F1 | 4 I1 | 5 I2 | 6 C1 | 7 C2 | 8 C3 | 9 C4 |
+ *   10 C5 | 11 C rest
+ * (F1,F2 = the two fine layers of Eq. (4); F3 = the next fine layer; C1..C5 =
+ * the five coarse layers next to I2) and by a Hilbert curve inside each
  * band; an edge takes the smaller band of its two cells (the fine-to-coarse
  * assignment of Eq. (5)), a vertex the smallest band of its three cells.
  * Every restricted phase then reads and writes contiguous index ranges.
@@ -174,7 +175,8 @@ int lts_regions_tiling(lts_regions r, int32_t tile_cells);
 #define LTS_ORDER_INDEX   1
 int lts_regions_ordering(lts_regions r, int32_t ordering);
 
-/* Number of cells, edges and vertices per band (arrays of 9). */
+/* Number of cells, edges and vertices per band (arrays of LTS_NBANDS). */
+#define LTS_NBANDS 12
 int lts_regions_counts(lts_regions r, int64_t* cells, int64_t* edges, int64_t* vertices);
 
 /* Band-order permutations: perm_cell[new] = original index (any may be NULL). */
@@ -185,6 +187,10 @@ int lts_regions_permutation(lts_regions r, int32_t* perm_cell, int32_t* perm_edg
 #define LTS_FP64 1
 #define LTS_MODE_LTS3   0   /* Algorithm 2.2 (LTS3), coarse step dt, M from regions */
 #define LTS_MODE_SSPRK3 1   /* Algorithm 2.1 (SSPRK3) on the whole mesh, step dt    */
+
+#define LTS_COARSE_STEP4  0
+#define LTS_COARSE_FAR    1
+#define LTS_COARSE_SERIAL 2
 
 typedef struct lts_params {
     double g;               /* gravity [m s^-2]                                        */
@@ -207,8 +213,13 @@ typedef struct lts_params {
     void* stream;           /* cudaStream_t to enqueue on; NULL = a library stream     */
     int32_t no_l2_hints;    /* 1: table loads without L2 eviction priorities (default:
                                keep the fine region, stream the coarse one)            */
-    int32_t serial_step4;   /* 1: Step 4 on the far coarse band after Step 3 instead of
-                               as a concurrent branch (results are identical)          */
+    int32_t coarse_schedule;/* order of the coarse phases (results are identical):
+                               LTS_COARSE_STEP4 (default): Step 4 on the coarse bands
+                               C3 and beyond runs as a concurrent graph branch beside
+                               Step 3; LTS_COARSE_FAR: Steps 1, 2 and 4 on the far
+                               coarse bands (C5+ for Step 1, C3+ for Steps 2 and 4)
+                               form that branch; LTS_COARSE_SERIAL: step order on one
+                               stream                                                  */
 } lts_params;
 
 /* Allocates the device state (band order) and uploads (h0, u0), given in the
@@ -228,8 +239,8 @@ int lts_step(lts_state s, int32_t n_coarse);
  * scratch states built from (m, r, h0, u0) and *base, and returns the
  * fastest as *best (base's g, dt, precision, mode, compensation and stream
  * kept; use_graph = 1).  Candidates: block_size 128 or 256, kernel_path 0
- * or 1, pdl on or off, L2 hints on or off, Step 4 concurrent or serial
- * (LTS3).  Each is timed over `steps` coarse steps after 3 warm-up steps;
+ * or 1, pdl on or off, L2 hints on or off, the coarse schedule (LTS3:
+ * LTS_COARSE_STEP4, _FAR or _SERIAL).  Each is timed over `steps` coarse steps after 3 warm-up steps;
  * the three fastest are timed twice more and the best of three wins.  With
  * flags & LTS_TUNE_ORDERING and no state using r, the other cell ordering
  * (lts_regions_ordering) is tried with the winner and r keeps the faster.
@@ -239,11 +250,16 @@ int lts_step(lts_state s, int32_t n_coarse);
  * Errors: LTS_EINVAL (bad arguments, nothing buildable), LTS_ENOMEM,
  * LTS_ECUDA. */
 #define LTS_TUNE_ORDERING 1
+typedef struct lts_tune_entry {
+    int32_t block_size, kernel_path, pdl, l2_hints, coarse_schedule, ordering;
+    double ms;              /* ms per coarse step (best of its timings; inf = not buildable) */
+} lts_tune_entry;
 typedef struct lts_tune_report {
     int32_t candidates;     /* configurations timed                              */
     int32_t ordering;       /* cell ordering r has afterwards (LTS_ORDER_*)      */
     double best_ms;         /* ms per coarse step of *best                       */
     double default_ms;      /* ms per coarse step of the library defaults        */
+    lts_tune_entry entry[32];   /* the first min(candidates, 32) timings          */
 } lts_tune_report;
 int lts_autotune(lts_mesh m, lts_regions r, const double* h0, const double* u0,
                  const lts_params* base, int32_t steps, int32_t flags, lts_params* best,

@@ -54,6 +54,7 @@ def lib():
         L.or_pv_flux.argtypes = [C.c_void_p, _f64p, _f64p, _f64p]
         L.or_rhs_swe.argtypes = [C.c_void_p, C.c_double, _f64p, _f64p, _f64p, _f64p]
         L.or_regions.argtypes = [C.c_void_p, _i8p, _i8p, _i8p]
+        L.or_regions_layers.argtypes = [C.c_void_p, _i8p, C.c_int, _i8p, _i8p]
         L.or_lts3_predict_coeffs.argtypes = [C.c_int, C.c_int, C.c_int, _f64p]
         L.or_ssprk3.argtypes = [C.c_void_p, C.c_void_p, C.c_double, C.c_int, _f64p, _f64p]
         L.or_rk4.argtypes = [C.c_void_p, C.c_void_p, C.c_double, C.c_int, _f64p, _f64p]
@@ -172,11 +173,16 @@ class Oracle:
                          np.ascontiguousarray(u, np.float64), H, U)
         return H, U
 
-    def regions(self, fine_mask):
-        """Labels of Eqs. (3)-(5): cells 0 F\\Fbar,1 F2,2 F1,3 I1,4 I2,5 C; edges 0,1,3,4,5."""
+    def regions(self, fine_mask, layers=1):
+        """Labels of Eqs. (3)-(5): cells 0 F\\Fbar,1 F2,2 F1,3 I1,4 I2,5 C; edges 0,1,3,4,5.
+        layers > 1: interfaces that many cells thick."""
         cl = np.zeros(self.nC, np.int8)
         el = np.zeros(self.nE, np.int8)
-        lib().or_regions(self._h, np.ascontiguousarray(fine_mask, np.int8), cl, el)
+        fm = np.ascontiguousarray(fine_mask, np.int8)
+        if layers == 1:
+            lib().or_regions(self._h, fm, cl, el)
+        elif lib().or_regions_layers(self._h, fm, int(layers), cl, el) != 0:
+            raise ValueError("layers must be >= 1")
         return cl, el
 
     # ---------------------------------------------------------- integrators (Section 2)

@@ -343,26 +343,44 @@ void or_rhs(const or_mesh* m, const or_system* sys, const double* h, const doubl
 /* ---------------------------------------------------------------- regions */
 
 /* Eqs. (3)-(5) with readings R1 and R6. */
+/* One sweep of Eq. (3)'s "shares at least one edge with": every cell that
+ * shares an edge with a marked cell becomes marked (synchronously). */
+static void or_grow(const or_mesh* m, char* mark, char* tmp) {
+    memcpy(tmp, mark, (size_t)m->nC);
+    for (int e = 0; e < m->nE; ++e) {
+        int a = m->CoE[2 * e], b = m->CoE[2 * e + 1];
+        if (mark[a]) tmp[b] = 1;
+        if (mark[b]) tmp[a] = 1;
+    }
+    memcpy(mark, tmp, (size_t)m->nC);
+}
+
 int or_regions(const or_mesh* m, const signed char* fine, signed char* cl, signed char* el) {
+    return or_regions_layers(m, fine, 1, cl, el);
+}
+
+int or_regions_layers(const or_mesh* m, const signed char* fine, int L, signed char* cl,
+                      signed char* el) {
+    if (L < 1) return -1;
     int nC = m->nC, nE = m->nE;
     char* inF = (char*)calloc(nC, 1);
     char* inI1 = (char*)calloc(nC, 1);
     char* inI2 = (char*)calloc(nC, 1);
     char* inF1 = (char*)calloc(nC, 1);
     char* inF2 = (char*)calloc(nC, 1);
+    char* reach = (char*)calloc(nC, 1);
+    char* tmp = (char*)calloc(nC, 1);
     for (int i = 0; i < nC; ++i) inF[i] = fine[i] != 0;
-    /* I1: not fine, shares an edge with a fine cell */
-    for (int e = 0; e < nE; ++e) {
-        int a = m->CoE[2 * e], b = m->CoE[2 * e + 1];
-        if (inF[a] && !inF[b]) inI1[b] = 1;
-        if (inF[b] && !inF[a]) inI1[a] = 1;
-    }
-    /* I2: neither fine nor I1, shares an edge with an I1 cell */
-    for (int e = 0; e < nE; ++e) {
-        int a = m->CoE[2 * e], b = m->CoE[2 * e + 1];
-        if (inI1[a] && !inF[b] && !inI1[b]) inI2[b] = 1;
-        if (inI1[b] && !inF[a] && !inI1[a]) inI2[a] = 1;
-    }
+    /* I1: not fine, reached from F by 1..L edge crossings (L = 1: shares an
+     * edge with a fine cell, Eq. 3) */
+    memcpy(reach, inF, (size_t)nC);
+    for (int k = 0; k < L; ++k) or_grow(m, reach, tmp);
+    for (int i = 0; i < nC; ++i) inI1[i] = reach[i] && !inF[i];
+    /* I2: neither fine nor I1, reached from I1 by 1..L further crossings */
+    for (int k = 0; k < L; ++k) or_grow(m, reach, tmp);
+    for (int i = 0; i < nC; ++i) inI2[i] = reach[i] && !inF[i] && !inI1[i];
+    free(reach);
+    free(tmp);
     /* F1: fine, shares an edge with an I1 cell */
     for (int e = 0; e < nE; ++e) {
         int a = m->CoE[2 * e], b = m->CoE[2 * e + 1];

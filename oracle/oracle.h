@@ -70,6 +70,13 @@ void or_rhs_swe(const or_mesh* m, double g, const double* h, const double* u,
  * edge_label: 0 F^e, 1 Fbar^e, 3 I1^e, 4 I2^e, 5 C^e                   */
 int or_regions(const or_mesh* m, const signed char* fine_mask,
                signed char* cell_label, signed char* edge_label);
+/* The same with interfaces L cells thick: I1 = the non-fine cells reached
+ * from F by 1..L edge crossings, I2 = those reached by L+1..2L (the thick
+ * interface layers of the speed-up runs of Section 3; L = 1 is Eq. 3).
+ * F1, F2 and the edge sets follow Eqs. (4)-(5) unchanged.  Returns -1 for
+ * L < 1. */
+int or_regions_layers(const or_mesh* m, const signed char* fine_mask, int L,
+                      signed char* cell_label, signed char* edge_label);
 
 /* Prediction coefficients of Steps 3.1.1 / 3.2.1 / 3.3.1 (LTS3):
  * x = c[0]*x_old + c[1]*x_1st + c[2]*x_2nd.  stage = 1, 2, 3. */

@@ -4,8 +4,8 @@
 //
 // Knobs: threads per block, the kernel path (three launches per right-hand
 // side or fused tiles), programmatic dependent launch, the L2
-// eviction-priority hints, whether Step 4 on the far coarse band runs as a
-// concurrent branch, and (optionally) the cell ordering inside the bands.
+// eviction-priority hints, the schedule of the coarse phases (which run as a
+// concurrent graph branch), and (optionally) the cell ordering in the bands.
 // None of them changes a result bit (each element's arithmetic is the same
 // in every configuration), so the choice is purely a matter of time.
 #include <algorithm>
@@ -22,7 +22,7 @@ using namespace lts;
 namespace {
 
 struct Candidate {
-    int block, path, pdl, no_l2, serial;
+    int block, path, pdl, no_l2, serial;   // serial: the coarse schedule
     double ms = INFINITY;
 };
 
@@ -32,7 +32,7 @@ lts_params apply(const lts_params& base, const Candidate& c) {
     p.kernel_path = c.path;
     p.pdl = c.pdl;
     p.no_l2_hints = c.no_l2;
-    p.serial_step4 = c.serial;
+    p.coarse_schedule = c.serial;
     p.use_graph = 1;
     p.profile = 0;
     p.stream = nullptr;
@@ -79,14 +79,16 @@ extern "C" int lts_autotune(lts_mesh m, lts_regions r, const double* h0, const d
     if (steps < 1 || steps > 100000) return set_error(LTS_EINVAL, "steps must be in [1, 100000]");
     std::vector<Candidate> cands;
     const bool lts3 = base->mode == LTS_MODE_LTS3;
-    for (int path = 0; path <= 1; ++path)
-        for (int block : {128, 256}) {
-            if (path == 1 && block != 256) continue;   // one block per 256-cell tile
-            for (int pdl = 1; pdl >= 0; --pdl)
-                for (int no_l2 = 0; no_l2 <= 1; ++no_l2)
-                    for (int serial = 0; serial <= (lts3 ? 1 : 0); ++serial)
-                        cands.push_back({block, path, pdl, no_l2, serial});
-        }
+    // three-launch path: every combination; fused tiles (one block per
+    // 256-cell tile): with PDL, without the FAR schedule
+    for (int block : {128, 256})
+        for (int pdl = 1; pdl >= 0; --pdl)
+            for (int no_l2 = 0; no_l2 <= 1; ++no_l2)
+                for (int sched = 0; sched <= (lts3 ? 2 : 0); ++sched)
+                    cands.push_back({block, 0, pdl, no_l2, sched});
+    for (int no_l2 = 0; no_l2 <= 1; ++no_l2)
+        for (int sched : {LTS_COARSE_STEP4, LTS_COARSE_SERIAL})
+            if (lts3 || sched == LTS_COARSE_STEP4) cands.push_back({256, 1, 1, no_l2, sched});
     // every candidate once, then the three fastest twice more (best of three)
     for (Candidate& c : cands) {
         int rc = time_config(m, r, h0, u0, apply(*base, c), steps, &c.ms);
@@ -110,11 +112,14 @@ extern "C" int lts_autotune(lts_mesh m, lts_regions r, const double* h0, const d
     if (!std::isfinite(win->ms)) return set_error(LTS_EINVAL, "no configuration could be built");
     double default_ms = INFINITY;
     for (const Candidate& c : cands)
-        if (c.block == 256 && c.path == 0 && c.pdl == 1 && c.no_l2 == 0 && c.serial == 0) default_ms = c.ms;
+        if (c.block == 256 && c.path == 0 && c.pdl == 1 && c.no_l2 == 0 && c.serial == LTS_COARSE_STEP4)
+            default_ms = c.ms;
     *best = apply(*base, *win);
     best->stream = base->stream;
     double best_ms = win->ms;
     int ordering = r->r.ordering, tried_orderings = 1;
+    const int ordering0 = ordering;
+    double other_ms = INFINITY;
     if ((flags & LTS_TUNE_ORDERING) && r->ref.load() == 1) {
         // the other cell ordering with the winning launch configuration
         const int other = 1 - ordering;
@@ -124,6 +129,7 @@ extern "C" int lts_autotune(lts_mesh m, lts_regions r, const double* h0, const d
         rc = time_config(m, r, h0, u0, apply(*base, *win), steps, &ms);
         if (rc != LTS_OK) return rc;
         tried_orderings = 2;
+        other_ms = ms;
         if (ms < best_ms) {
             best_ms = ms;
             ordering = other;
@@ -137,6 +143,15 @@ extern "C" int lts_autotune(lts_mesh m, lts_regions r, const double* h0, const d
         rep->best_ms = best_ms;
         rep->default_ms = default_ms;
         rep->ordering = ordering;
+        // every candidate ran with the initial ordering; the extra trial with the other one
+        int n = 0;
+        for (const Candidate& c : cands) {
+            if (n >= 32) break;
+            rep->entry[n++] = {c.block, c.path, c.pdl, 1 - c.no_l2, c.serial, ordering0, c.ms};
+        }
+        if (tried_orderings == 2 && n < 32)
+            rep->entry[n++] = {win->block, win->path, win->pdl, 1 - win->no_l2, win->serial, 1 - ordering0,
+                               other_ms};
     }
     return LTS_OK;
 }

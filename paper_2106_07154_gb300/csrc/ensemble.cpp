@@ -53,6 +53,9 @@ struct lts_ensemble_s {
     void* q = nullptr;
     void* ring_c = nullptr;
     void* ring_k = nullptr;
+    void* q_side = nullptr;       // intermediates of the concurrent far-coarse branch
+    void* ring_c_side = nullptr;
+    void* ring_k_side = nullptr;
     int* flag = nullptr;
     std::vector<Launch> plan[2];
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
@@ -205,6 +208,9 @@ int alloc_state(lts_ensemble_s* E) {
     E->q = A(E->NV);
     E->ring_c = A(static_cast<size_t>(E->MAXE) * E->NC);
     E->ring_k = A(E->NC);
+    E->q_side = A(E->NV);
+    E->ring_c_side = A(static_cast<size_t>(E->MAXE) * E->NC);
+    E->ring_k_side = A(E->NC);
     E->flag = static_cast<int*>(E->arena.alloc(sizeof(int), err));
     if (err != cudaSuccess)
         return set_error(err == cudaErrorMemoryAllocation ? LTS_ENOMEM : LTS_ECUDA, "ensemble state: %s",
@@ -263,6 +269,7 @@ int build_plan(lts_ensemble_s* E, int parity, int nsm) {
         F.reg = S->reg;
         F.p = S->p;
         F.p.profile = 0;
+        F.p.coarse_schedule = LTS_COARSE_FAR;   // every member's far coarse phases on the branch
         F.kc = S->kc;
         F.tsz = S->tsz;
         for (int k = 0; k < 4; ++k) F.buf[k] = E->buf[k];
@@ -277,6 +284,9 @@ int build_plan(lts_ensemble_s* E, int parity, int nsm) {
         F.q = E->q;
         F.ring_c = E->ring_c;
         F.ring_k = E->ring_k;
+        F.q_side = E->q_side;
+        F.ring_c_side = E->ring_c_side;
+        F.ring_k_side = E->ring_k_side;
         F.flag = E->flag;
         std::vector<LaunchDesc> plan;
         make_plan(&F, parity, plan);
@@ -292,7 +302,7 @@ int build_plan(lts_ensemble_s* E, int parity, int nsm) {
                 g.proto.fork = g.proto.join = false;
                 g.init = true;
             } else if (g.proto.kind != d.kind || g.proto.in_h != d.in_h || g.proto.in_u != d.in_u ||
-                       g.proto.branch != d.branch || g.proto.l2 != d.l2) {
+                       g.proto.branch != d.branch || g.proto.l2 != d.l2 || g.proto.q != d.q) {
                 return set_error(LTS_EINVAL, "internal error: member plans disagree at key %d", d.key);
             }
             for (int k = 0; k < d.nseg; ++k) {

@@ -187,6 +187,34 @@ __device__ __forceinline__ void griddep_launch_dependents() {
 }
 __device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// ------------------------------------------------- stage-update operands
+// The operands of an element's stage update (UPD: old value, input value and
+// their compensation words) or accumulation (ACC: the running sum).  The
+// edge pass loads them right after the dependency wait, beside its stencil
+// gathers, so the update adds no memory round trip after the tendency.
+// UPD: oh, ol = old value and its compensation word, xh, xl = input value
+// and its word; ACC: oh = the running sum (0 for the first term).
+template <class T>
+struct EpiOps {
+    T oh, ol, xh, xl;
+};
+
+enum : int { EPI_NONE = 0, EPI_UPD = 1, EPI_ACC = 2 };
+
+// in_x = null: the caller already holds the input value (it sets xh).
+template <class T, bool COMP>
+__device__ __forceinline__ void epi_load(const Ld& ld, const DevSeg<T>& s, int mode, int i, const T* in_x,
+                                         EpiOps<T>& o) {
+    if (mode == EPI_ACC) {
+        o.oh = s.flag ? T(0) : ld((const T*)s.p[0] + (i - s.base));
+    } else if (mode == EPI_UPD) {
+        o.oh = ld((const T*)s.p[0] + i);
+        o.ol = COMP ? ld((const T*)s.p[1] + i) : T(0);
+        if (in_x) o.xh = ld(in_x + i);
+        o.xl = COMP ? ld((const T*)s.p[2] + i) : T(0);
+    }
+}
+
 // ------------------------------------------------------------- kind 0: vertex
 
 // q_v = (zeta_v + f_v) / h_v with zeta_v = sum t_{e,v} (d_e/A_v) u_e and
@@ -325,7 +353,8 @@ __device__ __forceinline__ T ring_pass(const DevArgs<T>& a, int c) {
 // U_e = -(1/d_e) [ (C_{c1,p1} - C_{c0,p0})/2 + g((h1 - h0) + (b1 - b0)) + K1 - K0 ]
 // (-n_{e,c0} = -1, -n_{e,c1} = +1 carry the signs of the two ring shares).
 template <class T, bool COMP>
-__device__ __forceinline__ T edge_tendency(const DevArgs<T>& a, int e) {
+__device__ __forceinline__ T edge_tendency(const DevArgs<T>& a, int e, const DevSeg<T>& seg, int epi,
+                                           EpiOps<T>& eo) {
     const Tables<T>& t = a.t;
     const Ld ld(a.l2);
     const int N = t.nC;
@@ -335,6 +364,7 @@ __device__ __forceinline__ T edge_tendency(const DevArgs<T>& a, int e) {
     const T rdc = ld.stat(t.rdc + e);
     const T db = ld.stat(t.b + c1) - ld.stat(t.b + c0);
     griddep_wait();
+    epi_load<T, COMP>(ld, seg, epi, e, a.in_u, eo);
     const T C0 = ld(a.ring_c + p0 * N + c0), C1 = ld(a.ring_c + p1 * N + c1);
     // h1 - h0 is exact for nearby thicknesses (Sterbenz); with COMP the
     // compensation words restore the digits the FP32 thickness dropped.
@@ -598,24 +628,20 @@ __device__ __forceinline__ void pointwise(const DevSeg<T>& s, int i) {
     }
 }
 
-// Stage update (UPD) or correction accumulation (ACC) of a cell or edge value.
+// Stage update (UPD) or correction accumulation (ACC) of a cell or edge
+// value from the operands epi_load fetched.
 template <class T, bool COMP, bool IS_CELL>
-__device__ __forceinline__ void epilogue(const DevArgs<T>& a, const DevSeg<T>& s, bool acc_mode, int i,
-                                         T R, const T* in_x) {
-    if (acc_mode) {
+__device__ __forceinline__ void epilogue(const DevArgs<T>& a, const DevSeg<T>& s, int epi, int i, T R,
+                                         const EpiOps<T>& o) {
+    if (epi == EPI_ACC) {
         T* acc = (T*)s.p[0];
-        const int k = i - s.base;
-        acc[k] = s.flag ? R : acc[k] + R;
+        acc[i - s.base] = s.flag ? R : o.oh + R;
         return;
     }
-    const T* oh = (const T*)s.p[0];
-    const T* ol = (const T*)s.p[1];
-    const T* sl = (const T*)s.p[2];
     T* outh = (T*)s.p[3];
     T* outl = (T*)s.p[4];
     T yh, yl;
-    combine<T, COMP>(oh[i], COMP ? ol[i] : T(0), in_x[i], COMP ? sl[i] : T(0), s.c[0], s.c[1], R,
-                     yh, yl);
+    combine<T, COMP>(o.oh, o.ol, o.xh, o.xl, s.c[0], s.c[1], R, yh, yl);
     outh[i] = yh;
     if (COMP) outl[i] = yl;
     const bool ok = IS_CELL ? finite_pos(yh) : finite_val(yh);
@@ -646,11 +672,20 @@ __device__ __forceinline__ void phase_block(const DevArgs<T>& a, const DevSeg<T>
     if (KIND == 0 && type == SEG_VERT) {
         vertex_pv(a, i);
     } else if (KIND == 1 && is_ring(type)) {
+        // the cell update's operands are loaded after the ring (the ring pass
+        // holds ~40 registers; loading them earlier costs a resident block)
+        const int epi = type == SEG_RING ? EPI_NONE : type == SEG_RING_ACC ? EPI_ACC : EPI_UPD;
         const T H = ring_pass<T, COMP, MAXR>(a, i);
-        if (type != SEG_RING) epilogue<T, COMP, true>(a, s, type == SEG_RING_ACC, i, H, a.in_h);
+        if (epi != EPI_NONE) {
+            EpiOps<T> o;
+            epi_load<T, COMP>(Ld(a.l2), s, epi, i, a.in_h, o);
+            epilogue<T, COMP, true>(a, s, epi, i, H, o);
+        }
     } else if (KIND == 2 && (type == SEG_EDGE_UPD || type == SEG_EDGE_ACC)) {
-        const T U = edge_tendency<T, COMP>(a, i);
-        epilogue<T, COMP, false>(a, s, type == SEG_EDGE_ACC, i, U, a.in_u);
+        const int epi = type == SEG_EDGE_ACC ? EPI_ACC : EPI_UPD;
+        EpiOps<T> o;
+        const T U = edge_tendency<T, COMP>(a, i, s, epi, o);
+        epilogue<T, COMP, false>(a, s, epi, i, U, o);
     } else {
         griddep_wait();
         pointwise<T, COMP>(s, i);

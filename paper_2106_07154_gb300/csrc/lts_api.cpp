@@ -411,19 +411,36 @@ void plan_lts3(lts_state_s* S, int parity, std::vector<LaunchDesc>& out) {
     const int I1 = r.cb[B_I1];
     const int I1e = r.eb[B_I1];
     const SegDesc none;
+    // Coarse phases beside Step 3 (Algorithm 2.2 orders Steps 1, 2 and 4
+    // with Step 3 only through data: Step 3 reads the coarse stage values of
+    // bands up to C2 and writes none beyond I1).  STEP4: Step 4 on C3+ as a
+    // concurrent branch; FAR: Steps 1, 2 and 4 on the far bands as that
+    // branch; SERIAL (and the profiling modes): step order.
+    const int sched = S->p.profile != 0 ? LTS_COARSE_SERIAL : S->p.coarse_schedule;
+    const bool concurrent = sched != LTS_COARSE_SERIAL;
+    const bool far = sched == LTS_COARSE_FAR;
     out.clear();
     // Each right-hand side updating bands [lo, hi] is three launches:
-    // vertex bands [lo-1, hi+1], ring cells [lo, hi+1], edges [lo, hi].
-    // Step 1: first stage on Fbar u I1 u I2 u C (bands F2..C rest)
-    out.push_back(P.launch(0, X0, {P.vert(B_F3, B_CREST), P.copy(true, B_I2, B_C2, X0, XN, 0)}, KEY_STEP1 + 0));
-    out.push_back(P.launch(1, X0, {P.upd(true, B_F2, B_CREST, X0, X0, X1, A1, dt)}, KEY_STEP1 + 1));
-    out.push_back(P.launch(2, X0, {P.upd(false, B_F2, B_CREST, X0, X0, X1, A1, dt),
+    // vertex bands [lo-1, hi+1], ring cells [lo, hi+1] (ring results only on
+    // hi+1), edges [lo, hi].  A phase updating [lo, hi] reads [lo-1, hi+2].
+    // Step 1 (first stage on Fbar u I1 u I2 u C) and Step 2 (second stage on
+    // I1 u I2 u C).  Concurrent: the main stream updates bands up to C4
+    // (Step 1) and C2 (Step 2), exactly what Step 3 and Step 2 read.
+    const int s1_hi = far ? B_C4 : B_CREST;
+    const int s2_hi = far ? B_C2 : B_CREST;
+    auto ring_halo = [&](int hi) { return hi < B_CREST ? P.ring(hi + 1, hi + 1) : none; };
+    out.push_back(P.launch(0, X0, {P.vert(B_F3, std::min(s1_hi + 1, (int)B_CREST)),
+                                   P.copy(true, B_I2, B_C2, X0, XN, 0)}, KEY_STEP1 + 0));
+    out.push_back(P.launch(1, X0, {P.upd(true, B_F2, s1_hi, X0, X0, X1, A1, dt), ring_halo(s1_hi)},
+                           KEY_STEP1 + 1));
+    out.push_back(P.launch(2, X0, {P.upd(false, B_F2, s1_hi, X0, X0, X1, A1, dt),
                                    P.copy(false, B_I2, B_C2, X0, XN, 0),
                                    P.copy(true, B_I1, B_I1, X1, S->P1c, I1)}, KEY_STEP1 + 2));
-    // Step 2: second stage on I1 u I2 u C
-    out.push_back(P.launch(0, X1, {P.vert(B_F1, B_CREST), P.copy(false, B_I1, B_I1, X1, S->P1e, I1e)}, KEY_STEP2 + 0));
-    out.push_back(P.launch(1, X1, {P.upd(true, B_I1, B_CREST, X0, X1, X2, A2, dt / 4.0)}, KEY_STEP2 + 1));
-    out.push_back(P.launch(2, X1, {P.upd(false, B_I1, B_CREST, X0, X1, X2, A2, dt / 4.0),
+    out.push_back(P.launch(0, X1, {P.vert(B_F1, std::min(s2_hi + 1, (int)B_CREST)),
+                                   P.copy(false, B_I1, B_I1, X1, S->P1e, I1e)}, KEY_STEP2 + 0));
+    out.push_back(P.launch(1, X1, {P.upd(true, B_I1, s2_hi, X0, X1, X2, A2, dt / 4.0), ring_halo(s2_hi)},
+                           KEY_STEP2 + 1));
+    out.push_back(P.launch(2, X1, {P.upd(false, B_I1, s2_hi, X0, X1, X2, A2, dt / 4.0),
                                    P.copy(true, B_I1, B_I1, X2, S->P2c, I1)}, KEY_STEP2 + 2));
     const size_t after_step2 = out.size();
     for (auto& d : out) d.l2 = 2;   // Steps 1 and 2 stream the coarse region
@@ -456,23 +473,38 @@ void plan_lts3(lts_state_s* S, int parity, std::vector<LaunchDesc>& out) {
                                            P.acc(false, s - 1, k == 0), pe}, key + 2));
         }
     }
-    // Step 4 (third stage on C, reading R2) and Step 5 (interface correction).
-    // Step 4 depends only on Step 2 (reading A7 of the design notes): its part
-    // on the far coarse band C rest runs as a side branch concurrently with
-    // Step 3 (it reads x_2nd on bands C2..C rest and writes x_new on C rest,
-    // which Step 3 neither reads nor writes; its q / ring entries are disjoint
-    // from Step 3's).  The C1, C2 part, whose cells Step 3 still reads in
-    // x_new, follows Step 3 together with Step 5.
     for (size_t k = after_step2; k < out.size(); ++k) out[k].l2 = 1;   // fine substeps stay in L2
-    std::vector<LaunchDesc> side;
-    side.push_back(P.launch(0, X2, {P.vert(B_C2, B_CREST)}, KEY_SIDE + 0));
-    side.push_back(P.launch(1, X2, {P.upd(true, B_CREST, B_CREST, X0, X2, XN, A3, 2.0 * dt / 3.0)}, KEY_SIDE + 1));
-    side.push_back(P.launch(2, X2, {P.upd(false, B_CREST, B_CREST, X0, X2, XN, A3, 2.0 * dt / 3.0)}, KEY_SIDE + 2));
-    std::vector<LaunchDesc> tail;
-    tail.push_back(P.launch(0, X2, {P.vert(B_I2, B_C2)}, KEY_TAIL + 0));
-    tail.push_back(P.launch(1, X2, {P.upd(true, B_C1, B_C2, X0, X2, XN, A3, 2.0 * dt / 3.0),
-                                    P.replay(true, X0, XN, dtM)}, KEY_TAIL + 1));
-    tail.push_back(P.launch(2, X2, {P.upd(false, B_C1, B_C2, X0, X2, XN, A3, 2.0 * dt / 3.0),
+    // Step 4 (third stage on C, reading R2) and Step 5 (interface correction).
+    std::vector<LaunchDesc> side, tail;
+    if (concurrent) {
+        // The branch, with its own intermediates.  FAR: Step 1 on C5..C rest,
+        // Step 2 on C3..C rest; both: Step 4 on C3..C rest.  It reads stage
+        // values of bands >= C2 only, which the main stream finished before
+        // the fork, and writes bands Step 3 never reads.
+        if (far) {
+            side.push_back(P.launch(0, X0, {P.vert(B_C4, B_CREST)}, KEY_SIDE + 0));
+            side.push_back(P.launch(1, X0, {P.upd(true, B_C5, B_CREST, X0, X0, X1, A1, dt)}, KEY_SIDE + 1));
+            side.push_back(P.launch(2, X0, {P.upd(false, B_C5, B_CREST, X0, X0, X1, A1, dt)}, KEY_SIDE + 2));
+            side.push_back(P.launch(0, X1, {P.vert(B_C2, B_CREST)}, KEY_SIDE + 3));
+            side.push_back(P.launch(1, X1, {P.upd(true, B_C3, B_CREST, X0, X1, X2, A2, dt / 4.0)}, KEY_SIDE + 4));
+            side.push_back(P.launch(2, X1, {P.upd(false, B_C3, B_CREST, X0, X1, X2, A2, dt / 4.0)}, KEY_SIDE + 5));
+        }
+        side.push_back(P.launch(0, X2, {P.vert(B_C2, B_CREST)}, KEY_SIDE + 6));
+        side.push_back(P.launch(1, X2, {P.upd(true, B_C3, B_CREST, X0, X2, XN, A3, 2.0 * dt / 3.0)}, KEY_SIDE + 7));
+        side.push_back(P.launch(2, X2, {P.upd(false, B_C3, B_CREST, X0, X2, XN, A3, 2.0 * dt / 3.0)}, KEY_SIDE + 8));
+        for (auto& d : side) {
+            d.q = S->q_side;
+            d.ring_c = S->ring_c_side;
+            d.ring_k = S->ring_k_side;
+        }
+    }
+    // the near part of Step 4 (C1..C2 when concurrent, else all of C) and
+    // Step 5 after Step 3
+    const int s4_hi = concurrent ? B_C2 : B_CREST;
+    tail.push_back(P.launch(0, X2, {P.vert(B_I2, std::min(s4_hi + 1, (int)B_CREST))}, KEY_TAIL + 0));
+    tail.push_back(P.launch(1, X2, {P.upd(true, B_C1, s4_hi, X0, X2, XN, A3, 2.0 * dt / 3.0),
+                                    ring_halo(s4_hi), P.replay(true, X0, XN, dtM)}, KEY_TAIL + 1));
+    tail.push_back(P.launch(2, X2, {P.upd(false, B_C1, s4_hi, X0, X2, XN, A3, 2.0 * dt / 3.0),
                                     P.replay(false, X0, XN, dtM)}, KEY_TAIL + 2));
     for (auto& d : side) d.l2 = 2;
     for (auto& d : tail) d.l2 = 2;
@@ -482,18 +514,15 @@ void plan_lts3(lts_state_s* S, int parity, std::vector<LaunchDesc>& out) {
     };
     drop(side);
     drop(tail);
-    const bool concurrent = S->p.profile == 0 && !S->p.serial_step4 && !side.empty();
-    if (concurrent) {
-        // the side branch forks right after Step 2
+    if (!side.empty()) {
+        // the side branch forks right after Step 2 and joins before the tail
         for (auto& d : side) d.branch = 1;
         side.front().fork = true;
         if (!tail.empty()) tail.front().join = true;
         out.insert(out.begin() + static_cast<long>(after_step2), side.begin(), side.end());
-    } else {
-        out.insert(out.end(), side.begin(), side.end());
     }
     out.insert(out.end(), tail.begin(), tail.end());
-    if (concurrent && tail.empty()) {
+    if (!side.empty() && tail.empty()) {
         LaunchDesc j;   // nothing after Step 3: still join before the step ends
         j.join = true;
         j.key = KEY_TAIL - 1;
@@ -567,7 +596,7 @@ void plan_lts3_fused(lts_state_s* S, int parity, std::vector<LaunchDesc>& out) {
     // Step 4 on C rest concurrently with Step 3; C1, C2 and Step 5 after it
     std::vector<LaunchDesc> side, tail;
     side.push_back(P.launch(3, X2, {P.tiles(B_CREST, B_CREST, NOACC, X0, XN, A3, 2.0 * dt / 3.0, -1, false)}));
-    tail.push_back(P.launch(3, X2, {P.tiles(B_C1, B_C2, NOACC, X0, XN, A3, 2.0 * dt / 3.0, -1, false),
+    tail.push_back(P.launch(3, X2, {P.tiles(B_C1, B_C5, NOACC, X0, XN, A3, 2.0 * dt / 3.0, -1, false),
                                     P.replay(true, X0, XN, dtM), P.replay(false, X0, XN, dtM)}));
     for (auto& d : side) d.l2 = 2;
     for (auto& d : tail) d.l2 = 2;
@@ -577,7 +606,7 @@ void plan_lts3_fused(lts_state_s* S, int parity, std::vector<LaunchDesc>& out) {
     };
     drop(side);
     drop(tail);
-    const bool concurrent = S->p.profile == 0 && !S->p.serial_step4 && !side.empty();
+    const bool concurrent = S->p.profile == 0 && S->p.coarse_schedule != LTS_COARSE_SERIAL && !side.empty();
     size_t at = after_step2;
     if (concurrent) {
         for (auto& d : side) d.branch = 1;
@@ -731,6 +760,11 @@ int state_alloc(lts_state_s* S) {
     S->q = A(m.nV);
     S->ring_c = A(static_cast<size_t>(m.maxE) * m.nC);
     S->ring_k = A(m.nC);
+    if (S->p.mode == LTS_MODE_LTS3) {
+        S->q_side = A(m.nV);
+        S->ring_c_side = A(static_cast<size_t>(m.maxE) * m.nC);
+        S->ring_k_side = A(m.nC);
+    }
     S->flag = static_cast<int*>(S->arena.alloc(sizeof(int), err));
     S->stage_c = static_cast<double*>(S->arena.alloc(sizeof(double) * m.nC, err));
     S->stage_e = static_cast<double*>(S->arena.alloc(sizeof(double) * m.nE, err));
@@ -941,8 +975,8 @@ void lts_regions_destroy(lts_regions r) { release_regions(r); }
 
 int lts_regions_labels(lts_regions r, int8_t* cl, int8_t* el) {
     if (!r) return set_error(LTS_EINVAL, "null regions");
-    static const int8_t cmap[NBANDS] = {0, 0, 1, 2, 3, 4, 5, 5, 5};
-    static const int8_t emap[NBANDS] = {0, 0, 1, 1, 3, 4, 5, 5, 5};
+    static const int8_t cmap[NBANDS] = {0, 0, 1, 2, 3, 4, 5, 5, 5, 5, 5, 5};
+    static const int8_t emap[NBANDS] = {0, 0, 1, 1, 3, 4, 5, 5, 5, 5, 5, 5};
     if (cl)
         for (size_t i = 0; i < r->r.cband.size(); ++i) cl[i] = cmap[r->r.cband[i]];
     if (el)
@@ -1037,6 +1071,8 @@ int lts_state_create(lts_mesh mesh, lts_regions reg, const double* h0, const dou
     S->kc.block = bs;
     S->tsz = which ? 8 : 4;
     S->kc.maxdeg = mesh->m.maxE <= 8 ? 8 : MAX_DEGREE;
+    if (p->coarse_schedule < LTS_COARSE_STEP4 || p->coarse_schedule > LTS_COARSE_SERIAL)
+        return set_error(LTS_EINVAL, "coarse_schedule must be LTS_COARSE_STEP4, _FAR or _SERIAL");
     if (p->kernel_path != 0 && p->kernel_path != 1)
         return set_error(LTS_EINVAL, "kernel_path must be 0 (three launches) or 1 (fused tiles)");
     {

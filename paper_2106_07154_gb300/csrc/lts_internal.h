@@ -9,10 +9,12 @@
 namespace lts {
 
 // Bands of the band ordering (cells; an edge takes the smaller band of its
-// two cells, a vertex the smallest band of its three cells).
+// two cells, a vertex the smallest band of its three cells).  C1..C5 are the
+// coarse layers at edge distance 1..5 from I2: the halos the near-interface
+// coarse phases read, so the far coarse bands can run concurrently.
 enum Band : int {
     B_FDEEP = 0, B_F3 = 1, B_F2 = 2, B_F1 = 3, B_I1 = 4, B_I2 = 5, B_C1 = 6, B_C2 = 7,
-    B_CREST = 8, NBANDS = 9
+    B_C3 = 8, B_C4 = 9, B_C5 = 10, B_CREST = 11, NBANDS = 12
 };
 
 // Device tables in band order.  Cell "slot" arrays are slot-major:

@@ -104,6 +104,11 @@ struct lts_state_s {
     void* q = nullptr;
     void* ring_c = nullptr;   // [maxE*nC] per-slot PV contributions
     void* ring_k = nullptr;   // [nC] K_i
+    // intermediates of the concurrent far-coarse branch (its own, so the two
+    // branches never share a buffer)
+    void* q_side = nullptr;
+    void* ring_c_side = nullptr;
+    void* ring_k_side = nullptr;
     int* flag = nullptr;
     double* stage_c = nullptr;   // FP64 staging for I/O (original order)
     double* stage_e = nullptr;

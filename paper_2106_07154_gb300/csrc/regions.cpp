@@ -8,8 +8,8 @@
 // and every edge takes the finer of its two cells' regions, i.e. edges are
 // assigned from the fine to the coarse side (Eq. 5).
 // Bands (order of the device arrays):
-//   0 F deep | 1 F3 | 2 F2 | 3 F1 | 4 I1 | 5 I2 | 6 C1 | 7 C2 | 8 C rest
-// F3 is the fine layer next to F2, C1/C2 the two coarse layers next to I2
+//   0 F deep | 1 F3 | 2 F2 | 3 F1 | 4 I1 | 5 I2 | 6..10 C1..C5 | 11 C rest
+// F3 is the fine layer next to F2, C1..C5 the coarse layers next to I2
 // (the halo layers the restricted right-hand sides read).  Cells are in
 // Hilbert-curve order inside a band, edges follow their lower-indexed cell,
 // vertices their lowest cell.  Adjacent cells differ by at most one band, so
@@ -111,8 +111,7 @@ int compute_regions(const HostMesh& m, const int8_t* fine, int layers, int order
             int d = dout[i];
             if (d <= layers) b = B_I1;
             else if (d <= 2 * layers) b = B_I2;
-            else if (d == 2 * layers + 1) b = B_C1;
-            else if (d == 2 * layers + 2) b = B_C2;
+            else if (d - 2 * layers <= 5) b = B_C1 + (d - 2 * layers - 1);   // C1..C5
             else b = B_CREST;
         }
         r.cband[i] = static_cast<int8_t>(b);

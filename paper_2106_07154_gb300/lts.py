@@ -32,8 +32,11 @@ PATH_FUSED = 1
 LTS_ORDER_HILBERT = 0
 LTS_ORDER_INDEX = 1
 LTS_TUNE_ORDERING = 1
+LTS_COARSE_STEP4 = 0
+LTS_COARSE_FAR = 1
+LTS_COARSE_SERIAL = 2
 
-NBANDS = 9
+NBANDS = 12
 BAND_NAMES = ("F_deep", "F3", "F2", "F1", "I1", "I2", "C1", "C2", "C_rest")
 
 _DP = C.POINTER(C.c_double)
@@ -77,12 +80,18 @@ class lts_params(C.Structure):
                 ("mode", C.c_int32), ("compensated", C.c_int32), ("use_graph", C.c_int32),
                 ("block_size", C.c_int32), ("profile", C.c_int32), ("pdl", C.c_int32),
                 ("kernel_path", C.c_int32), ("stream", C.c_void_p), ("no_l2_hints", C.c_int32),
-                ("serial_step4", C.c_int32)]
+                ("coarse_schedule", C.c_int32)]
+
+
+class lts_tune_entry(C.Structure):
+    _fields_ = [("block_size", C.c_int32), ("kernel_path", C.c_int32), ("pdl", C.c_int32),
+                ("l2_hints", C.c_int32), ("coarse_schedule", C.c_int32), ("ordering", C.c_int32),
+                ("ms", C.c_double)]
 
 
 class lts_tune_report(C.Structure):
     _fields_ = [("candidates", C.c_int32), ("ordering", C.c_int32), ("best_ms", C.c_double),
-                ("default_ms", C.c_double)]
+                ("default_ms", C.c_double), ("entry", lts_tune_entry * 32)]
 
 
 class lts_ensemble_params(C.Structure):
@@ -311,15 +320,15 @@ def lts_regions_permutation(reg_h, nCells: int, nEdges: int, nVertices: int):
 def make_params(g: float, dt: float, precision: int = LTS_FP32, mode: int = LTS_MODE_LTS3,
                 compensated: bool = True, use_graph: bool = True, block_size: int = 0,
                 profile: int = 0, stream: int | None = None, pdl: bool = True,
-                kernel_path: int = 0, l2_hints: bool = True, serial_step4: bool = False):
+                kernel_path: int = 0, l2_hints: bool = True, coarse_schedule: int = 0):
     return lts_params(g, dt, precision, mode, int(compensated), int(use_graph), block_size,
                       int(profile), int(pdl), int(kernel_path), stream, int(not l2_hints),
-                      int(serial_step4))
+                      int(coarse_schedule))
 
 
 def params_dict(p: lts_params) -> dict:
     return {"block_size": p.block_size, "kernel_path": p.kernel_path, "pdl": bool(p.pdl),
-            "l2_hints": not p.no_l2_hints, "serial_step4": bool(p.serial_step4),
+            "l2_hints": not p.no_l2_hints, "coarse_schedule": int(p.coarse_schedule),
             "use_graph": bool(p.use_graph)}
 
 
@@ -331,8 +340,10 @@ def lts_autotune(mesh_h, reg_h, h0, u0, base: lts_params, steps: int = 20,
     _check(lib().lts_autotune(mesh_h, reg_h, _f64(h0).ctypes.data, _f64(u0).ctypes.data,
                               C.byref(base), int(steps), LTS_TUNE_ORDERING if tune_ordering else 0,
                               C.byref(best), C.byref(rep)))
+    table = [{f: getattr(e, f) for f, _ in lts_tune_entry._fields_}
+             for e in rep.entry[:min(rep.candidates, 32)]]
     return best, {"candidates": rep.candidates, "ordering": rep.ordering, "best_ms": rep.best_ms,
-                  "default_ms": rep.default_ms}
+                  "default_ms": rep.default_ms, "table": table}
 
 
 def lts_state_create_p(mesh_h, reg_h, h0, u0, p: lts_params):
@@ -346,9 +357,9 @@ def lts_state_create(mesh_h, reg_h, h0, u0, g: float, dt: float, precision: int 
                      mode: int = LTS_MODE_LTS3, compensated: bool = True, use_graph: bool = True,
                      block_size: int = 0, profile: int = 0, stream: int | None = None,
                      pdl: bool = True, kernel_path: int = 0, l2_hints: bool = True,
-                     serial_step4: bool = False):
+                     coarse_schedule: int = 0):
     p = make_params(g, dt, precision, mode, compensated, use_graph, block_size, profile, stream,
-                    pdl, kernel_path, l2_hints, serial_step4)
+                    pdl, kernel_path, l2_hints, coarse_schedule)
     h = C.c_void_p()
     _check(lib().lts_state_create(mesh_h, reg_h, _f64(h0).ctypes.data, _f64(u0).ctypes.data,
                                   C.byref(p), C.byref(h)))
@@ -485,7 +496,7 @@ class Model:
                  use_graph: bool = True, block_size: int = 0, profile: int = 0,
                  interface_layers: int = 1, stream: int | None = None, pdl: bool = True,
                  kernel_path: int = 0, tile_cells: int = 0, l2_hints: bool = True,
-                 serial_step4: bool = False, ordering: int = LTS_ORDER_HILBERT,
+                 coarse_schedule: int = 0, ordering: int = LTS_ORDER_HILBERT,
                  autotune: int = 0, tune_ordering: bool = False):
         """autotune > 0: time that many coarse steps per candidate configuration
         (lts_autotune) and build the state with the fastest; the choice is in
@@ -502,7 +513,7 @@ class Model:
         if ordering != LTS_ORDER_HILBERT:
             lts_regions_ordering(self.reg_h, ordering)
         p = make_params(g, dt, precision, mode, compensated, use_graph, block_size, profile, stream,
-                        pdl, kernel_path, l2_hints, serial_step4)
+                        pdl, kernel_path, l2_hints, coarse_schedule)
         if autotune:
             p, rep = lts_autotune(self.mesh_h, self.reg_h, h0, u0, p, autotune, tune_ordering)
             self.tuned = dict(params_dict(p), **rep)

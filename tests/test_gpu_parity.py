@@ -47,9 +47,9 @@ def run_gpu(w, n, precision, M=None, mode=lts.LTS_MODE_LTS3, dt=None, use_graph=
     return h, u, d
 
 
-def run_oracle(w, n, M=None, fine=None, dt=None):
+def run_oracle(w, n, M=None, fine=None, dt=None, layers=1):
     o = oracle.Oracle(w.mesh)
-    cl, el = o.regions(w.fine_mask if fine is None else fine)
+    cl, el = o.regions(w.fine_mask if fine is None else fine, layers)
     return o.lts3(w.h0, w.u0, cl, el, M or w.M, dt or w.dt, n, g=w.g)
 
 
@@ -207,10 +207,11 @@ def test_nonfinite_is_reported(sphw):
 
 
 def test_options_do_not_change_results(sphw):
-    """Cell ordering, L2 hints and Step-4 placement change only the access
-    pattern and the schedule, never an element's arithmetic."""
+    """Cell ordering, L2 hints and the coarse schedule change only the access
+    pattern and the launch order, never an element's arithmetic."""
     a = run_gpu(sphw, 6, lts.LTS_FP32)
-    for kw in ({"ordering": lts.LTS_ORDER_INDEX}, {"l2_hints": False}, {"serial_step4": True}):
+    for kw in ({"ordering": lts.LTS_ORDER_INDEX}, {"l2_hints": False},
+               {"coarse_schedule": lts.LTS_COARSE_FAR}, {"coarse_schedule": lts.LTS_COARSE_SERIAL}):
         with lts.Model(sphw.mesh, sphw.fine_mask, sphw.M, sphw.h0, sphw.u0, sphw.dt,
                        precision=lts.LTS_FP32, **kw) as m:
             m.step(6)
@@ -228,3 +229,15 @@ def test_autotune_picks_a_valid_config(sphw):
         m.step(4)
         h, u, _ = m.read()
     assert np.array_equal(h, a[0]) and np.array_equal(u, a[1])
+
+
+@pytest.mark.parametrize("layers", [2, 3])
+@pytest.mark.parametrize("precision", [lts.LTS_FP64, lts.LTS_FP32])
+def test_thick_interfaces_match_oracle(sphw, layers, precision):
+    """Interfaces L cells thick (reading: I1 = distance 1..L from F, I2 =
+    L+1..2L), in both precisions."""
+    n = 20
+    h, u, _ = run_gpu(sphw, n, precision, layers=layers)
+    rh, ru = run_oracle(sphw, n, layers=layers)
+    th, tu = (TOL64, TOL64) if precision == lts.LTS_FP64 else (TOL32_H, TOL32_U)
+    assert rel(h, rh) <= th and rel(u, ru) <= tu, (rel(h, rh), rel(u, ru))

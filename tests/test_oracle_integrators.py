@@ -28,8 +28,9 @@ def sphw():
 
 # ------------------------------------------------------------------ regions
 
-def _bfs_labels(mesh, fine):
-    """Independent restatement of Eqs. (3)-(5) by breadth-first distances."""
+def _bfs_labels(mesh, fine, layers=1):
+    """Independent restatement of Eqs. (3)-(5) by breadth-first distances
+    (interfaces `layers` cells thick: I1 = distance 1..L, I2 = L+1..2L)."""
     n = mesh["nCells"]
     coc, noc = mesh["cellsOnCell"], mesh["nEdgesOnCell"]
     nb = [list(coc[i, :noc[i]]) for i in range(n)]
@@ -54,8 +55,8 @@ def _bfs_labels(mesh, fine):
     dout = bfs(np.nonzero(isF)[0], ~isF | True)        # distance from F
     din = bfs(np.nonzero(~isF)[0], isF | True)          # distance from outside F
     cl = np.full(n, 5, np.int8)
-    cl[(dout == 1)] = 3
-    cl[(dout == 2)] = 4
+    cl[(dout >= 1) & (dout <= layers)] = 3
+    cl[(dout > layers) & (dout <= 2 * layers)] = 4
     cl[isF] = 0
     cl[isF & (din == 2)] = 1
     cl[isF & (din == 1) & np.array([any((not isF[j]) and dout[j] == 1 for j in nb[i]) for i in range(n)])] = 2
@@ -66,11 +67,12 @@ def _bfs_labels(mesh, fine):
 
 
 @pytest.mark.parametrize("which", ["hex", "sph"])
-def test_regions_match_brute_force(which, hexw, sphw):
+@pytest.mark.parametrize("layers", [1, 2, 3])
+def test_regions_match_brute_force(which, layers, hexw, sphw):
     w = hexw if which == "hex" else sphw
     o = oracle.Oracle(w.mesh)
-    cl, el = o.regions(w.fine_mask)
-    bcl, bel = _bfs_labels(w.mesh, w.fine_mask)
+    cl, el = o.regions(w.fine_mask, layers)
+    bcl, bel = _bfs_labels(w.mesh, w.fine_mask, layers)
     assert np.array_equal(cl, bcl)
     assert np.array_equal(el, bel)
     # the sets form a disjoint cover and are all present
@@ -261,3 +263,23 @@ def test_balanced_flow_stays_steady():
     assert drift_c < 5e-3 * 6000.0
     assert drift_f < 0.6 * drift_c, (drift_c, drift_f)
     assert diff_c < 0.05 * drift_c, (diff_c, drift_c)
+
+
+@pytest.mark.parametrize("layers", [2, 3])
+def test_thick_interfaces_conserve_mass_and_reduce_to_ssprk3(sphw, layers):
+    """Interfaces L cells thick (the speed-up runs of Section 3): mass stays
+    conserved to roundoff, and M = 1 is SSPRK3 bit for bit."""
+    w = sphw
+    o = oracle.Oracle(w.mesh)
+    cl, el = o.regions(w.fine_mask, layers)
+    c1, _ = o.regions(w.fine_mask, 1)
+    assert (cl == 3).sum() > (c1 == 3).sum() and (cl == 4).sum() > (c1 == 4).sum()
+    h, u = o.lts3(w.h0, w.u0, cl, el, w.M, w.dt, 5, g=w.g)
+    m0 = o.mass(w.h0)
+    assert abs(o.mass(h) - m0) <= 1e-13 * m0
+    dt1 = w.dt / w.M
+    ha, ua = o.lts3(w.h0, w.u0, cl, el, 1, dt1, 4, g=w.g)
+    hb, ub = o.ssprk3(w.h0, w.u0, dt1, 4, g=w.g)
+    assert np.array_equal(ha, hb) and np.array_equal(ua, ub)
+    with pytest.raises(ValueError):
+        o.regions(w.fine_mask, 0)
