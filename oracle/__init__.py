@@ -60,6 +60,10 @@ def lib():
         L.or_rk4.argtypes = [C.c_void_p, C.c_void_p, C.c_double, C.c_int, _f64p, _f64p]
         L.or_lts3.argtypes = [C.c_void_p, C.c_void_p, _i8p, _i8p, C.c_int, C.c_double, C.c_int,
                               C.c_int, _f64p, _f64p]
+        L.or_lts2.argtypes = [C.c_void_p, C.c_void_p, _i8p, _i8p, C.c_int, C.c_double, C.c_int,
+                              C.c_int, _f64p, _f64p]
+        L.or_ssprk2.argtypes = [C.c_void_p, C.c_void_p, C.c_double, C.c_int, _f64p, _f64p]
+        L.or_lts2_predict_coeffs.argtypes = [C.c_int, C.c_int, C.c_int, _f64p]
         L.or_mass.restype = C.c_double
         L.or_mass.argtypes = [C.c_void_p, _f64p]
         L.or_energy.restype = C.c_double
@@ -194,6 +198,27 @@ class Oracle:
         lib().or_ssprk3(self._h, C.addressof(s), dt, nsteps, h, u)
         return h, u
 
+    def ssprk2(self, h, u, dt, nsteps, g=9.81, lam_c=None, lam_e=None):
+        """Algorithm 2.1 (SSPRK2)."""
+        h = np.array(h, np.float64)
+        u = np.array(u, np.float64)
+        s = self._sys(g, lam_c, lam_e)
+        lib().or_ssprk2(self._h, C.addressof(s), dt, nsteps, h, u)
+        return h, u
+
+    def lts2(self, h, u, cell_label, edge_label, M, dt, nsteps, g=9.81, step5_form=0,
+             lam_c=None, lam_e=None):
+        """Algorithm 2.2, LTS2 branches."""
+        h = np.array(h, np.float64)
+        u = np.array(u, np.float64)
+        s = self._sys(g, lam_c, lam_e)
+        rc = lib().or_lts2(self._h, C.addressof(s), np.ascontiguousarray(cell_label, np.int8),
+                           np.ascontiguousarray(edge_label, np.int8), int(M), float(dt),
+                           int(nsteps), int(step5_form), h, u)
+        if rc != 0:
+            raise ValueError("or_lts2 failed")
+        return h, u
+
     def rk4(self, h, u, dt, nsteps, g=9.81, lam_c=None, lam_e=None):
         """Classical RK4, the reference-solution generator of Section 3.2."""
         h = np.array(h, np.float64)
@@ -223,8 +248,11 @@ class Oracle:
                                      np.ascontiguousarray(u, np.float64)))
 
 
-def predict_coeffs(k: int, M: int, stage: int) -> np.ndarray:
+def predict_coeffs(k: int, M: int, stage: int, order: int = 3) -> np.ndarray:
     """Steps 3.1.1/3.2.1/3.3.1: (c_old, c_1st, c_2nd) of the I1 prediction."""
     c = np.zeros(3)
-    lib().or_lts3_predict_coeffs(k, M, stage, c)
+    if order == 2:
+        lib().or_lts2_predict_coeffs(k, M, stage, c)
+    else:
+        lib().or_lts3_predict_coeffs(k, M, stage, c)
     return c

@@ -502,6 +502,27 @@ void or_rk4(const or_mesh* m, const or_system* sys, double dt, int nsteps,
     free(k3h); free(k3u); free(k4h); free(k4u);
 }
 
+/* Algorithm 2.1 with SSPRK2: omega_old = omega_1st = omega_rhs = 1/2. */
+static double ssp2_stage2(double x_old, double x_1st, double rhs, double dt) {
+    return 0.5 * x_old + 0.5 * x_1st + 0.5 * dt * rhs;
+}
+
+void or_ssprk2(const or_mesh* m, const or_system* sys, double dt, int nsteps,
+               double* h, double* u) {
+    int nC = m->nC, nE = m->nE;
+    double *h1 = xmalloc(nC * sizeof(double)), *u1 = xmalloc(nE * sizeof(double));
+    double *H = xmalloc(nC * sizeof(double)), *U = xmalloc(nE * sizeof(double));
+    for (int n = 0; n < nsteps; ++n) {
+        or_rhs(m, sys, h, u, H, U);
+        for (int i = 0; i < nC; ++i) h1[i] = ssp_stage1(h[i], H[i], dt);
+        for (int e = 0; e < nE; ++e) u1[e] = ssp_stage1(u[e], U[e], dt);
+        or_rhs(m, sys, h1, u1, H, U);
+        for (int i = 0; i < nC; ++i) h[i] = ssp2_stage2(h[i], h1[i], H[i], dt);
+        for (int e = 0; e < nE; ++e) u[e] = ssp2_stage2(u[e], u1[e], U[e], dt);
+    }
+    free(h1); free(u1); free(H); free(U);
+}
+
 /* ------------------------------------------------------------------ LTS3 */
 
 /* Steps 3.1.1 / 3.2.1 / 3.3.1 for LTS3:
@@ -669,6 +690,124 @@ int or_lts3(const or_mesh* m, const or_system* sys, const signed char* cl,
     free(h_old); free(u_old); free(h_1st); free(u_1st); free(h_2nd); free(u_2nd);
     free(h_oldk); free(u_oldk); free(h_1stk); free(u_1stk); free(h_2ndk); free(u_2ndk);
     free(H1); free(H2); free(H3); free(U1); free(U2); free(U3); free(H); free(U);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ LTS2 */
+
+/* Steps 3.1.1 / 3.2.1 for LTS2: alpha_k = k/M, beta_k = (k+1)/M and the
+ * tilde coefficients are 0, so x = (1 - a) x_old + a x_1st. */
+void or_lts2_predict_coeffs(int k, int M, int stage, double* c) {
+    double a = stage == 1 ? (double)k / (double)M : (double)(k + 1) / (double)M;
+    c[0] = 1.0 - a;
+    c[1] = a;
+    c[2] = 0.0;
+}
+
+int or_lts2(const or_mesh* m, const or_system* sys, const signed char* cl,
+            const signed char* el, int M, double dt, int nsteps, int step5_form,
+            double* h, double* u) {
+    if (M < 1) return -1;
+    int nC = m->nC, nE = m->nE;
+    size_t sc = (size_t)nC * sizeof(double), se = (size_t)nE * sizeof(double);
+    double *h_old = xmalloc(sc), *u_old = xmalloc(se);
+    double *h_1st = xmalloc(sc), *u_1st = xmalloc(se);
+    double *h_2nd = xmalloc(sc), *u_2nd = xmalloc(se);
+    double *h_oldk = xmalloc(sc), *u_oldk = xmalloc(se);
+    double *h_1stk = xmalloc(sc), *u_1stk = xmalloc(se);
+    double *H1 = xmalloc(sc), *H2 = xmalloc(sc);
+    double *U1 = xmalloc(se), *U2 = xmalloc(se);
+    double *H = xmalloc(sc), *U = xmalloc(se);
+    double dtM = dt / (double)M;
+    double c[3];
+
+    for (int n = 0; n < nsteps; ++n) {
+        memcpy(h_old, h, sc); memcpy(u_old, u, se);
+        memcpy(h_1st, h_old, sc); memcpy(u_1st, u_old, se);
+        memcpy(h_2nd, h_old, sc); memcpy(u_2nd, u_old, se);
+
+        /* Step 1: first stage on I1 u I2 u C (no Fbar for LTS2). */
+        or_rhs(m, sys, h_old, u_old, H, U);
+        for (int i = 0; i < nC; ++i) if (cl[i] >= 3) h_1st[i] = ssp_stage1(h_old[i], H[i], dt);
+        for (int e = 0; e < nE; ++e) if (el[e] >= 3) u_1st[e] = ssp_stage1(u_old[e], U[e], dt);
+
+        /* Step 2: second stage on C only. */
+        or_rhs(m, sys, h_1st, u_1st, H, U);
+        for (int i = 0; i < nC; ++i) if (C_C(cl[i])) h_2nd[i] = ssp2_stage2(h_old[i], h_1st[i], H[i], dt);
+        for (int e = 0; e < nE; ++e) if (el[e] == 5) u_2nd[e] = ssp2_stage2(u_old[e], u_1st[e], U[e], dt);
+
+        /* Step 3 (reading R4: the stage vectors start from the coarse stage
+         * values everywhere; two correction terms for LTS2). */
+        memcpy(h_oldk, h_old, sc); memcpy(u_oldk, u_old, se);
+        memcpy(h_1stk, h_1st, sc); memcpy(u_1stk, u_1st, se);
+        for (int i = 0; i < nC; ++i) H1[i] = H2[i] = 0.0;
+        for (int e = 0; e < nE; ++e) U1[e] = U2[e] = 0.0;
+
+        for (int k = 0; k < M; ++k) {
+            /* 3.1.1 predict I1 */
+            or_lts2_predict_coeffs(k, M, 1, c);
+            for (int i = 0; i < nC; ++i)
+                if (C_I1(cl[i])) h_oldk[i] = c[0] * h_old[i] + c[1] * h_1st[i] + c[2] * h_2nd[i];
+            for (int e = 0; e < nE; ++e)
+                if (el[e] == 3) u_oldk[e] = c[0] * u_old[e] + c[1] * u_1st[e] + c[2] * u_2nd[e];
+            /* 3.1.2 */
+            or_rhs(m, sys, h_oldk, u_oldk, H, U);
+            for (int i = 0; i < nC; ++i) if (C_I(cl[i])) H1[i] = H1[i] + H[i];
+            for (int e = 0; e < nE; ++e) if (el[e] == 3 || el[e] == 4) U1[e] = U1[e] + U[e];
+            /* 3.1.3 */
+            for (int i = 0; i < nC; ++i)
+                if (C_FINE(cl[i])) h_1stk[i] = ssp_stage1(h_oldk[i], H[i], dtM);
+            for (int e = 0; e < nE; ++e)
+                if (E_FINE(el[e])) u_1stk[e] = ssp_stage1(u_oldk[e], U[e], dtM);
+
+            /* 3.2.1 predict I1 */
+            or_lts2_predict_coeffs(k, M, 2, c);
+            for (int i = 0; i < nC; ++i)
+                if (C_I1(cl[i])) h_1stk[i] = c[0] * h_old[i] + c[1] * h_1st[i] + c[2] * h_2nd[i];
+            for (int e = 0; e < nE; ++e)
+                if (el[e] == 3) u_1stk[e] = c[0] * u_old[e] + c[1] * u_1st[e] + c[2] * u_2nd[e];
+            /* 3.2.2 */
+            or_rhs(m, sys, h_1stk, u_1stk, H, U);
+            for (int i = 0; i < nC; ++i) if (C_I(cl[i])) H2[i] = H2[i] + H[i];
+            for (int e = 0; e < nE; ++e) if (el[e] == 3 || el[e] == 4) U2[e] = U2[e] + U[e];
+            /* 3.2.3 (reading R3); LTS2: h^new = h^2nd, then h^{old,k+1} = h^new */
+            for (int i = 0; i < nC; ++i)
+                if (C_FINE(cl[i])) h_oldk[i] = ssp2_stage2(h_oldk[i], h_1stk[i], H[i], dtM);
+            for (int e = 0; e < nE; ++e)
+                if (E_FINE(el[e])) u_oldk[e] = ssp2_stage2(u_oldk[e], u_1stk[e], U[e], dtM);
+        }
+
+        /* Step 4 (LTS2): h^new = h^2nd on C. */
+        for (int i = 0; i < nC; ++i) if (C_C(cl[i])) h[i] = h_2nd[i];
+        for (int e = 0; e < nE; ++e) if (el[e] == 5) u[e] = u_2nd[e];
+        /* fine sets: the last substep */
+        for (int i = 0; i < nC; ++i) if (C_FINE(cl[i])) h[i] = h_oldk[i];
+        for (int e = 0; e < nE; ++e) if (E_FINE(el[e])) u[e] = u_oldk[e];
+
+        /* Step 5 (theta = 1/2, 1/2, 0), printed or as the replay of the two
+         * interface stages (reading R5). */
+        for (int i = 0; i < nC; ++i) {
+            if (!C_I(cl[i])) continue;
+            if (step5_form == 1) {
+                h[i] = h_old[i] + dtM * (H1[i] / 2.0 + H2[i] / 2.0);
+            } else {
+                double x1 = ssp_stage1(h_old[i], H1[i], dtM);
+                h[i] = ssp2_stage2(h_old[i], x1, H2[i], dtM);
+            }
+        }
+        for (int e = 0; e < nE; ++e) {
+            if (!(el[e] == 3 || el[e] == 4)) continue;
+            if (step5_form == 1) {
+                u[e] = u_old[e] + dtM * (U1[e] / 2.0 + U2[e] / 2.0);
+            } else {
+                double x1 = ssp_stage1(u_old[e], U1[e], dtM);
+                u[e] = ssp2_stage2(u_old[e], x1, U2[e], dtM);
+            }
+        }
+    }
+    free(h_old); free(u_old); free(h_1st); free(u_1st); free(h_2nd); free(u_2nd);
+    free(h_oldk); free(u_oldk); free(h_1stk); free(u_1stk);
+    free(H1); free(H2); free(U1); free(U2); free(H); free(U);
     return 0;
 }
 

@@ -100,6 +100,9 @@ void or_rhs(const or_mesh* m, const or_system* sys, const double* h, const doubl
 /* Algorithm 2.1 (SSPRK3), n steps of size dt, (h,u) advanced in place. */
 void or_ssprk3(const or_mesh* m, const or_system* sys, double dt, int nsteps,
                double* h, double* u);
+/* Algorithm 2.1 (SSPRK2: omega = 1/2, 1/2, 1/2), n steps of size dt. */
+void or_ssprk2(const or_mesh* m, const or_system* sys, double dt, int nsteps,
+               double* h, double* u);
 /* Classical RK4 (reference-solution generator, Section 3.2). */
 void or_rk4(const or_mesh* m, const or_system* sys, double dt, int nsteps,
             double* h, double* u);
@@ -109,6 +112,16 @@ void or_rk4(const or_mesh* m, const or_system* sys, double dt, int nsteps,
 int or_lts3(const or_mesh* m, const or_system* sys, const signed char* cell_label,
             const signed char* edge_label, int M, double dt, int nsteps,
             int step5_form, double* h, double* u);
+
+/* Algorithm 2.2 (LTS2 branches): Step 1 on I1 u I2 u C, Step 2 on C,
+ * Step 3 with two stages per substep (alpha_k = k/M, beta_k = (k+1)/M, no
+ * tilde terms), Step 4 h^new = h^2nd on C, Step 5 with theta = 1/2, 1/2.
+ * step5_form as for or_lts3. */
+int or_lts2(const or_mesh* m, const or_system* sys, const signed char* cell_label,
+            const signed char* edge_label, int M, double dt, int nsteps,
+            int step5_form, double* h, double* u);
+/* Steps 3.1.1 / 3.2.1 coefficients for LTS2 (stage 1 or 2), as for LTS3. */
+void or_lts2_predict_coeffs(int k, int M, int stage, double* c);
 
 /* Diagnostics: mass sum_i A_i h_i and energy sum_i A_i h_i (K_i + g(h_i/2 + b_i)). */
 double or_mass(const or_mesh* m, const double* h);
