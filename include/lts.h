@@ -142,7 +142,8 @@ void lts_mesh_destroy(lts_mesh m);
  * Host only: the first lts_state_create of each precision uploads the
  * band-ordered device tables (FP64 master geometry, FP32/FP64 coefficient
  * copies derived in FP64 and rounded once).
- *   order:            3 (LTS3); other values -> LTS_EINVAL.
+ *   order:            3 (LTS3) or 2 (LTS2, the second-order branches of
+ *                     Algorithm 2.2); other values -> LTS_EINVAL.
  *   M:                fine substeps per coarse step, >= 1.
  *   interface_layers: cells per interface layer (>= 1): I1 = cells at
  *                     edge-distance 1..L from F, I2 = distance L+1..2L.
@@ -185,8 +186,11 @@ int lts_regions_permutation(lts_regions r, int32_t* perm_cell, int32_t* perm_edg
 
 #define LTS_FP32 0
 #define LTS_FP64 1
-#define LTS_MODE_LTS3   0   /* Algorithm 2.2 (LTS3), coarse step dt, M from regions */
+#define LTS_MODE_LTS    0   /* Algorithm 2.2 of the regions' order (LTS2 or LTS3),
+                               coarse step dt, M from the regions                    */
+#define LTS_MODE_LTS3   0   /* the same value (the regions' order decides)           */
 #define LTS_MODE_SSPRK3 1   /* Algorithm 2.1 (SSPRK3) on the whole mesh, step dt    */
+#define LTS_MODE_SSPRK2 2   /* Algorithm 2.1 (SSPRK2) on the whole mesh, step dt    */
 
 #define LTS_COARSE_STEP4  0
 #define LTS_COARSE_FAR    1
@@ -196,7 +200,7 @@ typedef struct lts_params {
     double g;               /* gravity [m s^-2]                                        */
     double dt;              /* coarse step (LTS3) or step (SSPRK3) [s]                 */
     int32_t precision;      /* LTS_FP32 or LTS_FP64                                    */
-    int32_t mode;           /* LTS_MODE_LTS3 or LTS_MODE_SSPRK3                        */
+    int32_t mode;           /* LTS_MODE_LTS, LTS_MODE_SSPRK3 or LTS_MODE_SSPRK2        */
     int32_t compensated;    /* FP32: carry a compensation word with every state value
                                (stage sums and flux divergence compensated); ignored
                                for FP64                                                */

@@ -78,17 +78,22 @@ extern "C" int lts_autotune(lts_mesh m, lts_regions r, const double* h0, const d
     if (!m || !r || !h0 || !u0 || !base || !best) return set_error(LTS_EINVAL, "null argument");
     if (steps < 1 || steps > 100000) return set_error(LTS_EINVAL, "steps must be in [1, 100000]");
     std::vector<Candidate> cands;
-    const bool lts3 = base->mode == LTS_MODE_LTS3;
+    const bool lts3 = base->mode == LTS_MODE_LTS && r->r.order == 3;
+    const bool lts = base->mode == LTS_MODE_LTS;
+    const bool fused_ok = base->mode == LTS_MODE_SSPRK3 || lts3;
     // three-launch path: every combination; fused tiles (one block per
     // 256-cell tile): with PDL, without the FAR schedule
     for (int block : {128, 256})
         for (int pdl = 1; pdl >= 0; --pdl)
             for (int no_l2 = 0; no_l2 <= 1; ++no_l2)
-                for (int sched = 0; sched <= (lts3 ? 2 : 0); ++sched)
+                for (int sched = 0; sched <= (lts ? 2 : 0); ++sched) {
+                    if (sched == LTS_COARSE_FAR && !lts3) continue;   // LTS2: no far Steps 1/2
                     cands.push_back({block, 0, pdl, no_l2, sched});
-    for (int no_l2 = 0; no_l2 <= 1; ++no_l2)
-        for (int sched : {LTS_COARSE_STEP4, LTS_COARSE_SERIAL})
-            if (lts3 || sched == LTS_COARSE_STEP4) cands.push_back({256, 1, 1, no_l2, sched});
+                }
+    if (fused_ok)
+        for (int no_l2 = 0; no_l2 <= 1; ++no_l2)
+            for (int sched : {LTS_COARSE_STEP4, LTS_COARSE_SERIAL})
+                if (lts3 || sched == LTS_COARSE_STEP4) cands.push_back({256, 1, 1, no_l2, sched});
     // every candidate once, then the three fastest twice more (best of three)
     for (Candidate& c : cands) {
         int rc = time_config(m, r, h0, u0, apply(*base, c), steps, &c.ms);

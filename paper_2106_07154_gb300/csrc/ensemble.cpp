@@ -462,7 +462,8 @@ int lts_ensemble_create(const lts_state* members, int32_t n, const lts_ensemble_
         if (S->reg->device != dev) return set_error(LTS_EINVAL, "member %d lives on another device", m);
         if (S->kc.precision != s0->kc.precision || S->kc.comp != s0->kc.comp)
             return set_error(LTS_EINVAL, "member %d: precision or compensation differs from member 0", m);
-        if (S->p.mode != s0->p.mode) return set_error(LTS_EINVAL, "member %d: mode differs from member 0", m);
+        if (S->p.mode != s0->p.mode || S->reg->r.order != s0->reg->r.order)
+            return set_error(LTS_EINVAL, "member %d: mode or order differs from member 0", m);
         if (S->p.kernel_path != 0) return set_error(LTS_EINVAL, "member %d: ensembles need kernel_path 0", m);
         if (S->p.g != s0->p.g) return set_error(LTS_EINVAL, "member %d: g differs from member 0", m);
         if (S->kc.block != s0->kc.block) return set_error(LTS_EINVAL, "member %d: block size differs", m);

@@ -609,12 +609,12 @@ __device__ __forceinline__ void pointwise(const DevSeg<T>& s, int i) {
         dh[i - s.base] = sh[i - s.base2];
         if (COMP) dl[i - s.base] = sl[i - s.base2];
     } else if (s.type == SEG_REPLAY) {
-        // Step 5 as the replay of the three interface stages (reading R5).
+        // Step 5 as the replay of the interface stages (reading R5): three
+        // stages for LTS3, two for LTS2 (flag 2: x_new = x2).
         const T* oh = (const T*)s.p[0];
         const T* ol = (const T*)s.p[1];
         const T* a1 = (const T*)s.p[2];
         const T* a2 = (const T*)s.p[3];
-        const T* a3 = (const T*)s.p[4];
         T* outh = (T*)s.p[5];
         T* outl = (T*)s.p[6];
         const int k = i - s.base;
@@ -622,7 +622,13 @@ __device__ __forceinline__ void pointwise(const DevSeg<T>& s, int i) {
         T x1h, x1l, x2h, x2l, yh, yl;
         combine<T, COMP>(xh, xl, xh, xl, T(0), s.c[0], a1[k], x1h, x1l);
         combine<T, COMP>(xh, xl, x1h, x1l, s.c[3], s.c[1], a2[k], x2h, x2l);
-        combine<T, COMP>(xh, xl, x2h, x2l, s.c[4], s.c[2], a3[k], yh, yl);
+        if (s.flag == 2) {
+            yh = x2h;
+            yl = x2l;
+        } else {
+            const T* a3 = (const T*)s.p[4];
+            combine<T, COMP>(xh, xl, x2h, x2l, s.c[4], s.c[2], a3[k], yh, yl);
+        }
         outh[i] = yh;
         if (COMP) outl[i] = yl;
     }
@@ -749,8 +755,8 @@ DevSeg<T> to_dev(const SegDesc& s, int block0) {
     o.block0 = block0;
     o.pad = s.type == SEG_TILE ? s.flag2 : 0;
     for (int m = 0; m < 6; ++m) o.c[m] = static_cast<T>(m < 4 ? s.c[m] : 0.0);
-    if (s.type == SEG_REPLAY) {
-        o.c[3] = static_cast<T>(0.75);
+    if (s.type == SEG_REPLAY) {   // the weights a of the replayed stages 2 and 3
+        o.c[3] = static_cast<T>(s.flag == 2 ? 0.5 : 0.75);
         o.c[4] = static_cast<T>(1.0 / 3.0);
     }
     for (int m = 0; m < 10; ++m) o.p[m] = s.p[m];

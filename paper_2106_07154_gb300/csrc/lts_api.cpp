@@ -186,7 +186,7 @@ double launch_bytes(const LaunchDesc& d, const RegionsHost& r, int nC, int nE, i
                 bytes += n * T * 2.0 * (1 + c);
                 break;
             case SEG_REPLAY:
-                bytes += n * T * (5.0 + 2.0 * c);
+                bytes += n * T * ((g.flag == 2 ? 4.0 : 5.0) + 2.0 * c);
                 break;
         }
     }
@@ -293,9 +293,11 @@ struct Planner {
         s.p[0] = cell ? S->acc_c[stage] : S->acc_e[stage];
         return s;
     }
-    // x[I1] = prediction (Steps 3.x.1) from x_old (full), P1, P2 (compact)
+    // x[I1] = prediction (Steps 3.x.1) from x_old (full), P1, P2 (compact).
+    // order 2 (LTS2): the tilde coefficients are 0 and P2 is not used (P1
+    // stands in for it, multiplied by 0).
     SegDesc pred(bool cell, const SV& old, const SV& out, int k, int M, int which,
-                 const SV* x2full = nullptr) const {
+                 const SV* x2full = nullptr, int order = 3) const {
         double a, at;
         const double kk = k, MM = M;
         if (which == 1) {          // alpha
@@ -308,6 +310,7 @@ struct Planner {
             a = (2.0 * kk + 1.0) / (2.0 * MM);
             at = (2.0 * kk * kk + 2.0 * kk + 1.0) / (2.0 * MM * MM);
         }
+        if (order == 2) at = 0.0;
         const double c1 = a - at, c2 = 2.0 * at;
         SegDesc s;
         s.type = SEG_PRED;
@@ -320,7 +323,7 @@ struct Planner {
         s.cfam2 = FAM_I1;
         s.flag = (c1 == 0.0 && c2 == 0.0) ? 1 : (c1 == 1.0 && c2 == 0.0) ? 2 : (c1 == 0.0 && c2 == 1.0) ? 3 : 0;
         const SV& p1 = cell ? S->P1c : S->P1e;
-        const SV& p2 = cell ? S->P2c : S->P2e;
+        const SV& p2 = order == 2 ? p1 : (cell ? S->P2c : S->P2e);
         s.p[0] = cell ? old.hh : old.uh;
         s.p[1] = cell ? old.hl : old.ul;
         s.p[2] = cell ? p1.hh : p1.uh;
@@ -358,9 +361,10 @@ struct Planner {
         s.p[3] = cell ? dst.hl : dst.ul;
         return s;
     }
-    SegDesc replay(bool cell, const SV& old, const SV& out, double dtM) const {
+    SegDesc replay(bool cell, const SV& old, const SV& out, double dtM, int order = 3) const {
         SegDesc s;
         s.type = SEG_REPLAY;
+        s.flag = order == 2 ? 2 : 0;
         s.elem = cell ? ELEM_CELL : ELEM_EDGE;
         const int* ofs = cell ? cb : eb;
         s.begin = ofs[B_I1];
@@ -373,8 +377,9 @@ struct Planner {
         s.p[5] = cell ? out.hh : out.uh;
         s.p[6] = cell ? out.hl : out.ul;
         s.c[0] = dtM;
-        s.c[1] = dtM / 4.0;
+        s.c[1] = order == 2 ? dtM / 2.0 : dtM / 4.0;
         s.c[2] = 2.0 * dtM / 3.0;
+        if (order == 2) s.p[4] = s.p[3];   // no third accumulator (never read)
         return s;
     }
     LaunchDesc launch(int kind, const SV& in, std::initializer_list<SegDesc> segs, int key = -1) const {
@@ -532,6 +537,129 @@ void plan_lts3(lts_state_s* S, int parity, std::vector<LaunchDesc>& out) {
     out.erase(std::remove_if(out.begin(), out.end(),
                              [](const LaunchDesc& d) { return d.nseg == 0 && !d.fork && !d.join; }),
               out.end());
+}
+
+// Algorithm 2.2 with its LTS2 branches, three launches per right-hand side.
+// Step 1 (first stage) on I1 u I2 u C; Step 3: two stages per substep with
+// the linear predictions of I1 and two correction terms; Step 2 (second
+// stage on C, x_new = x_2nd there: Step 4) reads only first-stage values
+// that Step 3 leaves alone, so it runs after Step 3 or, for the bands C3
+// and beyond, as a concurrent branch beside it; Step 5 replays the two
+// interface stages.
+void plan_lts2(lts_state_s* S, int parity, std::vector<LaunchDesc>& out) {
+    const RegionsHost& r = S->reg->r;
+    Planner P{S, r, r.cb, r.eb, r.vb, S->kc.comp};
+    const SV& X0 = S->buf[parity];
+    const SV& XN = S->buf[1 - parity];
+    const SV& X1 = S->buf[2];
+    const double dt = S->p.dt;
+    const int M = r.M;
+    const double dtM = dt / M;
+    const int I1 = r.cb[B_I1];
+    const int I1e = r.eb[B_I1];
+    const SegDesc none;
+    const int sched = S->p.profile != 0 ? LTS_COARSE_SERIAL : S->p.coarse_schedule;
+    const bool concurrent = sched != LTS_COARSE_SERIAL;
+    auto ring_halo = [&](int hi) { return hi < B_CREST ? P.ring(hi + 1, hi + 1) : none; };
+    out.clear();
+    // Step 1 on I1 u I2 u C (bands I1..C rest); x_new on I2..C2 holds x_old
+    // while Step 3 reads it as a halo
+    out.push_back(P.launch(0, X0, {P.vert(B_F1, B_CREST), P.copy(true, B_I2, B_C2, X0, XN, 0)},
+                           KEY_STEP1 + 0));
+    out.push_back(P.launch(1, X0, {P.upd(true, B_I1, B_CREST, X0, X0, X1, A1, dt)}, KEY_STEP1 + 1));
+    out.push_back(P.launch(2, X0, {P.upd(false, B_I1, B_CREST, X0, X0, X1, A1, dt),
+                                   P.copy(false, B_I2, B_C2, X0, XN, 0),
+                                   P.copy(true, B_I1, B_I1, X1, S->P1c, I1)}, KEY_STEP1 + 2));
+    const size_t after_step1 = out.size();
+    for (auto& d : out) d.l2 = 2;
+    // Step 3
+    for (int k = 0; k < M; ++k) {
+        const SV& old = (k == 0) ? X0 : XN;
+        for (int s = 1; s <= 2; ++s) {
+            const SV& in = (s == 1) ? old : X1;
+            const SV& o = (s == 1) ? X1 : XN;
+            const double a = (s == 1) ? A1 : 0.5;
+            const double D = (s == 1) ? dtM : dtM / 2.0;
+            SegDesc pc, pe;
+            if (s == 1) {            // I1 at the second stage: beta_k
+                pc = P.pred(true, X0, X1, k, M, 2, nullptr, 2);
+                pe = P.pred(false, X0, X1, k, M, 2, nullptr, 2);
+            } else if (k + 1 < M) {  // I1 at the next substep: alpha_{k+1}
+                pc = P.pred(true, X0, XN, k + 1, M, 1, nullptr, 2);
+                pe = P.pred(false, X0, XN, k + 1, M, 1, nullptr, 2);
+            }
+            const SegDesc snap = (k == 0 && s == 1) ? P.copy(false, B_I1, B_I1, X1, S->P1e, I1e) : none;
+            const int key = KEY_STEP3 + 9 * k + 3 * (s - 1);
+            out.push_back(P.launch(0, in, {P.vert(B_FDEEP, B_C1), snap}, key + 0));
+            out.push_back(P.launch(1, in, {P.upd(true, B_FDEEP, B_F1, old, in, o, a, D),
+                                           P.acc(true, s - 1, k == 0), P.ring(B_C1, B_C1), pc}, key + 1));
+            out.push_back(P.launch(2, in, {P.upd(false, B_FDEEP, B_F1, old, in, o, a, D),
+                                           P.acc(false, s - 1, k == 0), pe}, key + 2));
+        }
+    }
+    for (size_t k = after_step1; k < out.size(); ++k) out[k].l2 = 1;
+    // Step 2 (= Step 4 for LTS2) on C and Step 5
+    std::vector<LaunchDesc> side, tail;
+    if (concurrent) {
+        side.push_back(P.launch(0, X1, {P.vert(B_C2, B_CREST)}, KEY_SIDE + 6));
+        side.push_back(P.launch(1, X1, {P.upd(true, B_C3, B_CREST, X0, X1, XN, 0.5, dt / 2.0)}, KEY_SIDE + 7));
+        side.push_back(P.launch(2, X1, {P.upd(false, B_C3, B_CREST, X0, X1, XN, 0.5, dt / 2.0)}, KEY_SIDE + 8));
+        for (auto& d : side) {
+            d.q = S->q_side;
+            d.ring_c = S->ring_c_side;
+            d.ring_k = S->ring_k_side;
+        }
+    }
+    const int s2_hi = concurrent ? B_C2 : B_CREST;
+    tail.push_back(P.launch(0, X1, {P.vert(B_I2, std::min(s2_hi + 1, (int)B_CREST))}, KEY_TAIL + 0));
+    tail.push_back(P.launch(1, X1, {P.upd(true, B_C1, s2_hi, X0, X1, XN, 0.5, dt / 2.0), ring_halo(s2_hi),
+                                    P.replay(true, X0, XN, dtM, 2)}, KEY_TAIL + 1));
+    tail.push_back(P.launch(2, X1, {P.upd(false, B_C1, s2_hi, X0, X1, XN, 0.5, dt / 2.0),
+                                    P.replay(false, X0, XN, dtM, 2)}, KEY_TAIL + 2));
+    for (auto& d : side) d.l2 = 2;
+    for (auto& d : tail) d.l2 = 2;
+    auto drop = [](std::vector<LaunchDesc>& v) {
+        v.erase(std::remove_if(v.begin(), v.end(), [](const LaunchDesc& d) { return d.nseg == 0; }),
+                v.end());
+    };
+    drop(side);
+    drop(tail);
+    if (!side.empty()) {
+        for (auto& d : side) d.branch = 1;
+        side.front().fork = true;
+        if (!tail.empty()) tail.front().join = true;
+        out.insert(out.begin() + static_cast<long>(after_step1), side.begin(), side.end());
+    }
+    out.insert(out.end(), tail.begin(), tail.end());
+    if (!side.empty() && tail.empty()) {
+        LaunchDesc j;
+        j.join = true;
+        j.key = KEY_TAIL - 1;
+        out.push_back(j);
+    }
+    out.erase(std::remove_if(out.begin(), out.end(),
+                             [](const LaunchDesc& d) { return d.nseg == 0 && !d.fork && !d.join; }),
+              out.end());
+}
+
+// Algorithm 2.1, SSPRK2 on the whole mesh.
+void plan_ssprk2(lts_state_s* S, int parity, std::vector<LaunchDesc>& out) {
+    const RegionsHost& r = S->reg->r;
+    Planner P{S, r, r.cb, r.eb, r.vb, S->kc.comp};
+    const SV& X0 = S->buf[parity];
+    const SV& XN = S->buf[1 - parity];
+    const SV& X1 = S->buf[2];
+    const double dt = S->p.dt;
+    out.clear();
+    const SV* ins[2] = {&X0, &X1};
+    const SV* outs[2] = {&X1, &XN};
+    const double as[2] = {A1, 0.5};
+    const double Ds[2] = {dt, dt / 2.0};
+    for (int s = 0; s < 2; ++s) {
+        out.push_back(P.launch(0, *ins[s], {P.vert(B_FDEEP, B_CREST)}, 3 * s + 0));
+        out.push_back(P.launch(1, *ins[s], {P.upd(true, B_FDEEP, B_CREST, X0, *ins[s], *outs[s], as[s], Ds[s])}, 3 * s + 1));
+        out.push_back(P.launch(2, *ins[s], {P.upd(false, B_FDEEP, B_CREST, X0, *ins[s], *outs[s], as[s], Ds[s])}, 3 * s + 2));
+    }
 }
 
 // The same plan with one fused tile launch per right-hand side.
@@ -760,7 +888,7 @@ int state_alloc(lts_state_s* S) {
     S->q = A(m.nV);
     S->ring_c = A(static_cast<size_t>(m.maxE) * m.nC);
     S->ring_k = A(m.nC);
-    if (S->p.mode == LTS_MODE_LTS3) {
+    if (S->p.mode == LTS_MODE_LTS) {
         S->q_side = A(m.nV);
         S->ring_c_side = A(static_cast<size_t>(m.maxE) * m.nC);
         S->ring_k_side = A(m.nC);
@@ -794,8 +922,14 @@ int write_state(lts_state_s* S, const double* h, const double* u) {
 namespace lts {
 int device_check() { return check_device(); }
 void make_plan(lts_state_s* S, int parity, std::vector<LaunchDesc>& out) {
-    if (S->p.mode == LTS_MODE_LTS3) plan_lts3(S, parity, out);
-    else plan_ssprk3(S, parity, out);
+    if (S->p.mode == LTS_MODE_LTS) {
+        if (S->reg->r.order == 2) plan_lts2(S, parity, out);
+        else plan_lts3(S, parity, out);
+    } else if (S->p.mode == LTS_MODE_SSPRK2) {
+        plan_ssprk2(S, parity, out);
+    } else {
+        plan_ssprk3(S, parity, out);
+    }
 }
 double plan_launch_bytes(const LaunchDesc& d, const RegionsHost& r, int nC, int nE, int nV, size_t T,
                          bool comp) {
@@ -952,7 +1086,7 @@ int lts_regions_set(lts_mesh m, const int8_t* fine_mask, int32_t order, int32_t 
                     lts_regions* out) {
     if (!m || !fine_mask || !out) return set_error(LTS_EINVAL, "null argument");
     *out = nullptr;
-    if (order != 3) return set_error(LTS_EINVAL, "order %d not supported (3 = LTS3)", order);
+    if (order != 2 && order != 3) return set_error(LTS_EINVAL, "order %d not supported (2 = LTS2, 3 = LTS3)", order);
     if (M < 1 || M > 4096) return set_error(LTS_EINVAL, "M must be in [1, 4096]");
     std::unique_ptr<lts_regions_s> R(new (std::nothrow) lts_regions_s);
     if (!R) return set_error(LTS_ENOMEM, "out of host memory");
@@ -965,6 +1099,7 @@ int lts_regions_set(lts_mesh m, const int8_t* fine_mask, int32_t order, int32_t 
     }
     if (rc != LTS_OK) return rc;
     R->r.M = M;
+    R->r.order = order;
     m->ref++;
     R->mesh = m;
     *out = R.release();
@@ -1015,6 +1150,7 @@ int lts_regions_ordering(lts_regions r, int32_t ordering) {
     }
     if (rc != LTS_OK) return rc;
     nr.M = r->r.M;
+    nr.order = r->r.order;
     r->r = std::move(nr);
     r->arena[0].reset();   // device tables are rebuilt on the next state creation
     r->arena[1].reset();
@@ -1048,8 +1184,10 @@ int lts_state_create(lts_mesh mesh, lts_regions reg, const double* h0, const dou
     if (!(p->dt > 0.0) || !(p->g > 0.0)) return set_error(LTS_EINVAL, "dt and g must be > 0");
     if (p->precision != LTS_FP32 && p->precision != LTS_FP64)
         return set_error(LTS_EINVAL, "precision must be LTS_FP32 or LTS_FP64");
-    if (p->mode != LTS_MODE_LTS3 && p->mode != LTS_MODE_SSPRK3)
-        return set_error(LTS_EINVAL, "mode must be LTS_MODE_LTS3 or LTS_MODE_SSPRK3");
+    if (p->mode != LTS_MODE_LTS && p->mode != LTS_MODE_SSPRK3 && p->mode != LTS_MODE_SSPRK2)
+        return set_error(LTS_EINVAL, "mode must be LTS_MODE_LTS, LTS_MODE_SSPRK3 or LTS_MODE_SSPRK2");
+    if (p->kernel_path == 1 && (p->mode == LTS_MODE_SSPRK2 || (p->mode == LTS_MODE_LTS && reg->r.order == 2)))
+        return set_error(LTS_EINVAL, "the fused tile kernel runs LTS3 and SSPRK3 only");
     int bs = p->block_size ? p->block_size : 256;
     if (bs < 32 || bs > 256 || bs % 32) return set_error(LTS_EINVAL, "block_size must be 32..256, multiple of 32");
     int rc = check_device();
@@ -1103,13 +1241,11 @@ int lts_state_create(lts_mesh mesh, lts_regions reg, const double* h0, const dou
         return rc;
     }
     for (int par = 0; par < 2; ++par) {
-        const bool fused = p->kernel_path == 1;
-        if (p->mode == LTS_MODE_LTS3) {
-            if (fused) plan_lts3_fused(S.get(), par, S->plan[par]);
-            else plan_lts3(S.get(), par, S->plan[par]);
+        if (p->kernel_path == 1) {
+            if (p->mode == LTS_MODE_LTS) plan_lts3_fused(S.get(), par, S->plan[par]);
+            else plan_ssprk3_fused(S.get(), par, S->plan[par]);
         } else {
-            if (fused) plan_ssprk3_fused(S.get(), par, S->plan[par]);
-            else plan_ssprk3(S.get(), par, S->plan[par]);
+            make_plan(S.get(), par, S->plan[par]);
         }
     }
     if (p->no_l2_hints)

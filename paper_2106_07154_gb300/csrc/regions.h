@@ -20,6 +20,7 @@ struct HostMesh {
 
 struct RegionsHost {
     int M = 1, layers = 1;
+    int order = 3;                                 // 2 = LTS2, 3 = LTS3
     int ordering = 0;                              // 0 Hilbert inside a band, 1 mesh index order
     std::vector<int8_t> fine;                      // the fine-cell mask the labels came from
     std::vector<int8_t> cband, eband, vband;      // original order

@@ -23,8 +23,10 @@ LTS_ETIMEOUT = -5
 LTS_ENODEV = -6
 LTS_FP32 = 0
 LTS_FP64 = 1
+LTS_MODE_LTS = 0
 LTS_MODE_LTS3 = 0
 LTS_MODE_SSPRK3 = 1
+LTS_MODE_SSPRK2 = 2
 LTS_NKINDS = 4
 KIND_NAMES = ("vertex", "ring", "edge", "tile")
 PATH_THREE = 0
@@ -497,7 +499,7 @@ class Model:
                  interface_layers: int = 1, stream: int | None = None, pdl: bool = True,
                  kernel_path: int = 0, tile_cells: int = 0, l2_hints: bool = True,
                  coarse_schedule: int = 0, ordering: int = LTS_ORDER_HILBERT,
-                 autotune: int = 0, tune_ordering: bool = False):
+                 autotune: int = 0, tune_ordering: bool = False, order: int = 3):
         """autotune > 0: time that many coarse steps per candidate configuration
         (lts_autotune) and build the state with the fastest; the choice is in
         self.tuned."""
@@ -507,7 +509,7 @@ class Model:
         self.mesh_h = self.reg_h = self.state_h = None
         self.tuned = None
         self.mesh_h = lts_mesh_create(mesh)
-        self.reg_h = lts_regions_set(self.mesh_h, fine_mask, 3, M, interface_layers)
+        self.reg_h = lts_regions_set(self.mesh_h, fine_mask, order, M, interface_layers)
         if tile_cells:
             lts_regions_tiling(self.reg_h, tile_cells)
         if ordering != LTS_ORDER_HILBERT:

@@ -38,10 +38,12 @@ def test_errors_without_gpu_are_reported_not_raised():
     try:
         # bad arguments are rejected before any device work
         try:
-            lts.lts_regions_set(mh, np.zeros(mesh["nCells"], np.int8), 2, 2)
-            assert False, "order 2 should be rejected"
+            lts.lts_regions_set(mh, np.zeros(mesh["nCells"], np.int8), 4, 2)
+            assert False, "order 4 should be rejected"
         except lts.LtsError as e:
             assert e.code == lts.LTS_EINVAL and "order" in str(e)
+        r2 = lts.lts_regions_set(mh, np.zeros(mesh["nCells"], np.int8), 2, 2)   # LTS2
+        lts.lts_regions_destroy(r2)
         try:
             lts.lts_regions_set(mh, np.zeros(mesh["nCells"], np.int8), 3, 0)
             assert False, "M = 0 should be rejected"
