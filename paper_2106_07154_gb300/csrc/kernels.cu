@@ -50,6 +50,7 @@ struct DevArgs {
     int* flag;
     int l2;           // 0 no hint, 1 keep in L2 (evict_last), 2 stream (evict_first)
     int smem;         // dynamic shared memory of the launch (fused tiles)
+    int L;            // layers per element (multi-layer states; 1 otherwise)
     // segment-table launches (ensembles): segments in device memory
     const DevSeg<T>* gseg;
     int ngseg;
@@ -105,6 +106,25 @@ struct Ld {
     __device__ __forceinline__ V stat(const V* q) const { return ld_static(q, pol); }
     template <class V>
     __device__ __forceinline__ V operator()(const V* q) const { return ld_state(q, pol); }
+};
+
+// ------------------------------------------------------------------ layers
+// Element index -> array index of the state and the intermediates.  A
+// multi-layer state stores the layers of an element next to each other
+// ([element * L + layer]); its kernels run one thread per (element, layer)
+// with the layers fastest, so the threads of a warp share their table loads
+// (one broadcast transaction) and read the state contiguously.  Mesh tables
+// are indexed by the element alone.  The single-layer map is the identity.
+template <bool LAYERED>
+struct Lay;
+template <>
+struct Lay<false> {
+    __device__ __forceinline__ int operator()(int x) const { return x; }
+};
+template <>
+struct Lay<true> {
+    int L, l;
+    __device__ __forceinline__ long long operator()(long long x) const { return x * L + l; }
 };
 
 // ---------------------------------------------------------------- arithmetic
@@ -202,16 +222,16 @@ struct EpiOps {
 enum : int { EPI_NONE = 0, EPI_UPD = 1, EPI_ACC = 2 };
 
 // in_x = null: the caller already holds the input value (it sets xh).
-template <class T, bool COMP>
+template <class T, bool COMP, bool LY>
 __device__ __forceinline__ void epi_load(const Ld& ld, const DevSeg<T>& s, int mode, int i, const T* in_x,
-                                         EpiOps<T>& o) {
+                                         EpiOps<T>& o, const Lay<LY>& y) {
     if (mode == EPI_ACC) {
-        o.oh = s.flag ? T(0) : ld((const T*)s.p[0] + (i - s.base));
+        o.oh = s.flag ? T(0) : ld((const T*)s.p[0] + y(i - s.base));
     } else if (mode == EPI_UPD) {
-        o.oh = ld((const T*)s.p[0] + i);
-        o.ol = COMP ? ld((const T*)s.p[1] + i) : T(0);
-        if (in_x) o.xh = ld(in_x + i);
-        o.xl = COMP ? ld((const T*)s.p[2] + i) : T(0);
+        o.oh = ld((const T*)s.p[0] + y(i));
+        o.ol = COMP ? ld((const T*)s.p[1] + y(i)) : T(0);
+        if (in_x) o.xh = ld(in_x + y(i));
+        o.xl = COMP ? ld((const T*)s.p[2] + y(i)) : T(0);
     }
 }
 
@@ -219,8 +239,8 @@ __device__ __forceinline__ void epi_load(const Ld& ld, const DevSeg<T>& s, int m
 
 // q_v = (zeta_v + f_v) / h_v with zeta_v = sum t_{e,v} (d_e/A_v) u_e and
 // h_v = sum (A_{i,v}/A_v) h_i.
-template <class T>
-__device__ __forceinline__ void vertex_pv(const DevArgs<T>& a, int v) {
+template <class T, bool LY>
+__device__ __forceinline__ void vertex_pv(const DevArgs<T>& a, int v, const Lay<LY>& y) {
     const Tables<T>& t = a.t;
     const Ld ld(a.l2);
     const int e0 = ld.stat(t.ve0 + v), e1 = ld.stat(t.ve1 + v), e2 = ld.stat(t.ve2 + v);
@@ -229,9 +249,9 @@ __device__ __forceinline__ void vertex_pv(const DevArgs<T>& a, int v) {
     const T k0 = ld.stat(t.vk0 + v), k1 = ld.stat(t.vk1 + v), k2 = ld.stat(t.vk2 + v);
     const T f = ld.stat(t.f + v);
     griddep_wait();
-    T zeta = d0 * ld(a.in_u + e0) + d1 * ld(a.in_u + e1) + d2 * ld(a.in_u + e2);
-    T hv = k0 * ld(a.in_h + c0) + k1 * ld(a.in_h + c1) + k2 * ld(a.in_h + c2);
-    a.q[v] = (zeta + f) / hv;
+    T zeta = d0 * ld(a.in_u + y(e0)) + d1 * ld(a.in_u + y(e1)) + d2 * ld(a.in_u + y(e2));
+    T hv = k0 * ld(a.in_h + y(c0)) + k1 * ld(a.in_h + y(c1)) + k2 * ld(a.in_h + y(c2));
+    a.q[y(v)] = (zeta + f) / hv;
 }
 
 // --------------------------------------------------------------- kind 1: ring
@@ -254,8 +274,8 @@ __device__ __forceinline__ void vertex_pv(const DevArgs<T>& a, int v) {
 // state gathers of a thread are issued as two independent waves.
 constexpr int UNCOND = 6;
 
-template <class T, bool COMP, int MAXR>
-__device__ __forceinline__ T ring_pass(const DevArgs<T>& a, int c) {
+template <class T, bool COMP, int MAXR, bool LY>
+__device__ __forceinline__ T ring_pass(const DevArgs<T>& a, int c, const Lay<LY>& y) {
     const Tables<T>& t = a.t;
     const Ld ld(a.l2);
     const int N = t.nC;
@@ -274,7 +294,7 @@ __device__ __forceinline__ T ring_pass(const DevArgs<T>& a, int c) {
     }
     const T rA = ld.stat(t.rA + c);
     griddep_wait();
-    const T hc = ld(a.in_h + c);
+    const T hc = ld(a.in_h + y(c));
     T G[MAXR], qv[MAXR], R[MAXR];
     T Kc = T(0), s = T(0), comp = T(0);
 #pragma unroll
@@ -286,9 +306,9 @@ __device__ __forceinline__ T ring_pass(const DevArgs<T>& a, int c) {
             const T snl = j < UNCOND ? SNL0[j % UNCOND] : ld.stat(t.snl + j * N + c);
             const T Rj = j < UNCOND ? R0[j % UNCOND] : ld.stat(t.sR + j * N + c);
             const T sK = j < UNCOND ? SK0[j % UNCOND] : ld.stat(t.sK + j * N + c);
-            const T uj = ld(a.in_u + e);
-            const T hnb = ld(a.in_h + nb);
-            qv[j] = ld(a.q + v);
+            const T uj = ld(a.in_u + y(e));
+            const T hnb = ld(a.in_h + y(nb));
+            qv[j] = ld(a.q + y(v));
             const bool in = j < n;
             const T F = T(0.5) * (hc + hnb) * uj;
             const T g = in ? mul_rn(snl, F) : T(0);
@@ -340,21 +360,21 @@ __device__ __forceinline__ T ring_pass(const DevArgs<T>& a, int c) {
             const T w = P[p] - T(0.5);
             const T C = qt[p] * (w * (Atot - G[p]) + Pn * Asuf - (A1 - P[p] * G[p])) +
                         (w * (Btot - gq) + Pn * Bsuf - (B1 - P[p] * gq));
-            a.ring_c[p * N + c] = C;
+            a.ring_c[y(p * N + c)] = C;
             Asuf += G[p];
             Bsuf += gq;
         }
     }
-    a.ring_k[c] = Kc;
+    a.ring_k[y(c)] = Kc;
     return -(s + comp) * rA;
 }
 
 // --------------------------------------------------------------- kind 2: edge
 // U_e = -(1/d_e) [ (C_{c1,p1} - C_{c0,p0})/2 + g((h1 - h0) + (b1 - b0)) + K1 - K0 ]
 // (-n_{e,c0} = -1, -n_{e,c1} = +1 carry the signs of the two ring shares).
-template <class T, bool COMP>
+template <class T, bool COMP, bool LY>
 __device__ __forceinline__ T edge_tendency(const DevArgs<T>& a, int e, const DevSeg<T>& seg, int epi,
-                                           EpiOps<T>& eo) {
+                                           EpiOps<T>& eo, const Lay<LY>& y) {
     const Tables<T>& t = a.t;
     const Ld ld(a.l2);
     const int N = t.nC;
@@ -364,18 +384,18 @@ __device__ __forceinline__ T edge_tendency(const DevArgs<T>& a, int e, const Dev
     const T rdc = ld.stat(t.rdc + e);
     const T db = ld.stat(t.b + c1) - ld.stat(t.b + c0);
     griddep_wait();
-    epi_load<T, COMP>(ld, seg, epi, e, a.in_u, eo);
-    const T C0 = ld(a.ring_c + p0 * N + c0), C1 = ld(a.ring_c + p1 * N + c1);
+    epi_load<T, COMP, LY>(ld, seg, epi, e, a.in_u, eo, y);
+    const T C0 = ld(a.ring_c + y(p0 * N + c0)), C1 = ld(a.ring_c + y(p1 * N + c1));
     // h1 - h0 is exact for nearby thicknesses (Sterbenz); with COMP the
     // compensation words restore the digits the FP32 thickness dropped.
-    T dh = ld(a.in_h + c1) - ld(a.in_h + c0);
-    if (COMP) dh += ld(a.in_hl + c1) - ld(a.in_hl + c0);
-    const T grad = a.g * (dh + db) + (ld(a.ring_k + c1) - ld(a.ring_k + c0));
+    T dh = ld(a.in_h + y(c1)) - ld(a.in_h + y(c0));
+    if (COMP) dh += ld(a.in_hl + y(c1)) - ld(a.in_hl + y(c0));
+    const T grad = a.g * (dh + db) + (ld(a.ring_k + y(c1)) - ld(a.ring_k + y(c0)));
     return -rdc * (T(0.5) * (C1 - C0) + grad);
 }
 
-template <class T, bool COMP>
-__device__ __forceinline__ void pointwise(const DevSeg<T>& s, int i);
+template <class T, bool COMP, bool LY>
+__device__ __forceinline__ void pointwise(const DevSeg<T>& s, int i, const Lay<LY>& y);
 template <class T>
 __device__ __forceinline__ int find_seg(const DevArgs<T>& a, int blk);
 
@@ -579,13 +599,13 @@ __global__ void __launch_bounds__(256) kernel_tiles(const __grid_constant__ DevA
     const int i = s.begin + (blockIdx.x - s.block0) * blockDim.x + threadIdx.x;
     if (i >= s.end) return;
     griddep_wait();
-    pointwise<T, COMP>(s, i);
+    pointwise<T, COMP, false>(s, i, Lay<false>{});
 }
 
 // ------------------------------------------------------------ pointwise parts
 
-template <class T, bool COMP>
-__device__ __forceinline__ void pointwise(const DevSeg<T>& s, int i) {
+template <class T, bool COMP, bool LY>
+__device__ __forceinline__ void pointwise(const DevSeg<T>& s, int i, const Lay<LY>& y) {
     if (s.type == SEG_PRED) {
         const T* oh = (const T*)s.p[0];
         const T* ol = (const T*)s.p[1];
@@ -595,19 +615,19 @@ __device__ __forceinline__ void pointwise(const DevSeg<T>& s, int i) {
         const T* x2l = (const T*)s.p[5];
         T* outh = (T*)s.p[6];
         T* outl = (T*)s.p[7];
-        const int k = i - s.base, k2 = i - s.base2;
+        const auto ii = y(i), k = y(i - s.base), k2 = y(i - s.base2);
         T yh, yl;
-        predict<T, COMP>(oh[i], COMP ? ol[i] : T(0), x1h[k], COMP ? x1l[k] : T(0), x2h[k2],
+        predict<T, COMP>(oh[ii], COMP ? ol[ii] : T(0), x1h[k], COMP ? x1l[k] : T(0), x2h[k2],
                          COMP ? x2l[k2] : T(0), s.c[0], s.c[1], s.flag, yh, yl);
-        outh[i] = yh;
-        if (COMP) outl[i] = yl;
+        outh[ii] = yh;
+        if (COMP) outl[ii] = yl;
     } else if (s.type == SEG_COPY) {
         const T* sh = (const T*)s.p[0];
         const T* sl = (const T*)s.p[1];
         T* dh = (T*)s.p[2];
         T* dl = (T*)s.p[3];
-        dh[i - s.base] = sh[i - s.base2];
-        if (COMP) dl[i - s.base] = sl[i - s.base2];
+        dh[y(i - s.base)] = sh[y(i - s.base2)];
+        if (COMP) dl[y(i - s.base)] = sl[y(i - s.base2)];
     } else if (s.type == SEG_REPLAY) {
         // Step 5 as the replay of the interface stages (reading R5): three
         // stages for LTS3, two for LTS2 (flag 2: x_new = x2).
@@ -617,8 +637,8 @@ __device__ __forceinline__ void pointwise(const DevSeg<T>& s, int i) {
         const T* a2 = (const T*)s.p[3];
         T* outh = (T*)s.p[5];
         T* outl = (T*)s.p[6];
-        const int k = i - s.base;
-        const T xh = oh[i], xl = COMP ? ol[i] : T(0);
+        const auto ii = y(i), k = y(i - s.base);
+        const T xh = oh[ii], xl = COMP ? ol[ii] : T(0);
         T x1h, x1l, x2h, x2l, yh, yl;
         combine<T, COMP>(xh, xl, xh, xl, T(0), s.c[0], a1[k], x1h, x1l);
         combine<T, COMP>(xh, xl, x1h, x1l, s.c[3], s.c[1], a2[k], x2h, x2l);
@@ -629,27 +649,27 @@ __device__ __forceinline__ void pointwise(const DevSeg<T>& s, int i) {
             const T* a3 = (const T*)s.p[4];
             combine<T, COMP>(xh, xl, x2h, x2l, s.c[4], s.c[2], a3[k], yh, yl);
         }
-        outh[i] = yh;
-        if (COMP) outl[i] = yl;
+        outh[ii] = yh;
+        if (COMP) outl[ii] = yl;
     }
 }
 
 // Stage update (UPD) or correction accumulation (ACC) of a cell or edge
 // value from the operands epi_load fetched.
-template <class T, bool COMP, bool IS_CELL>
+template <class T, bool COMP, bool IS_CELL, bool LY>
 __device__ __forceinline__ void epilogue(const DevArgs<T>& a, const DevSeg<T>& s, int epi, int i, T R,
-                                         const EpiOps<T>& o) {
+                                         const EpiOps<T>& o, const Lay<LY>& y) {
     if (epi == EPI_ACC) {
         T* acc = (T*)s.p[0];
-        acc[i - s.base] = s.flag ? R : o.oh + R;
+        acc[y(i - s.base)] = s.flag ? R : o.oh + R;
         return;
     }
     T* outh = (T*)s.p[3];
     T* outl = (T*)s.p[4];
     T yh, yl;
     combine<T, COMP>(o.oh, o.ol, o.xh, o.xl, s.c[0], s.c[1], R, yh, yl);
-    outh[i] = yh;
-    if (COMP) outl[i] = yl;
+    outh[y(i)] = yh;
+    if (COMP) outl[y(i)] = yl;
     const bool ok = IS_CELL ? finite_pos(yh) : finite_val(yh);
     if (!ok) atomicOr(a.flag, IS_CELL ? 1 : 2);
 }
@@ -669,40 +689,52 @@ __device__ __forceinline__ bool is_ring(int type) {
 }
 
 // The work of (virtual) block `vblk` of segment s.
-template <class T, bool COMP, int MAXR, int KIND>
+template <class T, bool COMP, int MAXR, int KIND, bool LY>
 __device__ __forceinline__ void phase_block(const DevArgs<T>& a, const DevSeg<T>& s, int vblk) {
     const int type = s.type;
     const int local = (vblk - s.block0) * blockDim.x + threadIdx.x;
-    const int i = s.begin + local;
+    int i, l = 0;
+    if (LY) {   // (element, layer), layers fastest
+        const int q = local / a.L;
+        i = s.begin + q;
+        l = local - q * a.L;
+    } else {
+        i = s.begin + local;
+    }
     if (i >= s.end) return;
+    Lay<LY> y;
+    if constexpr (LY) {
+        y.L = a.L;
+        y.l = l;
+    }
     if (KIND == 0 && type == SEG_VERT) {
-        vertex_pv(a, i);
+        vertex_pv<T, LY>(a, i, y);
     } else if (KIND == 1 && is_ring(type)) {
         // the cell update's operands are loaded after the ring (the ring pass
         // holds ~40 registers; loading them earlier costs a resident block)
         const int epi = type == SEG_RING ? EPI_NONE : type == SEG_RING_ACC ? EPI_ACC : EPI_UPD;
-        const T H = ring_pass<T, COMP, MAXR>(a, i);
+        const T H = ring_pass<T, COMP, MAXR, LY>(a, i, y);
         if (epi != EPI_NONE) {
             EpiOps<T> o;
-            epi_load<T, COMP>(Ld(a.l2), s, epi, i, a.in_h, o);
-            epilogue<T, COMP, true>(a, s, epi, i, H, o);
+            epi_load<T, COMP, LY>(Ld(a.l2), s, epi, i, a.in_h, o, y);
+            epilogue<T, COMP, true, LY>(a, s, epi, i, H, o, y);
         }
     } else if (KIND == 2 && (type == SEG_EDGE_UPD || type == SEG_EDGE_ACC)) {
         const int epi = type == SEG_EDGE_ACC ? EPI_ACC : EPI_UPD;
         EpiOps<T> o;
-        const T U = edge_tendency<T, COMP>(a, i, s, epi, o);
-        epilogue<T, COMP, false>(a, s, epi, i, U, o);
+        const T U = edge_tendency<T, COMP, LY>(a, i, s, epi, o, y);
+        epilogue<T, COMP, false, LY>(a, s, epi, i, U, o, y);
     } else {
         griddep_wait();
-        pointwise<T, COMP>(s, i);
+        pointwise<T, COMP, LY>(s, i, y);
     }
 }
 
-template <class T, bool COMP, int MAXR, int KIND>
+template <class T, bool COMP, int MAXR, int KIND, bool LY = false>
 __global__ void __launch_bounds__(256) kernel_phase(const __grid_constant__ DevArgs<T> a) {
     griddep_launch_dependents();
     const int sidx = find_seg(a, blockIdx.x);
-    phase_block<T, COMP, MAXR, KIND>(a, a.seg[sidx], blockIdx.x);
+    phase_block<T, COMP, MAXR, KIND, LY>(a, a.seg[sidx], blockIdx.x);
 }
 
 // Segment-table variant (ensembles of meshes: one launch carries the
@@ -724,7 +756,7 @@ template <class T, bool COMP, int MAXR, int KIND>
 __global__ void __launch_bounds__(256) kernel_phase_table(const __grid_constant__ DevArgs<T> a) {
     griddep_launch_dependents();
     for (int vb = blockIdx.x; vb < a.vblocks; vb += gridDim.x)
-        phase_block<T, COMP, MAXR, KIND>(a, a.gseg[find_gseg(a, vb)], vb);
+        phase_block<T, COMP, MAXR, KIND, false>(a, a.gseg[find_gseg(a, vb)], vb);
 }
 
 template <class K, class A>
@@ -763,9 +795,9 @@ DevSeg<T> to_dev(const SegDesc& s, int block0) {
     return o;
 }
 
-inline int seg_blocks(const SegDesc& s, int block) {
+inline int seg_blocks(const SegDesc& s, int block, int layers = 1) {
     return s.type == SEG_TILE ? s.end - s.begin              // one block per tile
-                              : (s.end - s.begin + block - 1) / block;
+                              : static_cast<int>((static_cast<long long>(s.end - s.begin) * layers + block - 1) / block);
 }
 
 template <class T>
@@ -785,19 +817,21 @@ void fill_args(DevArgs<T>& a, const LaunchDesc& d, const void* tables, int smem,
     a.gseg = nullptr;
     a.ngseg = 0;
     a.vblocks = 0;
+    a.L = 1;
 }
 
 template <class T, bool COMP, int MAXR>
 cudaError_t launch_t(const LaunchDesc& d, const void* tables, int block, bool pdl, int smem, int* flag,
-                     cudaStream_t st) {
+                     cudaStream_t st, int layers) {
     DevArgs<T> a;
     fill_args(a, d, tables, smem, flag);
+    a.L = layers;
     int blocks = 0, ns = 0;
     for (int k = 0; k < d.nseg; ++k) {
         const SegDesc& s = d.seg[k];
         if (s.end <= s.begin) continue;
         a.seg[ns++] = to_dev<T>(s, blocks);
-        blocks += seg_blocks(s, block);
+        blocks += seg_blocks(s, block, layers);
     }
     a.nseg = ns;
     for (int k = ns; k < MAXSEG; ++k) {
@@ -812,6 +846,13 @@ cudaError_t launch_t(const LaunchDesc& d, const void* tables, int block, bool pd
             if (e != cudaSuccess) return e;
         }
         return launch_kernel(kernel_tiles<T, COMP, MAXR>, blocks, block, pdl, st, a, smem);
+    }
+    if (layers > 1) {
+        switch (d.kind) {
+            case 0: return launch_kernel(kernel_phase<T, COMP, MAXR, 0, true>, blocks, block, pdl, st, a);
+            case 1: return launch_kernel(kernel_phase<T, COMP, MAXR, 1, true>, blocks, block, pdl, st, a);
+            default: return launch_kernel(kernel_phase<T, COMP, MAXR, 2, true>, blocks, block, pdl, st, a);
+        }
     }
     switch (d.kind) {
         case 0: return launch_kernel(kernel_phase<T, COMP, MAXR, 0>, blocks, block, pdl, st, a);
@@ -842,23 +883,27 @@ cudaError_t launch_table_t(const LaunchDesc& d, const void* dsegs, int nseg, int
 
 // ------------------------------------------------------------ state I/O
 
+// State I/O: host arrays are [layer][element] in the caller's order, device
+// arrays [element * L + layer] in band order (L = 1: a plain permutation).
 template <class T, bool COMP>
-__global__ void scatter_kernel(int n, const int* perm, const double* src, T* hi, T* lo) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double x = src[perm[i]];
+__global__ void scatter_kernel(int n, int L, const int* perm, const double* src, T* hi, T* lo) {
+    const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= static_cast<long long>(n) * L) return;
+    const int e = static_cast<int>(i / L), l = static_cast<int>(i - static_cast<long long>(e) * L);
+    double x = src[static_cast<long long>(l) * n + perm[e]];
     T h = static_cast<T>(x);
     hi[i] = h;
     if (COMP) lo[i] = static_cast<T>(x - static_cast<double>(h));
 }
 
 template <class T, bool COMP>
-__global__ void gather_kernel(int n, const int* perm, const T* hi, const T* lo, double* dst) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+__global__ void gather_kernel(int n, int L, const int* perm, const T* hi, const T* lo, double* dst) {
+    const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= static_cast<long long>(n) * L) return;
+    const int e = static_cast<int>(i / L), l = static_cast<int>(i - static_cast<long long>(e) * L);
     double x = static_cast<double>(hi[i]);
     if (COMP) x += static_cast<double>(lo[i]);
-    dst[perm[i]] = x;
+    dst[static_cast<long long>(l) * n + perm[e]] = x;
 }
 
 // ------------------------------------------------------------ FP64 diagnostics
@@ -866,18 +911,23 @@ __global__ void gather_kernel(int n, const int* perm, const T* hi, const T* lo, 
 // fixed blocking and a fixed-order tree, so the result is deterministic.
 constexpr int DIAG_THREADS = 256;
 
+// (summed over the layers of a multi-layer state: element-major, layers
+// innermost)
 template <class T, bool COMP>
 __global__ void __launch_bounds__(DIAG_THREADS) diag_kernel(const Tables<T> t, const T* hh, const T* hl,
                                                            const T* uh, const T* ul, double g,
-                                                           double* partial) {
+                                                           double* partial, int L) {
     __shared__ double sm[2][DIAG_THREADS];
     const int N = t.nC;
+    const long long NL = static_cast<long long>(N) * L;
     double m = 0.0, en = 0.0;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
-        double h = static_cast<double>(hh[c]) + (COMP ? static_cast<double>(hl[c]) : 0.0);
+    for (long long x = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; x < NL;
+         x += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int c = static_cast<int>(x / L), l = static_cast<int>(x - static_cast<long long>(c) * L);
+        double h = static_cast<double>(hh[x]) + (COMP ? static_cast<double>(hl[x]) : 0.0);
         double K = 0.0;
         for (int j = 0; j < t.cn[c]; ++j) {
-            int e = t.se[j * N + c];
+            const long long e = static_cast<long long>(t.se[j * N + c]) * L + l;
             double u = static_cast<double>(uh[e]) + (COMP ? static_cast<double>(ul[e]) : 0.0);
             K += t.sK64[j * N + c] * u * u;
         }
@@ -928,8 +978,9 @@ __global__ void __launch_bounds__(DIAG_THREADS) diag_final(const double* partial
 template <class T, bool COMP>
 cudaError_t launch_any(const LaunchDesc& d, const void* tables, const KernelConfig& kc, int* flag,
                        cudaStream_t s) {
-    if (kc.maxdeg <= 8) return launch_t<T, COMP, 8>(d, tables, kc.block, kc.pdl, kc.tile_smem, flag, s);
-    return launch_t<T, COMP, MAX_DEGREE>(d, tables, kc.block, kc.pdl, kc.tile_smem, flag, s);
+    const int L = kc.layers > 1 ? kc.layers : 1;
+    if (kc.maxdeg <= 8) return launch_t<T, COMP, 8>(d, tables, kc.block, kc.pdl, kc.tile_smem, flag, s, L);
+    return launch_t<T, COMP, MAX_DEGREE>(d, tables, kc.block, kc.pdl, kc.tile_smem, flag, s, L);
 }
 
 }  // namespace
@@ -1003,45 +1054,50 @@ int table_blocks_per_sm(const KernelConfig& kc, int kind) {
 cudaError_t launch_scatter_state(const KernelConfig& kc, int n, const int* perm, const double* src,
                                  void* hi, void* lo, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    int b = 256, g = (n + b - 1) / b;
+    const int L = kc.layers > 1 ? kc.layers : 1;
+    const int b = 256;
+    const long long g = (static_cast<long long>(n) * L + b - 1) / b;
     if (kc.precision == 1)
-        scatter_kernel<double, false><<<g, b, 0, s>>>(n, perm, src, (double*)hi, nullptr);
+        scatter_kernel<double, false><<<g, b, 0, s>>>(n, L, perm, src, (double*)hi, nullptr);
     else if (kc.comp)
-        scatter_kernel<float, true><<<g, b, 0, s>>>(n, perm, src, (float*)hi, (float*)lo);
+        scatter_kernel<float, true><<<g, b, 0, s>>>(n, L, perm, src, (float*)hi, (float*)lo);
     else
-        scatter_kernel<float, false><<<g, b, 0, s>>>(n, perm, src, (float*)hi, nullptr);
+        scatter_kernel<float, false><<<g, b, 0, s>>>(n, L, perm, src, (float*)hi, nullptr);
     return cudaGetLastError();
 }
 
 cudaError_t launch_gather_state(const KernelConfig& kc, int n, const int* perm, const void* hi,
                                 const void* lo, double* dst, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    int b = 256, g = (n + b - 1) / b;
+    const int L = kc.layers > 1 ? kc.layers : 1;
+    const int b = 256;
+    const long long g = (static_cast<long long>(n) * L + b - 1) / b;
     if (kc.precision == 1)
-        gather_kernel<double, false><<<g, b, 0, s>>>(n, perm, (const double*)hi, nullptr, dst);
+        gather_kernel<double, false><<<g, b, 0, s>>>(n, L, perm, (const double*)hi, nullptr, dst);
     else if (kc.comp)
-        gather_kernel<float, true><<<g, b, 0, s>>>(n, perm, (const float*)hi, (const float*)lo, dst);
+        gather_kernel<float, true><<<g, b, 0, s>>>(n, L, perm, (const float*)hi, (const float*)lo, dst);
     else
-        gather_kernel<float, false><<<g, b, 0, s>>>(n, perm, (const float*)hi, nullptr, dst);
+        gather_kernel<float, false><<<g, b, 0, s>>>(n, L, perm, (const float*)hi, nullptr, dst);
     return cudaGetLastError();
 }
 
 cudaError_t launch_diagnostics(const KernelConfig& kc, const void* tables, const void* h_hi,
                                const void* h_lo, const void* u_hi, const void* u_lo, double g,
                                double* partial, int nblocks, double* out2, cudaStream_t s) {
+    const int L = kc.layers > 1 ? kc.layers : 1;
     if (kc.precision == 1) {
         const Tables<double>& t = *static_cast<const Tables<double>*>(tables);
         diag_kernel<double, false><<<nblocks, DIAG_THREADS, 0, s>>>(
-            t, (const double*)h_hi, nullptr, (const double*)u_hi, nullptr, g, partial);
+            t, (const double*)h_hi, nullptr, (const double*)u_hi, nullptr, g, partial, L);
     } else {
         const Tables<float>& t = *static_cast<const Tables<float>*>(tables);
         if (kc.comp)
             diag_kernel<float, true><<<nblocks, DIAG_THREADS, 0, s>>>(
                 t, (const float*)h_hi, (const float*)h_lo, (const float*)u_hi, (const float*)u_lo, g,
-                partial);
+                partial, L);
         else
             diag_kernel<float, false><<<nblocks, DIAG_THREADS, 0, s>>>(
-                t, (const float*)h_hi, nullptr, (const float*)u_hi, nullptr, g, partial);
+                t, (const float*)h_hi, nullptr, (const float*)u_hi, nullptr, g, partial, L);
     }
     diag_final<<<1, DIAG_THREADS, 0, s>>>(partial, nblocks, out2);
     return cudaGetLastError();

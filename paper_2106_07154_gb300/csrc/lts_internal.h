@@ -141,6 +141,7 @@ struct KernelConfig {
     int tile_smem;   // dynamic shared memory of the fused kernel (bytes)
     int mindeg;      // smallest cell degree of the mesh (slots loaded unconditionally)
     bool pdl;        // programmatic dependent launch
+    int layers = 1;  // layers per element (multi-layer states)
 };
 
 // kernels.cu
