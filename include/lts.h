@@ -217,6 +217,14 @@ typedef struct lts_params {
     void* stream;           /* cudaStream_t to enqueue on; NULL = a library stream     */
     int32_t no_l2_hints;    /* 1: table loads without L2 eviction priorities (default:
                                keep the fine region, stream the coarse one)            */
+    int32_t layers;         /* independent shallow-water layers advanced on the same
+                               mesh (0 or 1 = one).  The paper's speed-up runs repeat
+                               every computation for 100 layers to model an ocean
+                               workload; here the layers share every mesh-table load.
+                               h0/u0, lts_read and lts_write then take [layers][nCells]
+                               and [layers][nEdges] (layer-major, original order inside
+                               a layer); diagnostics sum over the layers.  Three-launch
+                               path only, no ensembles.                                */
     int32_t coarse_schedule;/* order of the coarse phases (results are identical):
                                LTS_COARSE_STEP4 (default): Step 4 on the coarse bands
                                C3 and beyond runs as a concurrent graph branch beside

@@ -465,6 +465,7 @@ int lts_ensemble_create(const lts_state* members, int32_t n, const lts_ensemble_
         if (S->p.mode != s0->p.mode || S->reg->r.order != s0->reg->r.order)
             return set_error(LTS_EINVAL, "member %d: mode or order differs from member 0", m);
         if (S->p.kernel_path != 0) return set_error(LTS_EINVAL, "member %d: ensembles need kernel_path 0", m);
+        if (S->kc.layers != 1) return set_error(LTS_EINVAL, "member %d: ensembles take single-layer states", m);
         if (S->p.g != s0->p.g) return set_error(LTS_EINVAL, "member %d: g differs from member 0", m);
         if (S->kc.block != s0->kc.block) return set_error(LTS_EINVAL, "member %d: block size differs", m);
         E->members.push_back(S);

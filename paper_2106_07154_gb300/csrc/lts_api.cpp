@@ -108,19 +108,21 @@ int build_tables(lts_regions_s* R, int which, Tables<T>& t) {
 
 // ------------------------------------------------------- algorithmic bytes
 // Bytes of every array element a launch touches, each counted once (a
-// perfect cache): the compulsory traffic of the launch.
+// perfect cache): the compulsory traffic of the launch.  Mesh tables are
+// read once per element; state and intermediates once per layer.
 double launch_bytes(const LaunchDesc& d, const RegionsHost& r, int nC, int nE, int nV, size_t T,
-                    bool comp) {
+                    bool comp, int layers) {
     std::vector<char> mh(nC, 0), mhl(nC, 0), mu(nE, 0), mq(nV, 0), mk(nC, 0), mb(nC, 0);
     std::vector<char> mrow(nC, 0), mvert(nV, 0);   // fused tiles: ring rows and vertices read
-    double bytes = 0.0;
+    double tab = 0.0, st = 0.0;   // table bytes, state bytes per layer
     const double c = comp ? 1.0 : 0.0;
     for (int s = 0; s < d.nseg; ++s) {
         const SegDesc& g = d.seg[s];
         const double n = std::max(0, g.end - g.begin);
         switch (g.type) {
             case SEG_VERT:
-                bytes += n * (24.0 + 7.0 * T + T);   // vc, ve, vk, vd, f; q write
+                tab += n * (24.0 + 7.0 * T);   // vc, ve, vk, vd, f
+                st += n * T;                   // q write
                 for (int v = g.begin; v < g.end; ++v)
                     for (int q = 0; q < 3; ++q) {
                         mh[r.vc[static_cast<size_t>(q) * nV + v]] = 1;
@@ -131,8 +133,9 @@ double launch_bytes(const LaunchDesc& d, const RegionsHost& r, int nC, int nE, i
             case SEG_RING_UPD:
             case SEG_RING_ACC:
                 for (int k = g.begin; k < g.end; ++k) {
-                    // cn, rA; per slot se, sn, sv, snl, sR, sK and the C write; K write
-                    bytes += 1.0 + T + r.cn[k] * (12.0 + 4.0 * T) + T;
+                    // cn, rA; per slot se, sn, sv, snl, sR, sK; the C and K writes
+                    tab += 1.0 + T + r.cn[k] * (12.0 + 3.0 * T);
+                    st += r.cn[k] * T + T;
                     mh[k] = 1;
                     for (int j = 0; j < r.cn[k]; ++j) {
                         mu[r.se[static_cast<size_t>(j) * nC + k]] = 1;
@@ -140,12 +143,12 @@ double launch_bytes(const LaunchDesc& d, const RegionsHost& r, int nC, int nE, i
                         mq[r.sv[static_cast<size_t>(j) * nC + k]] = 1;
                     }
                 }
-                if (g.type == SEG_RING_UPD) bytes += n * T * (2.0 + 3.0 * c);
-                if (g.type == SEG_RING_ACC) bytes += n * T * (g.flag ? 1 : 2);
+                if (g.type == SEG_RING_UPD) st += n * T * (2.0 + 3.0 * c);
+                if (g.type == SEG_RING_ACC) st += n * T * (g.flag ? 1 : 2);
                 break;
             case SEG_EDGE_UPD:
             case SEG_EDGE_ACC:
-                bytes += n * (12.0 + T);                     // ec0, ec1, ep, rdc
+                tab += n * (12.0 + T);                       // ec0, ec1, ep, rdc
                 for (int e = g.begin; e < g.end; ++e) {
                     mu[e] = 1;
                     for (int cc : {r.ec0[e], r.ec1[e]}) {
@@ -153,18 +156,19 @@ double launch_bytes(const LaunchDesc& d, const RegionsHost& r, int nC, int nE, i
                         if (comp) mhl[cc] = 1;
                     }
                 }
-                bytes += n * 2.0 * T;                        // the two ring shares C (one per edge end)
-                bytes += g.type == SEG_EDGE_UPD ? n * T * (2.0 + 3.0 * c) : n * T * (g.flag ? 1 : 2);
+                st += n * 2.0 * T;                           // the two ring shares C (one per edge end)
+                st += g.type == SEG_EDGE_UPD ? n * T * (2.0 + 3.0 * c) : n * T * (g.flag ? 1 : 2);
                 break;
             case SEG_TILE:
                 for (int tl = g.begin; tl < g.end; ++tl) {
                     const int4 ta = r.tile_a[tl], tb = r.tile_b[tl];
                     const bool acc = tl >= g.flag2;
                     // own cells: epilogue; all local cells: ring tables; vertices; edges
-                    bytes += ta.y * T * (acc ? (g.flag ? 1.0 : 2.0) : (2.0 + 3.0 * c));
-                    bytes += static_cast<double>(tb.y - tb.x) *
-                             (12.0 + T + 4.0 + (acc ? T * (g.flag ? 1.0 : 2.0) : T * (2.0 + 3.0 * c)));
-                    bytes += 8.0 * 4 + 8.0 * 4;   // tile descriptors
+                    st += ta.y * T * (acc ? (g.flag ? 1.0 : 2.0) : (2.0 + 3.0 * c));
+                    tab += static_cast<double>(tb.y - tb.x) * (12.0 + T + 4.0);
+                    st += static_cast<double>(tb.y - tb.x) *
+                          (acc ? T * (g.flag ? 1.0 : 2.0) : T * (2.0 + 3.0 * c));
+                    tab += 8.0 * 4 + 8.0 * 4;   // tile descriptors
                     for (int k = 0; k < ta.w; ++k) {
                         const int cc = k < ta.y ? ta.x + k : r.halo[ta.z + (k - ta.y)];
                         mrow[cc] = 1;
@@ -180,13 +184,13 @@ double launch_bytes(const LaunchDesc& d, const RegionsHost& r, int nC, int nE, i
                 }
                 break;
             case SEG_PRED:
-                bytes += n * T * (g.flag ? 2.0 * (1 + c) : 4.0 * (1 + c));
+                st += n * T * (g.flag ? 2.0 * (1 + c) : 4.0 * (1 + c));
                 break;
             case SEG_COPY:
-                bytes += n * T * 2.0 * (1 + c);
+                st += n * T * 2.0 * (1 + c);
                 break;
             case SEG_REPLAY:
-                bytes += n * T * ((g.flag == 2 ? 4.0 : 5.0) + 2.0 * c);
+                st += n * T * ((g.flag == 2 ? 4.0 : 5.0) + 2.0 * c);
                 break;
         }
     }
@@ -194,7 +198,7 @@ double launch_bytes(const LaunchDesc& d, const RegionsHost& r, int nC, int nE, i
     // local cell, and the state the rings gather; vertex tables and their gathers
     for (int k = 0; k < nC; ++k) {
         if (!mrow[k]) continue;
-        bytes += 1.0 + T + r.cn[k] * (10.0 + 3.0 * T);
+        tab += 1.0 + T + r.cn[k] * (10.0 + 3.0 * T);
         mh[k] = 1;
         for (int j = 0; j < r.cn[k]; ++j) {
             mu[r.se[static_cast<size_t>(j) * nC + k]] = 1;
@@ -203,17 +207,20 @@ double launch_bytes(const LaunchDesc& d, const RegionsHost& r, int nC, int nE, i
     }
     for (int v = 0; v < nV; ++v) {
         if (!mvert[v]) continue;
-        bytes += 24.0 + 7.0 * T;
+        tab += 24.0 + 7.0 * T;
         for (int q = 0; q < 3; ++q) {
             mh[r.vc[static_cast<size_t>(q) * nV + v]] = 1;
             mu[r.ve[static_cast<size_t>(q) * nV + v]] = 1;
         }
     }
-    double cnt = 0.0;
-    for (int k = 0; k < nC; ++k) cnt += mh[k] + mhl[k] + mk[k] + mb[k];
+    double cnt = 0.0, cntb = 0.0;
+    for (int k = 0; k < nC; ++k) {
+        cnt += mh[k] + mhl[k] + mk[k];
+        cntb += mb[k];
+    }
     for (char x : mu) cnt += x;
     for (char x : mq) cnt += x;
-    return bytes + cnt * T;
+    return tab + cntb * T + layers * (st + cnt * T);
 }
 
 // ------------------------------------------------------------ phase plans
@@ -862,7 +869,9 @@ int state_alloc(lts_state_s* S) {
     const size_t T = S->tsz;
     const bool comp = S->kc.comp;
     cudaError_t err = cudaSuccess;
-    auto A = [&](size_t n) { return S->arena.alloc(n * T, err); };
+    // state-sized arrays hold every layer ([element * L + layer])
+    const size_t Ly = static_cast<size_t>(S->kc.layers);
+    auto A = [&](size_t n) { return S->arena.alloc(n * Ly * T, err); };
     for (int k = 0; k < 4; ++k) {
         S->buf[k].hh = A(m.nC);
         S->buf[k].uh = A(m.nE);
@@ -894,8 +903,8 @@ int state_alloc(lts_state_s* S) {
         S->ring_k_side = A(m.nC);
     }
     S->flag = static_cast<int*>(S->arena.alloc(sizeof(int), err));
-    S->stage_c = static_cast<double*>(S->arena.alloc(sizeof(double) * m.nC, err));
-    S->stage_e = static_cast<double*>(S->arena.alloc(sizeof(double) * m.nE, err));
+    S->stage_c = static_cast<double*>(S->arena.alloc(sizeof(double) * m.nC * Ly, err));
+    S->stage_e = static_cast<double*>(S->arena.alloc(sizeof(double) * m.nE * Ly, err));
     S->diag_blocks = std::max(1, std::min(1024, (m.nC + 255) / 256));
     S->diag_partial = static_cast<double*>(S->arena.alloc(sizeof(double) * 2 * S->diag_blocks, err));
     S->diag_out = static_cast<double*>(S->arena.alloc(sizeof(double) * 2, err));
@@ -910,8 +919,9 @@ int state_alloc(lts_state_s* S) {
 int write_state(lts_state_s* S, const double* h, const double* u) {
     const HostMesh& m = S->reg->mesh->m;
     const SV& X = S->buf[S->parity];
-    CUDA_TRY(cudaMemcpyAsync(S->stage_c, h, sizeof(double) * m.nC, cudaMemcpyHostToDevice, S->stream));
-    CUDA_TRY(cudaMemcpyAsync(S->stage_e, u, sizeof(double) * m.nE, cudaMemcpyHostToDevice, S->stream));
+    const size_t Ly = static_cast<size_t>(S->kc.layers);
+    CUDA_TRY(cudaMemcpyAsync(S->stage_c, h, sizeof(double) * m.nC * Ly, cudaMemcpyHostToDevice, S->stream));
+    CUDA_TRY(cudaMemcpyAsync(S->stage_e, u, sizeof(double) * m.nE * Ly, cudaMemcpyHostToDevice, S->stream));
     CUDA_TRY(launch_scatter_state(S->kc, m.nC, S->reg->d_perm_c, S->stage_c, X.hh, X.hl, S->stream));
     CUDA_TRY(launch_scatter_state(S->kc, m.nE, S->reg->d_perm_e, S->stage_e, X.uh, X.ul, S->stream));
     return LTS_OK;
@@ -933,7 +943,7 @@ void make_plan(lts_state_s* S, int parity, std::vector<LaunchDesc>& out) {
 }
 double plan_launch_bytes(const LaunchDesc& d, const RegionsHost& r, int nC, int nE, int nV, size_t T,
                          bool comp) {
-    return launch_bytes(d, r, nC, nE, nV, T, comp);
+    return launch_bytes(d, r, nC, nE, nV, T, comp, 1);
 }
 }  // namespace lts
 
@@ -1209,6 +1219,13 @@ int lts_state_create(lts_mesh mesh, lts_regions reg, const double* h0, const dou
     S->kc.block = bs;
     S->tsz = which ? 8 : 4;
     S->kc.maxdeg = mesh->m.maxE <= 8 ? 8 : MAX_DEGREE;
+    const int layers = p->layers > 0 ? p->layers : 1;
+    if (layers > 65536) return set_error(LTS_EINVAL, "layers must be in [1, 65536]");
+    if (layers > 1 && p->kernel_path != 0)
+        return set_error(LTS_EINVAL, "multi-layer states run the three-launch path only (kernel_path 0)");
+    if (static_cast<long long>(mesh->m.maxE) * mesh->m.nC * layers > 0x7fffffffLL * 8LL ||
+        static_cast<long long>(mesh->m.nE) * layers > 0x7fffffffLL)
+        return set_error(LTS_EINVAL, "mesh x layers too large");
     if (p->coarse_schedule < LTS_COARSE_STEP4 || p->coarse_schedule > LTS_COARSE_SERIAL)
         return set_error(LTS_EINVAL, "coarse_schedule must be LTS_COARSE_STEP4, _FAR or _SERIAL");
     if (p->kernel_path != 0 && p->kernel_path != 1)
@@ -1220,6 +1237,7 @@ int lts_state_create(lts_mesh mesh, lts_regions reg, const double* h0, const dou
     }
     S->kc.mindeg = *std::min_element(mesh->m.nEoC.begin(), mesh->m.nEoC.end());
     S->kc.pdl = p->pdl != 0 && p->profile == 0;
+    S->kc.layers = layers;
     S->tables = which ? static_cast<const void*>(&reg->t64) : static_cast<const void*>(&reg->t32);
     if (p->stream) {
         S->stream = static_cast<cudaStream_t>(p->stream);
@@ -1255,7 +1273,7 @@ int lts_state_create(lts_mesh mesh, lts_regions reg, const double* h0, const dou
     const HostMesh& m = mesh->m;
     for (LaunchDesc& d : S->plan[0]) {
         if (d.nseg == 0) continue;
-        d.bytes = launch_bytes(d, reg->r, m.nC, m.nE, m.nV, S->tsz, S->kc.comp);
+        d.bytes = launch_bytes(d, reg->r, m.nC, m.nE, m.nV, S->tsz, S->kc.comp, S->kc.layers);
         S->bytes[d.kind] += d.bytes;
         S->launches[d.kind] += 1;
     }
@@ -1355,11 +1373,13 @@ int lts_read(lts_state s, double* h, double* u, lts_diag* d) {
     const SV& X = s->buf[s->parity];
     if (h) {
         CUDA_TRY(launch_gather_state(s->kc, m.nC, s->reg->d_perm_c, X.hh, X.hl, s->stage_c, s->stream));
-        CUDA_TRY(cudaMemcpyAsync(h, s->stage_c, sizeof(double) * m.nC, cudaMemcpyDeviceToHost, s->stream));
+        CUDA_TRY(cudaMemcpyAsync(h, s->stage_c, sizeof(double) * m.nC * s->kc.layers, cudaMemcpyDeviceToHost,
+                                 s->stream));
     }
     if (u) {
         CUDA_TRY(launch_gather_state(s->kc, m.nE, s->reg->d_perm_e, X.uh, X.ul, s->stage_e, s->stream));
-        CUDA_TRY(cudaMemcpyAsync(u, s->stage_e, sizeof(double) * m.nE, cudaMemcpyDeviceToHost, s->stream));
+        CUDA_TRY(cudaMemcpyAsync(u, s->stage_e, sizeof(double) * m.nE * s->kc.layers, cudaMemcpyDeviceToHost,
+                                 s->stream));
     }
     double diag[2] = {0, 0};
     if (d) {

@@ -82,7 +82,7 @@ class lts_params(C.Structure):
                 ("mode", C.c_int32), ("compensated", C.c_int32), ("use_graph", C.c_int32),
                 ("block_size", C.c_int32), ("profile", C.c_int32), ("pdl", C.c_int32),
                 ("kernel_path", C.c_int32), ("stream", C.c_void_p), ("no_l2_hints", C.c_int32),
-                ("coarse_schedule", C.c_int32)]
+                ("layers", C.c_int32), ("coarse_schedule", C.c_int32)]
 
 
 class lts_tune_entry(C.Structure):
@@ -322,15 +322,17 @@ def lts_regions_permutation(reg_h, nCells: int, nEdges: int, nVertices: int):
 def make_params(g: float, dt: float, precision: int = LTS_FP32, mode: int = LTS_MODE_LTS3,
                 compensated: bool = True, use_graph: bool = True, block_size: int = 0,
                 profile: int = 0, stream: int | None = None, pdl: bool = True,
-                kernel_path: int = 0, l2_hints: bool = True, coarse_schedule: int = 0):
+                kernel_path: int = 0, l2_hints: bool = True, coarse_schedule: int = 0,
+                layers: int = 1):
     return lts_params(g, dt, precision, mode, int(compensated), int(use_graph), block_size,
                       int(profile), int(pdl), int(kernel_path), stream, int(not l2_hints),
-                      int(coarse_schedule))
+                      int(layers), int(coarse_schedule))
 
 
 def params_dict(p: lts_params) -> dict:
     return {"block_size": p.block_size, "kernel_path": p.kernel_path, "pdl": bool(p.pdl),
             "l2_hints": not p.no_l2_hints, "coarse_schedule": int(p.coarse_schedule),
+            "layers": int(p.layers),
             "use_graph": bool(p.use_graph)}
 
 
@@ -499,10 +501,12 @@ class Model:
                  interface_layers: int = 1, stream: int | None = None, pdl: bool = True,
                  kernel_path: int = 0, tile_cells: int = 0, l2_hints: bool = True,
                  coarse_schedule: int = 0, ordering: int = LTS_ORDER_HILBERT,
-                 autotune: int = 0, tune_ordering: bool = False, order: int = 3):
+                 autotune: int = 0, tune_ordering: bool = False, order: int = 3, layers: int = 1):
         """autotune > 0: time that many coarse steps per candidate configuration
         (lts_autotune) and build the state with the fastest; the choice is in
-        self.tuned."""
+        self.tuned.  layers > 1: h0, u0 (and read/write) are [layers][nCells],
+        [layers][nEdges] arrays."""
+        self.layers = max(1, int(layers))
         self.nC = int(mesh["nCells"])
         self.nE = int(mesh["nEdges"])
         self.nV = int(mesh["nVertices"])
@@ -515,7 +519,11 @@ class Model:
         if ordering != LTS_ORDER_HILBERT:
             lts_regions_ordering(self.reg_h, ordering)
         p = make_params(g, dt, precision, mode, compensated, use_graph, block_size, profile, stream,
-                        pdl, kernel_path, l2_hints, coarse_schedule)
+                        pdl, kernel_path, l2_hints, coarse_schedule, self.layers)
+        h0 = np.ascontiguousarray(h0, np.float64).reshape(-1)
+        u0 = np.ascontiguousarray(u0, np.float64).reshape(-1)
+        if h0.size != self.layers * self.nC or u0.size != self.layers * self.nE:
+            raise ValueError("h0/u0 must hold layers x nCells / layers x nEdges values")
         if autotune:
             p, rep = lts_autotune(self.mesh_h, self.reg_h, h0, u0, p, autotune, tune_ordering)
             self.tuned = dict(params_dict(p), **rep)
@@ -525,10 +533,15 @@ class Model:
         lts_step(self.state_h, n)
 
     def read(self, h_out=None, u_out=None):
-        return lts_read(self.state_h, self.nC, self.nE, h_out, u_out)
+        L = self.layers
+        h, u, d = lts_read(self.state_h, L * self.nC, L * self.nE, h_out, u_out)
+        if L > 1 and h_out is None:
+            h, u = h.reshape(L, self.nC), u.reshape(L, self.nE)
+        return h, u, d
 
     def write(self, h, u, time=0.0, steps=0):
-        lts_write(self.state_h, h, u, time, steps)
+        lts_write(self.state_h, np.ascontiguousarray(h, np.float64).reshape(-1),
+                  np.ascontiguousarray(u, np.float64).reshape(-1), time, steps)
 
     def labels(self):
         return lts_regions_labels(self.reg_h, self.nC, self.nE)
