@@ -392,7 +392,8 @@ def extras(args, w, model, stats, stream, h_gpu, u_gpu, diag):
     # ---- per-kernel timing: the same coarse-step graph with an event-record
     #      node before and after every kernel node, on the state's stream
     tuned = model.tuned or {}
-    knobs = {k: tuned[k] for k in ("block_size", "kernel_path", "l2_hints", "coarse_schedule") if k in tuned}
+    knobs = {k: tuned[k] for k in ("block_size", "kernel_path", "l2_hints", "coarse_schedule",
+                                   "ring_occupancy") if k in tuned}
     if "ordering" in tuned:
         knobs["ordering"] = tuned["ordering"]
     prof = lts.Model(w.mesh, w.fine_mask, w.M, w.h0, w.u0, w.dt, w.g, precision=prec,

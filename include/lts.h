@@ -225,6 +225,10 @@ typedef struct lts_params {
                                and [layers][nEdges] (layer-major, original order inside
                                a layer); diagnostics sum over the layers.  Three-launch
                                path only, no ensembles.                                */
+    int32_t ring_occupancy; /* FP32, three-launch path: 0 (default) or 6 / 8 = the ring
+                               pass built for that many resident 256-thread blocks per
+                               SM (fewer registers, some spills), leaving block slots
+                               for the next launch's table prefetch                   */
     int32_t coarse_schedule;/* order of the coarse phases (results are identical):
                                LTS_COARSE_STEP4 (default): Step 4 on the coarse bands
                                C3 and beyond runs as a concurrent graph branch beside
@@ -252,8 +256,10 @@ int lts_step(lts_state s, int32_t n_coarse);
  * fastest as *best (base's g, dt, precision, mode, compensation and stream
  * kept; use_graph = 1).  Candidates: block_size 128 or 256, kernel_path 0
  * or 1, pdl on or off, L2 hints on or off, the coarse schedule (LTS3:
- * LTS_COARSE_STEP4, _FAR or _SERIAL).  Each is timed over `steps` coarse steps after 3 warm-up steps;
- * the three fastest are timed twice more and the best of three wins.  With
+ * LTS_COARSE_STEP4, _FAR or _SERIAL).  Each is timed over `steps` coarse
+ * steps after 3 warm-up steps; the three fastest are timed twice more and
+ * the best of three wins.  With the winner, FP32 states also try the ring
+ * occupancy variants 6 and 8 (best of two timings each).  With
  * flags & LTS_TUNE_ORDERING and no state using r, the other cell ordering
  * (lts_regions_ordering) is tried with the winner and r keeps the faster.
  * No configuration changes a result bit; the tuner only chooses speed.  The
@@ -263,7 +269,7 @@ int lts_step(lts_state s, int32_t n_coarse);
  * LTS_ECUDA. */
 #define LTS_TUNE_ORDERING 1
 typedef struct lts_tune_entry {
-    int32_t block_size, kernel_path, pdl, l2_hints, coarse_schedule, ordering;
+    int32_t block_size, kernel_path, pdl, l2_hints, coarse_schedule, ordering, ring_occupancy;
     double ms;              /* ms per coarse step (best of its timings; inf = not buildable) */
 } lts_tune_entry;
 typedef struct lts_tune_report {

@@ -24,6 +24,7 @@ namespace {
 struct Candidate {
     int block, path, pdl, no_l2, serial;   // serial: the coarse schedule
     double ms = INFINITY;
+    int occ = 0;                           // ring occupancy variant
 };
 
 lts_params apply(const lts_params& base, const Candidate& c) {
@@ -33,6 +34,7 @@ lts_params apply(const lts_params& base, const Candidate& c) {
     p.pdl = c.pdl;
     p.no_l2_hints = c.no_l2;
     p.coarse_schedule = c.serial;
+    p.ring_occupancy = c.occ;
     p.use_graph = 1;
     p.profile = 0;
     p.stream = nullptr;
@@ -119,6 +121,24 @@ extern "C" int lts_autotune(lts_mesh m, lts_regions r, const double* h0, const d
     for (const Candidate& c : cands)
         if (c.block == 256 && c.path == 0 && c.pdl == 1 && c.no_l2 == 0 && c.serial == LTS_COARSE_STEP4)
             default_ms = c.ms;
+    // the FP32 ring-pass occupancy variants with the winning configuration
+    Candidate occ_best = *win;
+    std::vector<Candidate> occ_tried;
+    if (base->precision == LTS_FP32 && win->path == 0) {
+        for (int occ : {6, 8}) {
+            Candidate c = *win;
+            c.occ = occ;
+            for (int rep_k = 0; rep_k < 2; ++rep_k) {
+                double ms = INFINITY;
+                int rc = time_config(m, r, h0, u0, apply(*base, c), steps, &ms);
+                if (rc != LTS_OK) return rc;
+                c.ms = rep_k == 0 ? ms : std::min(c.ms, ms);
+            }
+            occ_tried.push_back(c);
+            if (c.ms < occ_best.ms) occ_best = c;
+        }
+    }
+    win = &occ_best;
     *best = apply(*base, *win);
     best->stream = base->stream;
     double best_ms = win->ms;
@@ -144,7 +164,7 @@ extern "C" int lts_autotune(lts_mesh m, lts_regions r, const double* h0, const d
         }
     }
     if (rep) {
-        rep->candidates = static_cast<int32_t>(cands.size()) + (tried_orderings - 1);
+        rep->candidates = static_cast<int32_t>(cands.size() + occ_tried.size()) + (tried_orderings - 1);
         rep->best_ms = best_ms;
         rep->default_ms = default_ms;
         rep->ordering = ordering;
@@ -152,11 +172,13 @@ extern "C" int lts_autotune(lts_mesh m, lts_regions r, const double* h0, const d
         int n = 0;
         for (const Candidate& c : cands) {
             if (n >= 32) break;
-            rep->entry[n++] = {c.block, c.path, c.pdl, 1 - c.no_l2, c.serial, ordering0, c.ms};
+            rep->entry[n++] = {c.block, c.path, c.pdl, 1 - c.no_l2, c.serial, ordering0, 0, c.ms};
         }
+        for (const Candidate& c : occ_tried)
+            if (n < 32) rep->entry[n++] = {c.block, c.path, c.pdl, 1 - c.no_l2, c.serial, ordering0, c.occ, c.ms};
         if (tried_orderings == 2 && n < 32)
             rep->entry[n++] = {win->block, win->path, win->pdl, 1 - win->no_l2, win->serial, 1 - ordering0,
-                               other_ms};
+                               win->occ, other_ms};
     }
     return LTS_OK;
 }

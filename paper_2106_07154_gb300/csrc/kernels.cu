@@ -737,6 +737,16 @@ __global__ void __launch_bounds__(256) kernel_phase(const __grid_constant__ DevA
     phase_block<T, COMP, MAXR, KIND, LY>(a, a.seg[sidx], blockIdx.x);
 }
 
+// The FP32 ring pass compiled for MINB resident 256-thread blocks per SM
+// (fewer registers, possibly spills): a fine-region launch then leaves block
+// slots free, where the next launch's blocks prefetch their tables.
+template <bool COMP, int MINB>
+__global__ void __launch_bounds__(256, MINB) kernel_ring_occ(const __grid_constant__ DevArgs<float> a) {
+    griddep_launch_dependents();
+    const int sidx = find_seg(a, blockIdx.x);
+    phase_block<float, COMP, 8, 1, false>(a, a.seg[sidx], blockIdx.x);
+}
+
 // Segment-table variant (ensembles of meshes: one launch carries the
 // segments of every member, more than fit in the kernel parameters).  A
 // persistent grid walks the virtual blocks; each finds its segment by a
@@ -822,7 +832,7 @@ void fill_args(DevArgs<T>& a, const LaunchDesc& d, const void* tables, int smem,
 
 template <class T, bool COMP, int MAXR>
 cudaError_t launch_t(const LaunchDesc& d, const void* tables, int block, bool pdl, int smem, int* flag,
-                     cudaStream_t st, int layers) {
+                     cudaStream_t st, int layers, int ring_occ) {
     DevArgs<T> a;
     fill_args(a, d, tables, smem, flag);
     a.L = layers;
@@ -853,6 +863,10 @@ cudaError_t launch_t(const LaunchDesc& d, const void* tables, int block, bool pd
             case 1: return launch_kernel(kernel_phase<T, COMP, MAXR, 1, true>, blocks, block, pdl, st, a);
             default: return launch_kernel(kernel_phase<T, COMP, MAXR, 2, true>, blocks, block, pdl, st, a);
         }
+    }
+    if constexpr (sizeof(T) == 4 && MAXR == 8) {
+        if (d.kind == 1 && ring_occ == 6) return launch_kernel(kernel_ring_occ<COMP, 6>, blocks, block, pdl, st, a);
+        if (d.kind == 1 && ring_occ == 8) return launch_kernel(kernel_ring_occ<COMP, 8>, blocks, block, pdl, st, a);
     }
     switch (d.kind) {
         case 0: return launch_kernel(kernel_phase<T, COMP, MAXR, 0>, blocks, block, pdl, st, a);
@@ -979,8 +993,9 @@ template <class T, bool COMP>
 cudaError_t launch_any(const LaunchDesc& d, const void* tables, const KernelConfig& kc, int* flag,
                        cudaStream_t s) {
     const int L = kc.layers > 1 ? kc.layers : 1;
-    if (kc.maxdeg <= 8) return launch_t<T, COMP, 8>(d, tables, kc.block, kc.pdl, kc.tile_smem, flag, s, L);
-    return launch_t<T, COMP, MAX_DEGREE>(d, tables, kc.block, kc.pdl, kc.tile_smem, flag, s, L);
+    if (kc.maxdeg <= 8)
+        return launch_t<T, COMP, 8>(d, tables, kc.block, kc.pdl, kc.tile_smem, flag, s, L, kc.ring_occ);
+    return launch_t<T, COMP, MAX_DEGREE>(d, tables, kc.block, kc.pdl, kc.tile_smem, flag, s, L, 0);
 }
 
 }  // namespace

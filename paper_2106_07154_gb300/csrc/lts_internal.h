@@ -142,6 +142,7 @@ struct KernelConfig {
     int mindeg;      // smallest cell degree of the mesh (slots loaded unconditionally)
     bool pdl;        // programmatic dependent launch
     int layers = 1;  // layers per element (multi-layer states)
+    int ring_occ = 0;  // FP32 ring pass built for 6 or 8 resident blocks per SM (0: default)
 };
 
 // kernels.cu

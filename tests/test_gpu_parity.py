@@ -211,7 +211,8 @@ def test_options_do_not_change_results(sphw):
     pattern and the launch order, never an element's arithmetic."""
     a = run_gpu(sphw, 6, lts.LTS_FP32)
     for kw in ({"ordering": lts.LTS_ORDER_INDEX}, {"l2_hints": False},
-               {"coarse_schedule": lts.LTS_COARSE_FAR}, {"coarse_schedule": lts.LTS_COARSE_SERIAL}):
+               {"coarse_schedule": lts.LTS_COARSE_FAR}, {"coarse_schedule": lts.LTS_COARSE_SERIAL},
+               {"ring_occupancy": 6}, {"ring_occupancy": 8}):
         with lts.Model(sphw.mesh, sphw.fine_mask, sphw.M, sphw.h0, sphw.u0, sphw.dt,
                        precision=lts.LTS_FP32, **kw) as m:
             m.step(6)
