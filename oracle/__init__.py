@@ -63,6 +63,10 @@ def lib():
         L.or_lts2.argtypes = [C.c_void_p, C.c_void_p, _i8p, _i8p, C.c_int, C.c_double, C.c_int,
                               C.c_int, _f64p, _f64p]
         L.or_ssprk2.argtypes = [C.c_void_p, C.c_void_p, C.c_double, C.c_int, _f64p, _f64p]
+        L.or_region_ids.argtypes = [C.c_void_p, _i8p, _i8p, _i8p, _i8p, _i8p]
+        L.or_lts3_multi.argtypes = [C.c_void_p, C.c_void_p, _i8p, _i8p, _i8p, _i8p, C.c_int,
+                                    np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS"),
+                                    C.c_double, C.c_int, C.c_int, _f64p, _f64p]
         L.or_lts2_predict_coeffs.argtypes = [C.c_int, C.c_int, C.c_int, _f64p]
         L.or_mass.restype = C.c_double
         L.or_mass.argtypes = [C.c_void_p, _f64p]
@@ -217,6 +221,33 @@ class Oracle:
                            int(nsteps), int(step5_form), h, u)
         if rc != 0:
             raise ValueError("or_lts2 failed")
+        return h, u
+
+    def region_ids(self, region_of_fine, cell_label, edge_label):
+        """Region (1..R) of every fine/interface cell and edge, 0 on the coarse sets."""
+        creg = np.zeros(self.nC, np.int8)
+        ereg = np.zeros(self.nE, np.int8)
+        rc = lib().or_region_ids(self._h, np.ascontiguousarray(region_of_fine, np.int8),
+                                 np.ascontiguousarray(cell_label, np.int8),
+                                 np.ascontiguousarray(edge_label, np.int8), creg, ereg)
+        if rc != 0:
+            raise ValueError("the regions' fine and interface sets touch")
+        return creg, ereg
+
+    def lts3_multi(self, h, u, region_of_fine, Ms, dt, nsteps, g=9.81, step5_form=0,
+                   lam_c=None, lam_e=None):
+        """Several disjoint fine regions with their own M sharing the coarse step."""
+        rof = np.ascontiguousarray(region_of_fine, np.int8)
+        cl, el = self.regions((rof > 0).astype(np.int8))
+        creg, ereg = self.region_ids(rof, cl, el)
+        h = np.array(h, np.float64)
+        u = np.array(u, np.float64)
+        s = self._sys(g, lam_c, lam_e)
+        Ms = np.ascontiguousarray(Ms, np.int32)
+        rc = lib().or_lts3_multi(self._h, C.addressof(s), cl, el, creg, ereg, len(Ms), Ms,
+                                 float(dt), int(nsteps), int(step5_form), h, u)
+        if rc != 0:
+            raise ValueError("or_lts3_multi failed")
         return h, u
 
     def rk4(self, h, u, dt, nsteps, g=9.81, lam_c=None, lam_e=None):

@@ -811,6 +811,175 @@ int or_lts2(const or_mesh* m, const or_system* sys, const signed char* cl,
     return 0;
 }
 
+/* ---------------------------------------------- several fine regions (LTS3) */
+
+/* Region of every cell and edge of the fine and interface sets: a walk out
+ * of each region's fine cells through the non-coarse cells (labels 0..4);
+ * 0 for the coarse sets.  Returns -1 if two regions' sets touch. */
+int or_region_ids(const or_mesh* m, const signed char* region_of_fine, const signed char* cl,
+                  const signed char* el, signed char* creg, signed char* ereg) {
+    int nC = m->nC, nE = m->nE, bad = 0;
+    int* queue = (int*)xmalloc((size_t)nC * sizeof(int));
+    int head = 0, tail = 0;
+    for (int i = 0; i < nC; ++i) {
+        creg[i] = 0;
+        if (cl[i] <= 2 && region_of_fine[i] > 0) {
+            creg[i] = region_of_fine[i];
+            queue[tail++] = i;
+        }
+    }
+    while (head < tail) {
+        int i = queue[head++];
+        for (int j = 0; j < m->nEoC[i]; ++j) {
+            int e = m->EoC[(size_t)i * m->maxE + j];
+            int nb = m->CoE[2 * e] == i ? m->CoE[2 * e + 1] : m->CoE[2 * e];
+            if (cl[nb] == 5) continue;
+            if (creg[nb] == 0) {
+                creg[nb] = creg[i];
+                queue[tail++] = nb;
+            } else if (creg[nb] != creg[i]) {
+                bad = 1;
+            }
+        }
+    }
+    for (int e = 0; e < nE; ++e) {
+        int a = m->CoE[2 * e], b = m->CoE[2 * e + 1];
+        ereg[e] = el[e] == 5 ? 0 : (cl[a] <= cl[b] ? creg[a] : creg[b]);
+    }
+    free(queue);
+    return bad ? -1 : 0;
+}
+
+int or_lts3_multi(const or_mesh* m, const or_system* sys, const signed char* cl,
+                  const signed char* el, const signed char* creg, const signed char* ereg,
+                  int nreg, const int* Ms, double dt, int nsteps, int step5_form, double* h,
+                  double* u) {
+    for (int r = 0; r < nreg; ++r)
+        if (Ms[r] < 1) return -1;
+    int nC = m->nC, nE = m->nE;
+    size_t sc = (size_t)nC * sizeof(double), se = (size_t)nE * sizeof(double);
+    double *h_old = xmalloc(sc), *u_old = xmalloc(se);
+    double *h_1st = xmalloc(sc), *u_1st = xmalloc(se);
+    double *h_2nd = xmalloc(sc), *u_2nd = xmalloc(se);
+    double *h_oldk = xmalloc(sc), *u_oldk = xmalloc(se);
+    double *h_1stk = xmalloc(sc), *u_1stk = xmalloc(se);
+    double *h_2ndk = xmalloc(sc), *u_2ndk = xmalloc(se);
+    double *H1 = xmalloc(sc), *H2 = xmalloc(sc), *H3 = xmalloc(sc);
+    double *U1 = xmalloc(se), *U2 = xmalloc(se), *U3 = xmalloc(se);
+    double *H = xmalloc(sc), *U = xmalloc(se);
+    double c[3];
+
+    for (int n = 0; n < nsteps; ++n) {
+        memcpy(h_old, h, sc); memcpy(u_old, u, se);
+        memcpy(h_1st, h_old, sc); memcpy(u_1st, u_old, se);
+        memcpy(h_2nd, h_old, sc); memcpy(u_2nd, u_old, se);
+        /* Steps 1 and 2 on the union of the sets, as for one region */
+        or_rhs(m, sys, h_old, u_old, H, U);
+        for (int i = 0; i < nC; ++i)
+            if (!C_FINE(cl[i]) || C_FBAR(cl[i])) h_1st[i] = ssp_stage1(h_old[i], H[i], dt);
+        for (int e = 0; e < nE; ++e)
+            if (!E_FINE(el[e]) || E_FBAR(el[e])) u_1st[e] = ssp_stage1(u_old[e], U[e], dt);
+        or_rhs(m, sys, h_1st, u_1st, H, U);
+        for (int i = 0; i < nC; ++i)
+            if (cl[i] >= 3) h_2nd[i] = ssp_stage2(h_old[i], h_1st[i], H[i], dt);
+        for (int e = 0; e < nE; ++e)
+            if (el[e] >= 3) u_2nd[e] = ssp_stage2(u_old[e], u_1st[e], U[e], dt);
+        memcpy(h_oldk, h_old, sc); memcpy(u_oldk, u_old, se);
+        memcpy(h_1stk, h_1st, sc); memcpy(u_1stk, u_1st, se);
+        memcpy(h_2ndk, h_2nd, sc); memcpy(u_2ndk, u_2nd, se);
+        for (int i = 0; i < nC; ++i) H1[i] = H2[i] = H3[i] = 0.0;
+        for (int e = 0; e < nE; ++e) U1[e] = U2[e] = U3[e] = 0.0;
+
+        /* Step 3 for each region with its own M (the regions' right-hand sides
+         * read disjoint neighbourhoods, so their order does not matter) */
+        for (int r = 1; r <= nreg; ++r) {
+            const int M = Ms[r - 1];
+            const double dtM = dt / (double)M;
+#define IN_R(i) (creg[i] == r)
+#define EN_R(e) (ereg[e] == r)
+            for (int k = 0; k < M; ++k) {
+                or_lts3_predict_coeffs(k, M, 1, c);
+                for (int i = 0; i < nC; ++i)
+                    if (IN_R(i) && C_I1(cl[i])) h_oldk[i] = c[0] * h_old[i] + c[1] * h_1st[i] + c[2] * h_2nd[i];
+                for (int e = 0; e < nE; ++e)
+                    if (EN_R(e) && el[e] == 3) u_oldk[e] = c[0] * u_old[e] + c[1] * u_1st[e] + c[2] * u_2nd[e];
+                or_rhs(m, sys, h_oldk, u_oldk, H, U);
+                for (int i = 0; i < nC; ++i) if (IN_R(i) && C_I(cl[i])) H1[i] = H1[i] + H[i];
+                for (int e = 0; e < nE; ++e) if (EN_R(e) && (el[e] == 3 || el[e] == 4)) U1[e] = U1[e] + U[e];
+                for (int i = 0; i < nC; ++i)
+                    if (IN_R(i) && C_FINE(cl[i])) h_1stk[i] = ssp_stage1(h_oldk[i], H[i], dtM);
+                for (int e = 0; e < nE; ++e)
+                    if (EN_R(e) && E_FINE(el[e])) u_1stk[e] = ssp_stage1(u_oldk[e], U[e], dtM);
+
+                or_lts3_predict_coeffs(k, M, 2, c);
+                for (int i = 0; i < nC; ++i)
+                    if (IN_R(i) && C_I1(cl[i])) h_1stk[i] = c[0] * h_old[i] + c[1] * h_1st[i] + c[2] * h_2nd[i];
+                for (int e = 0; e < nE; ++e)
+                    if (EN_R(e) && el[e] == 3) u_1stk[e] = c[0] * u_old[e] + c[1] * u_1st[e] + c[2] * u_2nd[e];
+                or_rhs(m, sys, h_1stk, u_1stk, H, U);
+                for (int i = 0; i < nC; ++i) if (IN_R(i) && C_I(cl[i])) H2[i] = H2[i] + H[i];
+                for (int e = 0; e < nE; ++e) if (EN_R(e) && (el[e] == 3 || el[e] == 4)) U2[e] = U2[e] + U[e];
+                for (int i = 0; i < nC; ++i)
+                    if (IN_R(i) && C_FINE(cl[i])) h_2ndk[i] = ssp_stage2(h_oldk[i], h_1stk[i], H[i], dtM);
+                for (int e = 0; e < nE; ++e)
+                    if (EN_R(e) && E_FINE(el[e])) u_2ndk[e] = ssp_stage2(u_oldk[e], u_1stk[e], U[e], dtM);
+
+                or_lts3_predict_coeffs(k, M, 3, c);
+                for (int i = 0; i < nC; ++i)
+                    if (IN_R(i) && C_I1(cl[i])) h_2ndk[i] = c[0] * h_old[i] + c[1] * h_1st[i] + c[2] * h_2nd[i];
+                for (int e = 0; e < nE; ++e)
+                    if (EN_R(e) && el[e] == 3) u_2ndk[e] = c[0] * u_old[e] + c[1] * u_1st[e] + c[2] * u_2nd[e];
+                or_rhs(m, sys, h_2ndk, u_2ndk, H, U);
+                for (int i = 0; i < nC; ++i) if (IN_R(i) && C_I(cl[i])) H3[i] = H3[i] + H[i];
+                for (int e = 0; e < nE; ++e) if (EN_R(e) && (el[e] == 3 || el[e] == 4)) U3[e] = U3[e] + U[e];
+                for (int i = 0; i < nC; ++i)
+                    if (IN_R(i) && C_FINE(cl[i])) h_oldk[i] = ssp_stage3(h_oldk[i], h_2ndk[i], H[i], dtM);
+                for (int e = 0; e < nE; ++e)
+                    if (EN_R(e) && E_FINE(el[e])) u_oldk[e] = ssp_stage3(u_oldk[e], u_2ndk[e], U[e], dtM);
+            }
+#undef IN_R
+#undef EN_R
+        }
+
+        /* Step 4 on C */
+        or_rhs(m, sys, h_2nd, u_2nd, H, U);
+        for (int i = 0; i < nC; ++i)
+            if (C_C(cl[i])) h[i] = ssp_stage3(h_old[i], h_2nd[i], H[i], dt);
+        for (int e = 0; e < nE; ++e)
+            if (el[e] == 5) u[e] = ssp_stage3(u_old[e], u_2nd[e], U[e], dt);
+        for (int i = 0; i < nC; ++i) if (C_FINE(cl[i])) h[i] = h_oldk[i];
+        for (int e = 0; e < nE; ++e) if (E_FINE(el[e])) u[e] = u_oldk[e];
+
+        /* Step 5 on each region's interface with its own dt/M */
+        for (int i = 0; i < nC; ++i) {
+            if (!C_I(cl[i]) || creg[i] < 1) continue;
+            const double dtM = dt / (double)Ms[creg[i] - 1];
+            if (step5_form == 1) {
+                h[i] = h_old[i] + dtM * (H1[i] / 6.0 + H2[i] / 6.0 + 2.0 * H3[i] / 3.0);
+            } else {
+                double x1 = ssp_stage1(h_old[i], H1[i], dtM);
+                double x2 = ssp_stage2(h_old[i], x1, H2[i], dtM);
+                h[i] = ssp_stage3(h_old[i], x2, H3[i], dtM);
+            }
+        }
+        for (int e = 0; e < nE; ++e) {
+            if (!(el[e] == 3 || el[e] == 4) || ereg[e] < 1) continue;
+            const double dtM = dt / (double)Ms[ereg[e] - 1];
+            if (step5_form == 1) {
+                u[e] = u_old[e] + dtM * (U1[e] / 6.0 + U2[e] / 6.0 + 2.0 * U3[e] / 3.0);
+            } else {
+                double x1 = ssp_stage1(u_old[e], U1[e], dtM);
+                double x2 = ssp_stage2(u_old[e], x1, U2[e], dtM);
+                u[e] = ssp_stage3(u_old[e], x2, U3[e], dtM);
+            }
+        }
+    }
+    free(h_old); free(u_old); free(h_1st); free(u_1st); free(h_2nd); free(u_2nd);
+    free(h_oldk); free(u_oldk); free(h_1stk); free(u_1stk); free(h_2ndk); free(u_2ndk);
+    free(H1); free(H2); free(H3); free(U1); free(U2); free(U3); free(H); free(U);
+    return 0;
+}
+
 /* ------------------------------------------------------------ diagnostics */
 
 double or_mass(const or_mesh* m, const double* h) {

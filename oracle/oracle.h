@@ -123,6 +123,19 @@ int or_lts2(const or_mesh* m, const or_system* sys, const signed char* cell_labe
 /* Steps 3.1.1 / 3.2.1 coefficients for LTS2 (stage 1 or 2), as for LTS3. */
 void or_lts2_predict_coeffs(int k, int M, int stage, double* c);
 
+/* Several disjoint fine regions r = 1..nreg, each with its own M_r, sharing
+ * the coarse step (the regions of the Remark in Section 2.3, not nested):
+ * Steps 1, 2 and 4 of Algorithm 2.2 on the union of the sets, Step 3 and
+ * Step 5 per region with M_r on its own F, I1, I2.  Labels come from
+ * or_regions on the union of the regions' cells; creg/ereg from
+ * or_region_ids (0 = coarse).  The regions' sets must not touch. */
+int or_region_ids(const or_mesh* m, const signed char* region_of_fine, const signed char* cell_label,
+                  const signed char* edge_label, signed char* creg, signed char* ereg);
+int or_lts3_multi(const or_mesh* m, const or_system* sys, const signed char* cell_label,
+                  const signed char* edge_label, const signed char* creg, const signed char* ereg,
+                  int nreg, const int* M, double dt, int nsteps, int step5_form, double* h,
+                  double* u);
+
 /* Diagnostics: mass sum_i A_i h_i and energy sum_i A_i h_i (K_i + g(h_i/2 + b_i)). */
 double or_mass(const or_mesh* m, const double* h);
 double or_energy(const or_mesh* m, double g, const double* h, const double* u);
