@@ -152,6 +152,22 @@ int lts_regions_set(lts_mesh m, const int8_t* fine_mask, int32_t order, int32_t 
                     int32_t interface_layers, lts_regions* out);
 void lts_regions_destroy(lts_regions r);
 
+/* Several disjoint fine regions, each with its own M, sharing the coarse
+ * step (the more-than-two-regions case of the Remark in Section 2.3, for
+ * regions that are not nested): Steps 1, 2 and 4 of Algorithm 2.2 run on
+ * the union of the sets; Step 3 and Step 5 run per region r with M[r-1] on
+ * its own fine and interface sets.  region_of_cell[i] = r in 1..nregions
+ * for the fine cells of region r, 0 elsewhere.  Each region's cells of the
+ * bands F..C5 form one contiguous block (band order and Hilbert order
+ * inside), the far coarse cells a last block; the plans of the blocks merge
+ * launch by launch into segment-table launches.  A region's fine,
+ * interface and first two coarse layers must not touch another region's
+ * (LTS_EINVAL).  LTS3 only (order 3); three-launch path, one layer, no
+ * profiling, no fused tiles.  nregions = 1 is lts_regions_set. */
+int lts_regions_set_multi(lts_mesh m, const int8_t* region_of_cell, int32_t nregions,
+                          const int32_t* M, int32_t order, int32_t interface_layers,
+                          lts_regions* out);
+
 /* Region labels in the caller's original order (host arrays):
  *   cell_label [nCells]: 0 F \ Fbar, 1 F2, 2 F1, 3 I1, 4 I2, 5 C
  *   edge_label [nEdges]: 0 F^e, 1 Fbar^e, 3 I1^e, 4 I2^e, 5 C^e

@@ -28,11 +28,6 @@
 using namespace lts;
 
 struct lts_ensemble_s {
-    struct Launch {
-        LaunchDesc d;                 // kind, buffers, L2 policy, branch, fork, join
-        const void* dsegs = nullptr;  // device segment records
-        int nseg = 0, vblocks = 0, grid = 0;
-    };
     std::vector<lts_state_s*> members;
     std::vector<double> t0;           // member clocks when the ensemble was made
     std::vector<int64_t> steps0;
@@ -57,7 +52,7 @@ struct lts_ensemble_s {
     void* ring_c_side = nullptr;
     void* ring_k_side = nullptr;
     int* flag = nullptr;
-    std::vector<Launch> plan[2];
+    std::vector<TableLaunch> plan[2];
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -253,15 +248,8 @@ bool placed_in_bounds(const lts_ensemble_s* E, size_t m, const SegDesc& s) {
     return fam_ok(s.cfam, s.base) && fam_ok(s.cfam2, s.base2);
 }
 
-struct Group {
-    LaunchDesc proto;
-    std::vector<SegDesc> segs;
-    double bytes = 0.0;
-    bool init = false;
-};
-
 int build_plan(lts_ensemble_s* E, int parity, int nsm) {
-    std::map<int, Group> groups;
+    std::vector<std::vector<LaunchDesc>> plans;
     for (size_t m = 0; m < E->members.size(); ++m) {
         lts_state_s* S = E->members[m];
         // a view of the member whose buffers are the packed ones
@@ -292,110 +280,33 @@ int build_plan(lts_ensemble_s* E, int parity, int nsm) {
         make_plan(&F, parity, plan);
         F.reg = nullptr;
         const HostMesh& hm = S->reg->mesh->m;
-        for (const LaunchDesc& d : plan) {
-            if (d.nseg == 0) continue;   // fork / join markers are rebuilt below
-            if (d.key < 0) return set_error(LTS_EINVAL, "internal error: unkeyed launch");
-            Group& g = groups[d.key];
-            if (!g.init) {
-                g.proto = d;
-                g.proto.nseg = 0;
-                g.proto.fork = g.proto.join = false;
-                g.init = true;
-            } else if (g.proto.kind != d.kind || g.proto.in_h != d.in_h || g.proto.in_u != d.in_u ||
-                       g.proto.branch != d.branch || g.proto.l2 != d.l2 || g.proto.q != d.q) {
-                return set_error(LTS_EINVAL, "internal error: member plans disagree at key %d", d.key);
-            }
+        for (LaunchDesc& d : plan) {
+            if (d.nseg == 0) continue;
+            d.bytes = plan_launch_bytes(d, S->reg->r, hm.nC, hm.nE, hm.nV, S->tsz, S->kc.comp);
             for (int k = 0; k < d.nseg; ++k) {
                 if (d.seg[k].elem < 0) return set_error(LTS_EINVAL, "ensembles run the three-launch path only");
                 const SegDesc ps = place(E, m, d.seg[k]);
                 if (ps.end > ps.begin && !placed_in_bounds(E, m, ps))
                     return set_error(LTS_EINVAL, "internal error: member %zu segment (type %d) out of bounds", m,
                                      ps.type);
-                g.segs.push_back(ps);
+                d.seg[k] = ps;
             }
-            g.bytes += plan_launch_bytes(d, S->reg->r, hm.nC, hm.nE, hm.nV, S->tsz, S->kc.comp);
         }
+        plans.push_back(std::move(plan));
     }
-    // device segment records of every launch, one allocation
-    std::vector<std::vector<unsigned char>> recs;
-    std::vector<lts_ensemble_s::Launch> out;
-    std::vector<size_t> rec_off;
-    size_t total = 0;
-    for (auto& kv : groups) {
-        Group& g = kv.second;
-        lts_ensemble_s::Launch L;
-        L.d = g.proto;
-        std::vector<unsigned char> rec;
-        L.vblocks = encode_segment_table(E->kc, g.segs.data(), static_cast<int>(g.segs.size()), rec, &L.nseg);
-        if (L.vblocks < 0) return set_error(LTS_EINVAL, "internal error: segment kind not tabled");
-        if (L.nseg == 0) continue;
-        const int per_sm = table_blocks_per_sm(E->kc, L.d.kind);
-        L.grid = per_sm > 0 ? per_sm * nsm : 0;
-        if (parity == 0) {
-            E->bytes[L.d.kind] += g.bytes;
-            E->launches += 1;
-            E->segments += L.nseg;
-        }
-        total = (total + 255) & ~size_t(255);
-        rec_off.push_back(total);
-        total += rec.size();
-        recs.push_back(std::move(rec));
-        out.push_back(L);
+    TablePlanStats st;
+    int rc = merge_table_plan(E->kc, plans, nsm, E->arena, E->plan[parity], &st);
+    if (rc != LTS_OK) return rc;
+    if (parity == 0) {
+        for (int k = 0; k < NKINDS; ++k) E->bytes[k] = st.bytes[k];
+        E->launches = st.launches;
+        E->segments = st.segments;
     }
-    cudaError_t err = cudaSuccess;
-    unsigned char* dev = static_cast<unsigned char*>(E->arena.alloc(std::max<size_t>(total, 256), err));
-    if (err != cudaSuccess) return set_error(LTS_ENOMEM, "ensemble segment tables: %s", cudaGetErrorString(err));
-    CUDA_TRY(cudaDeviceSynchronize());
-    for (size_t k = 0; k < out.size(); ++k) {
-        CUDA_TRY(cudaMemcpy(dev + rec_off[k], recs[k].data(), recs[k].size(), cudaMemcpyHostToDevice));
-        out[k].dsegs = dev + rec_off[k];
-    }
-    // side branch (Step 4 on the far coarse band): fork before its first
-    // launch, join before the first launch of the tail, or at the end
-    int first_side = -1, first_tail = -1;
-    for (size_t k = 0; k < out.size(); ++k) {
-        if (out[k].d.branch && first_side < 0) first_side = static_cast<int>(k);
-        if (!out[k].d.branch && first_side >= 0 && first_tail < 0 &&
-            k > static_cast<size_t>(first_side) && out[k].d.key >= KEY_TAIL)
-            first_tail = static_cast<int>(k);
-    }
-    if (first_side >= 0) {
-        out[first_side].d.fork = true;
-        if (first_tail >= 0) {
-            out[first_tail].d.join = true;
-        } else {
-            lts_ensemble_s::Launch j;
-            j.d.join = true;
-            out.push_back(j);
-        }
-    }
-    E->plan[parity] = std::move(out);
     return LTS_OK;
 }
 
-int enqueue(lts_ensemble_s* E, const std::vector<lts_ensemble_s::Launch>& plan, cudaStream_t st,
-            cudaStream_t side) {
-    bool after_event[2] = {false, false};
-    for (const auto& L : plan) {
-        if (L.d.fork) {
-            CUDA_TRY(cudaEventRecord(E->ev_fork, st));
-            CUDA_TRY(cudaStreamWaitEvent(side, E->ev_fork, 0));
-            after_event[1] = true;
-        }
-        if (L.d.join) {
-            CUDA_TRY(cudaEventRecord(E->ev_join, side));
-            CUDA_TRY(cudaStreamWaitEvent(st, E->ev_join, 0));
-            after_event[0] = true;
-        }
-        if (L.nseg == 0) continue;
-        KernelConfig kc = E->kc;
-        if (after_event[L.d.branch]) kc.pdl = false;
-        after_event[L.d.branch] = false;
-        cudaError_t e = launch_phase_table(L.d, L.dsegs, L.nseg, L.vblocks, L.grid, E->tables, kc, E->flag,
-                                           L.d.branch ? side : st);
-        if (e != cudaSuccess) return set_error(LTS_ECUDA, "ensemble launch: %s", cudaGetErrorString(e));
-    }
-    return LTS_OK;
+int enqueue(lts_ensemble_s* E, const std::vector<TableLaunch>& plan, cudaStream_t st, cudaStream_t side) {
+    return enqueue_table_plan(plan, E->tables, E->kc, E->flag, st, side, E->ev_fork, E->ev_join);
 }
 
 int capture(lts_ensemble_s* E) {
@@ -439,6 +350,119 @@ int copy_member(lts_ensemble_s* E, size_t m, bool into_member) {
 }
 
 }  // namespace
+
+namespace lts {
+
+int merge_table_plan(const KernelConfig& kc, const std::vector<std::vector<LaunchDesc>>& plans, int nsm,
+                     DeviceArena& arena, std::vector<TableLaunch>& out_plan, TablePlanStats* stats) {
+    struct Group {
+        LaunchDesc proto;
+        std::vector<SegDesc> segs;
+        double bytes = 0.0;
+        bool init = false;
+    };
+    std::map<int, Group> groups;
+    for (const auto& plan : plans)
+        for (const LaunchDesc& d : plan) {
+            if (d.nseg == 0) continue;   // fork / join markers are rebuilt below
+            if (d.key < 0) return set_error(LTS_EINVAL, "internal error: unkeyed launch");
+            Group& g = groups[d.key];
+            if (!g.init) {
+                g.proto = d;
+                g.proto.nseg = 0;
+                g.proto.fork = g.proto.join = false;
+                g.init = true;
+            } else if (g.proto.kind != d.kind || g.proto.in_h != d.in_h || g.proto.in_u != d.in_u ||
+                       g.proto.branch != d.branch || g.proto.l2 != d.l2 || g.proto.q != d.q) {
+                return set_error(LTS_EINVAL, "internal error: member plans disagree at key %d", d.key);
+            }
+            for (int k = 0; k < d.nseg; ++k) g.segs.push_back(d.seg[k]);
+            g.bytes += d.bytes;
+        }
+    // device segment records of every launch, one allocation
+    std::vector<std::vector<unsigned char>> recs;
+    std::vector<TableLaunch> out;
+    std::vector<size_t> rec_off;
+    size_t total = 0;
+    TablePlanStats st;
+    for (auto& kv : groups) {
+        Group& g = kv.second;
+        TableLaunch L;
+        L.d = g.proto;
+        L.d.bytes = g.bytes;
+        std::vector<unsigned char> rec;
+        L.vblocks = encode_segment_table(kc, g.segs.data(), static_cast<int>(g.segs.size()), rec, &L.nseg);
+        if (L.vblocks < 0) return set_error(LTS_EINVAL, "internal error: segment kind not tabled");
+        if (L.nseg == 0) continue;
+        const int per_sm = table_blocks_per_sm(kc, L.d.kind);
+        L.grid = (per_sm > 0 && nsm > 0) ? per_sm * nsm : 0;
+        st.bytes[L.d.kind] += g.bytes;
+        st.launches += 1;
+        st.segments += L.nseg;
+        total = (total + 255) & ~size_t(255);
+        rec_off.push_back(total);
+        total += rec.size();
+        recs.push_back(std::move(rec));
+        out.push_back(L);
+    }
+    cudaError_t err = cudaSuccess;
+    unsigned char* dev = static_cast<unsigned char*>(arena.alloc(std::max<size_t>(total, 256), err));
+    if (err != cudaSuccess) return set_error(LTS_ENOMEM, "segment tables: %s", cudaGetErrorString(err));
+    CUDA_TRY(cudaDeviceSynchronize());
+    for (size_t k = 0; k < out.size(); ++k) {
+        CUDA_TRY(cudaMemcpy(dev + rec_off[k], recs[k].data(), recs[k].size(), cudaMemcpyHostToDevice));
+        out[k].dsegs = dev + rec_off[k];
+    }
+    // the concurrent branch: fork before its first launch, join before the
+    // first launch of the tail, or at the end
+    int first_side = -1, first_tail = -1;
+    for (size_t k = 0; k < out.size(); ++k) {
+        if (out[k].d.branch && first_side < 0) first_side = static_cast<int>(k);
+        if (!out[k].d.branch && first_side >= 0 && first_tail < 0 &&
+            k > static_cast<size_t>(first_side) && out[k].d.key >= KEY_TAIL)
+            first_tail = static_cast<int>(k);
+    }
+    if (first_side >= 0) {
+        out[first_side].d.fork = true;
+        if (first_tail >= 0) {
+            out[first_tail].d.join = true;
+        } else {
+            TableLaunch j;
+            j.d.join = true;
+            out.push_back(j);
+        }
+    }
+    out_plan = std::move(out);
+    if (stats) *stats = st;
+    return LTS_OK;
+}
+
+int enqueue_table_plan(const std::vector<TableLaunch>& plan, const void* tables, const KernelConfig& kc,
+                       int* flag, cudaStream_t st, cudaStream_t side, cudaEvent_t ev_fork, cudaEvent_t ev_join) {
+    bool after_event[2] = {false, false};
+    for (const auto& L : plan) {
+        if (L.d.fork) {
+            CUDA_TRY(cudaEventRecord(ev_fork, st));
+            CUDA_TRY(cudaStreamWaitEvent(side, ev_fork, 0));
+            after_event[1] = true;
+        }
+        if (L.d.join) {
+            CUDA_TRY(cudaEventRecord(ev_join, side));
+            CUDA_TRY(cudaStreamWaitEvent(st, ev_join, 0));
+            after_event[0] = true;
+        }
+        if (L.nseg == 0) continue;
+        KernelConfig k = kc;
+        if (after_event[L.d.branch]) k.pdl = false;
+        after_event[L.d.branch] = false;
+        cudaError_t e = launch_phase_table(L.d, L.dsegs, L.nseg, L.vblocks, L.grid, tables, k, flag,
+                                           L.d.branch ? side : st);
+        if (e != cudaSuccess) return set_error(LTS_ECUDA, "table launch: %s", cudaGetErrorString(e));
+    }
+    return LTS_OK;
+}
+
+}  // namespace lts
 
 extern "C" {
 

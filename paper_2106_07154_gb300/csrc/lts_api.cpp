@@ -840,6 +840,59 @@ int enqueue_plan_timed(lts_state_s* S, const std::vector<LaunchDesc>& plan, cuda
     return LTS_OK;
 }
 
+// Several fine regions: the plan of every block (one per region with its M
+// and its own snapshots and correction terms, one for the far coarse cells),
+// each seeing the shared state buffers and its block's band offsets, merged
+// launch by launch into segment-table launches.
+int build_multi_plan(lts_state_s* S, int parity, int nsm, TablePlanStats* st) {
+    const RegionsHost& r = S->reg->r;
+    const HostMesh& m = S->reg->mesh->m;
+    std::vector<std::vector<LaunchDesc>> plans;
+    for (int b = 0; b <= r.nreg; ++b) {
+        lts_regions_s view;   // band offsets and M of block b only (planning needs no more)
+        for (int k = 0; k <= NBANDS; ++k) {
+            view.r.cb[k] = r.mcb[b][k];
+            view.r.eb[k] = r.meb[b][k];
+            view.r.vb[k] = r.mvb[b][k];
+        }
+        view.r.M = b < r.nreg ? r.Mr[b] : 1;
+        view.r.order = r.order;
+        view.r.layers = r.layers;
+        lts_state_s F;
+        F.reg = &view;
+        F.p = S->p;
+        F.kc = S->kc;
+        F.tsz = S->tsz;
+        for (int k = 0; k < 4; ++k) F.buf[k] = S->buf[k];
+        const auto& mb = S->mbufs[b];
+        F.P1c = mb.P1c;
+        F.P1e = mb.P1e;
+        F.P2c = mb.P2c;
+        F.P2e = mb.P2e;
+        for (int k = 0; k < 3; ++k) {
+            F.acc_c[k] = mb.acc_c[k];
+            F.acc_e[k] = mb.acc_e[k];
+        }
+        F.q = S->q;
+        F.ring_c = S->ring_c;
+        F.ring_k = S->ring_k;
+        F.q_side = S->q_side;
+        F.ring_c_side = S->ring_c_side;
+        F.ring_k_side = S->ring_k_side;
+        F.flag = S->flag;
+        std::vector<LaunchDesc> plan;
+        make_plan(&F, parity, plan);
+        F.reg = nullptr;
+        for (LaunchDesc& d : plan) {
+            if (d.nseg == 0) continue;
+            if (S->p.no_l2_hints) d.l2 = 0;
+            d.bytes = launch_bytes(d, r, m.nC, m.nE, m.nV, S->tsz, S->kc.comp, 1);
+        }
+        plans.push_back(std::move(plan));
+    }
+    return merge_table_plan(S->kc, plans, nsm, S->arena, S->tplan[parity], st);
+}
+
 int capture_graphs(lts_state_s* S) {
     for (int p = 0; p < 2; ++p) {
         if (S->p.profile == 2) {
@@ -848,8 +901,10 @@ int capture_graphs(lts_state_s* S) {
         }
         cudaGraph_t g = nullptr;
         CUDA_TRY(cudaStreamBeginCapture(S->capture_stream, cudaStreamCaptureModeThreadLocal));
-        int rc = S->p.profile == 2 ? enqueue_plan_timed(S, S->plan[p], S->capture_stream, p)
-                                   : enqueue_plan(S, S->plan[p], S->capture_stream, S->capture_side);
+        int rc = S->multi ? enqueue_table_plan(S->tplan[p], S->tables, S->kc, S->flag, S->capture_stream,
+                                               S->capture_side, S->ev_fork, S->ev_join)
+                 : S->p.profile == 2 ? enqueue_plan_timed(S, S->plan[p], S->capture_stream, p)
+                                     : enqueue_plan(S, S->plan[p], S->capture_stream, S->capture_side);
         cudaError_t e = cudaStreamEndCapture(S->capture_stream, &g);
         if (rc != LTS_OK) {
             if (g) cudaGraphDestroy(g);
@@ -878,6 +933,28 @@ int state_alloc(lts_state_s* S) {
         if (comp) {
             S->buf[k].hl = A(m.nC);
             S->buf[k].ul = A(m.nE);
+        }
+    }
+    if (S->multi) {
+        // one set of interface snapshots and correction terms per region
+        S->mbufs.assign(r.nreg + 1, lts_state_s::MemberBufs{});
+        for (int b = 0; b < r.nreg; ++b) {
+            auto& mb = S->mbufs[b];
+            const auto &cb = r.mcb[b], &eb = r.meb[b];
+            const int n1c = cb[B_I1 + 1] - cb[B_I1], n1e = eb[B_I1 + 1] - eb[B_I1];
+            const int nic = cb[B_I2 + 1] - cb[B_I1], nie = eb[B_I2 + 1] - eb[B_I1];
+            for (SV* p : {&mb.P1c, &mb.P2c}) {
+                p->hh = A(n1c);
+                if (comp) p->hl = A(n1c);
+            }
+            for (SV* p : {&mb.P1e, &mb.P2e}) {
+                p->uh = A(n1e);
+                if (comp) p->ul = A(n1e);
+            }
+            for (int k = 0; k < 3; ++k) {
+                mb.acc_c[k] = A(nic);
+                mb.acc_e[k] = A(nie);
+            }
         }
     }
     const int nI1c = r.cb[B_I1 + 1] - r.cb[B_I1], nI1e = r.eb[B_I1 + 1] - r.eb[B_I1];
@@ -1116,6 +1193,33 @@ int lts_regions_set(lts_mesh m, const int8_t* fine_mask, int32_t order, int32_t 
     return LTS_OK;
 }
 
+int lts_regions_set_multi(lts_mesh m, const int8_t* region_of_cell, int32_t nregions, const int32_t* M,
+                          int32_t order, int32_t layers, lts_regions* out) {
+    if (!m || !region_of_cell || !M || !out) return set_error(LTS_EINVAL, "null argument");
+    *out = nullptr;
+    if (order != 3) return set_error(LTS_EINVAL, "several fine regions run LTS3 only (order 3)");
+    if (nregions < 1 || nregions > 64) return set_error(LTS_EINVAL, "nregions must be in [1, 64]");
+    for (int k = 0; k < nregions; ++k)
+        if (M[k] < 1 || M[k] > 4096) return set_error(LTS_EINVAL, "M of region %d must be in [1, 4096]", k + 1);
+    std::unique_ptr<lts_regions_s> R(new (std::nothrow) lts_regions_s);
+    if (!R) return set_error(LTS_ENOMEM, "out of host memory");
+    int rc;
+    try {
+        rc = compute_regions_multi(m->m, region_of_cell, nregions, layers, 0, R->r);
+        if (rc == LTS_OK && nregions == 1) rc = build_tiles(m->m, R->r, kDefaultTileCells);
+    } catch (const std::bad_alloc&) {
+        return set_error(LTS_ENOMEM, "out of host memory");
+    }
+    if (rc != LTS_OK) return rc;
+    R->r.M = M[0];
+    R->r.Mr.assign(M, M + nregions);
+    R->r.order = order;
+    m->ref++;
+    R->mesh = m;
+    *out = R.release();
+    return LTS_OK;
+}
+
 void lts_regions_destroy(lts_regions r) { release_regions(r); }
 
 int lts_regions_labels(lts_regions r, int8_t* cl, int8_t* el) {
@@ -1131,6 +1235,7 @@ int lts_regions_labels(lts_regions r, int8_t* cl, int8_t* el) {
 
 int lts_regions_tiling(lts_regions r, int32_t tile_cells) {
     if (!r) return set_error(LTS_EINVAL, "null regions");
+    if (r->r.nreg > 1) return set_error(LTS_EINVAL, "several fine regions have no tiles (three-launch path)");
     if (r->ref.load() != 1) return set_error(LTS_EINVAL, "regions are in use by a state");
     int rc;
     try {
@@ -1152,14 +1257,20 @@ int lts_regions_ordering(lts_regions r, int32_t ordering) {
     RegionsHost nr;
     int rc;
     try {
-        const std::vector<int8_t> fine = r->r.fine;
-        rc = compute_regions(r->mesh->m, fine.data(), r->r.layers, ordering, nr);
-        if (rc == LTS_OK) rc = build_tiles(r->mesh->m, nr, r->r.tile_cells);
+        if (r->r.nreg > 1) {
+            const std::vector<int8_t> rid = r->r.rid;
+            rc = compute_regions_multi(r->mesh->m, rid.data(), r->r.nreg, r->r.layers, ordering, nr);
+        } else {
+            const std::vector<int8_t> fine = r->r.fine;
+            rc = compute_regions(r->mesh->m, fine.data(), r->r.layers, ordering, nr);
+            if (rc == LTS_OK) rc = build_tiles(r->mesh->m, nr, r->r.tile_cells);
+        }
     } catch (const std::bad_alloc&) {
         return set_error(LTS_ENOMEM, "out of host memory");
     }
     if (rc != LTS_OK) return rc;
     nr.M = r->r.M;
+    nr.Mr = r->r.Mr;
     nr.order = r->r.order;
     r->r = std::move(nr);
     r->arena[0].reset();   // device tables are rebuilt on the next state creation
@@ -1198,6 +1309,10 @@ int lts_state_create(lts_mesh mesh, lts_regions reg, const double* h0, const dou
         return set_error(LTS_EINVAL, "mode must be LTS_MODE_LTS, LTS_MODE_SSPRK3 or LTS_MODE_SSPRK2");
     if (p->kernel_path == 1 && (p->mode == LTS_MODE_SSPRK2 || (p->mode == LTS_MODE_LTS && reg->r.order == 2)))
         return set_error(LTS_EINVAL, "the fused tile kernel runs LTS3 and SSPRK3 only");
+    const bool multi = reg->r.nreg > 1 && p->mode == LTS_MODE_LTS;
+    if (multi && (p->kernel_path != 0 || p->profile != 0 || (p->layers > 1)))
+        return set_error(LTS_EINVAL,
+                         "several fine regions run the three-launch path, single layer, without profiling");
     int bs = p->block_size ? p->block_size : 256;
     if (bs < 32 || bs > 256 || bs % 32) return set_error(LTS_EINVAL, "block_size must be 32..256, multiple of 32");
     int rc = check_device();
@@ -1255,13 +1370,36 @@ int lts_state_create(lts_mesh mesh, lts_regions reg, const double* h0, const dou
     CUDA_TRY(cudaEventCreateWithFlags(&S->ev_join, cudaEventDisableTiming));
     reg->ref++;
     S->reg = reg;
+    S->multi = multi;
     rc = state_alloc(S.get());
     if (rc != LTS_OK) {
         release_regions(reg);
         S->reg = nullptr;
         return rc;
     }
-    for (int par = 0; par < 2; ++par) {
+    if (multi) {
+        int nsm = 0;
+        CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        for (int par = 0; par < 2 && rc == LTS_OK; ++par) {
+            TablePlanStats st;
+            rc = build_multi_plan(S.get(), par, nsm, &st);
+            if (par == 0)
+                for (int k = 0; k < NKINDS; ++k) {
+                    S->bytes[k] = st.bytes[k];
+                    S->launches[k] = 0;
+                }
+            if (par == 0)
+                for (const auto& L : S->tplan[0])
+                    if (L.nseg) S->launches[L.d.kind] += 1;
+        }
+        if (rc != LTS_OK) {
+            lts_regions_s* keep = S->reg;
+            S.reset();
+            release_regions(keep);
+            return rc;
+        }
+    }
+    for (int par = 0; par < 2 && !multi; ++par) {
         if (p->kernel_path == 1) {
             if (p->mode == LTS_MODE_LTS) plan_lts3_fused(S.get(), par, S->plan[par]);
             else plan_ssprk3_fused(S.get(), par, S->plan[par]);
@@ -1360,7 +1498,9 @@ int lts_step(lts_state s, int32_t n) {
         if (s->exec[s->parity]) {
             CUDA_TRY(cudaGraphLaunch(s->exec[s->parity], s->stream));
         } else {
-            int rc = enqueue_plan(s, s->plan[s->parity], s->stream, s->side_stream);
+            int rc = s->multi ? enqueue_table_plan(s->tplan[s->parity], s->tables, s->kc, s->flag, s->stream,
+                                                   s->side_stream, s->ev_fork, s->ev_join)
+                              : enqueue_plan(s, s->plan[s->parity], s->stream, s->side_stream);
             if (rc != LTS_OK) return rc;
         }
         s->parity ^= 1;

@@ -77,6 +77,13 @@ struct lts_regions_s {
     int device = -1;
 };
 
+// One launch of a segment-table plan (ensembles, several fine regions): the
+// segments live in device memory, any number per launch.
+struct TableLaunch {
+    lts::LaunchDesc d;            // kind, buffers, L2 policy, branch, fork, join, bytes
+    const void* dsegs = nullptr;  // device segment records
+    int nseg = 0, vblocks = 0, grid = 0;
+};
 struct SV {   // one state vector (h, u) with optional compensation words
     void* hh = nullptr;
     void* hl = nullptr;
@@ -116,6 +123,17 @@ struct lts_state_s {
     double* diag_out = nullptr;
     int diag_blocks = 0;
     std::vector<lts::LaunchDesc> plan[2];
+    // several fine regions: one plan per region (and one for the far coarse
+    // cells), merged launch by launch into segment-table launches; each
+    // region keeps its own interface snapshots and correction terms
+    bool multi = false;
+    std::vector<TableLaunch> tplan[2];
+    struct MemberBufs {
+        SV P1c, P1e, P2c, P2e;
+        void* acc_c[3] = {};
+        void* acc_e[3] = {};
+    };
+    std::vector<MemberBufs> mbufs;
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
     int parity = 0;
     int64_t steps = 0;
@@ -130,6 +148,18 @@ struct lts_state_s {
 };
 
 namespace lts {
+
+struct TablePlanStats {
+    double bytes[NKINDS] = {};
+    int launches = 0, segments = 0;
+};
+// Merges plans whose segments already index the shared arrays, launch by
+// launch in key order (d.bytes of every member launch summed per launch);
+// nsm > 0: persistent grids of resident blocks x nsm.  ensemble.cpp.
+int merge_table_plan(const KernelConfig& kc, const std::vector<std::vector<LaunchDesc>>& plans, int nsm,
+                     DeviceArena& arena, std::vector<TableLaunch>& out, TablePlanStats* stats);
+int enqueue_table_plan(const std::vector<TableLaunch>& plan, const void* tables, const KernelConfig& kc,
+                       int* flag, cudaStream_t st, cudaStream_t side, cudaEvent_t ev_fork, cudaEvent_t ev_join);
 
 // Internal planning API used by the ensemble (ensemble.cpp).
 int device_check();

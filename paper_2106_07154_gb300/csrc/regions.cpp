@@ -87,7 +87,32 @@ std::vector<int> bfs(const HostMesh& m, const std::vector<char>& source,
 
 }  // namespace
 
+namespace {
+int regions_impl(const HostMesh& m, const int8_t* fine, int layers, int ordering, RegionsHost& r,
+                 const int8_t* rid, int nreg);
+}
+
 int compute_regions(const HostMesh& m, const int8_t* fine, int layers, int ordering, RegionsHost& r) {
+    return regions_impl(m, fine, layers, ordering, r, nullptr, 1);
+}
+
+int compute_regions_multi(const HostMesh& m, const int8_t* region_of_cell, int nreg, int layers, int ordering,
+                          RegionsHost& r) {
+    if (nreg < 1 || nreg > 64) return set_error(LTS_EINVAL, "number of regions must be in [1, 64]");
+    std::vector<int8_t> fine(m.nC);
+    for (int i = 0; i < m.nC; ++i) {
+        if (region_of_cell[i] < 0 || region_of_cell[i] > nreg)
+            return set_error(LTS_EINVAL, "region id %d of cell %d out of range", region_of_cell[i], i);
+        fine[i] = region_of_cell[i] > 0;
+    }
+    const int rc = regions_impl(m, fine.data(), layers, ordering, r, nreg > 1 ? region_of_cell : nullptr, nreg);
+    if (rc == LTS_OK) r.rid.assign(region_of_cell, region_of_cell + m.nC);
+    return rc;
+}
+
+namespace {
+int regions_impl(const HostMesh& m, const int8_t* fine, int layers, int ordering, RegionsHost& r,
+                 const int8_t* rid, int nreg) {
     if (layers < 1) return set_error(LTS_EINVAL, "interface_layers must be >= 1");
     if (ordering != 0 && ordering != 1) return set_error(LTS_EINVAL, "ordering must be 0 or 1");
     r.ordering = ordering;
@@ -123,7 +148,50 @@ int compute_regions(const HostMesh& m, const int8_t* fine, int layers, int order
     for (int v = 0; v < nV; ++v)
         r.vband[v] = std::min({r.cband[m.CoV[3 * v]], r.cband[m.CoV[3 * v + 1]], r.cband[m.CoV[3 * v + 2]]});
 
-    // ---- cells: band, then Hilbert key (or the mesh's own index)
+    // ---- blocks: one region's near bands (F deep..C5) per block, then the far
+    //      coarse cells; a single region is block 0 and C rest block 1
+    r.nreg = nreg;
+    std::vector<int> cblock(nC, 0);
+    if (!rid) {
+        for (int i = 0; i < nC; ++i) cblock[i] = r.cband[i] == B_CREST ? 1 : 0;
+    } else {
+        // walk out of each region's fine cells through the near bands; the
+        // bands up to C2 (which Step 3 reads) must not meet another region's
+        std::vector<int> reg(nC, 0), queue;
+        queue.reserve(nC);
+        for (int i = 0; i < nC; ++i)
+            if (fine[i]) {
+                reg[i] = rid[i];
+                queue.push_back(i);
+            }
+        for (size_t h = 0; h < queue.size(); ++h) {
+            const int i = queue[h];
+            for (int j = 0; j < m.nEoC[i]; ++j) {
+                const int nb = m.CoC[static_cast<size_t>(i) * m.maxE + j];
+                if (r.cband[nb] == B_CREST) continue;
+                if (reg[nb] == 0) {
+                    reg[nb] = reg[i];
+                    queue.push_back(nb);
+                } else if (reg[nb] != reg[i] && r.cband[nb] <= B_C2 && r.cband[i] <= B_C2) {
+                    return set_error(LTS_EINVAL,
+                                     "fine regions %d and %d are too close: their fine, interface and first "
+                                     "two coarse layers touch", reg[i], reg[nb]);
+                }
+            }
+        }
+        for (int i = 0; i < nC; ++i) cblock[i] = r.cband[i] == B_CREST ? nreg : reg[i] - 1;
+    }
+    auto eblock = [&](int e) {
+        const int a = m.CoE[2 * e], b = m.CoE[2 * e + 1];
+        return r.cband[a] <= r.cband[b] ? cblock[a] : cblock[b];
+    };
+    auto vblock = [&](int v) {
+        int best = m.CoV[3 * v];
+        for (int q = 1; q < 3; ++q)
+            if (r.cband[m.CoV[3 * v + q]] < r.cband[best]) best = m.CoV[3 * v + q];
+        return cblock[best];
+    };
+    // ---- cells: block, band, then Hilbert key (or the mesh's own index)
     std::vector<uint64_t> key(nC);
     double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
     for (int i = 0; i < nC; ++i) {
@@ -142,6 +210,7 @@ int compute_regions(const HostMesh& m, const int8_t* fine, int layers, int order
     r.perm_c.resize(nC);
     std::iota(r.perm_c.begin(), r.perm_c.end(), 0);
     std::stable_sort(r.perm_c.begin(), r.perm_c.end(), [&](int a, int b) {
+        if (cblock[a] != cblock[b]) return cblock[a] < cblock[b];
         if (r.cband[a] != r.cband[b]) return r.cband[a] < r.cband[b];
         return key[a] < key[b];
     });
@@ -154,7 +223,10 @@ int compute_regions(const HostMesh& m, const int8_t* fine, int layers, int order
         int a = r.inv_c[m.CoE[2 * e]], b = r.inv_c[m.CoE[2 * e + 1]];
         return std::make_pair(std::min(a, b), std::max(a, b));
     };
+    std::vector<int> eblk(nE);
+    for (int e = 0; e < nE; ++e) eblk[e] = eblock(e);
     std::stable_sort(r.perm_e.begin(), r.perm_e.end(), [&](int a, int b) {
+        if (eblk[a] != eblk[b]) return eblk[a] < eblk[b];
         if (r.eband[a] != r.eband[b]) return r.eband[a] < r.eband[b];
         return ekey(a) < ekey(b);
     });
@@ -167,7 +239,10 @@ int compute_regions(const HostMesh& m, const int8_t* fine, int layers, int order
         int a = r.inv_c[m.CoV[3 * v]], b = r.inv_c[m.CoV[3 * v + 1]], c = r.inv_c[m.CoV[3 * v + 2]];
         return std::min({a, b, c});
     };
+    std::vector<int> vblk(nV);
+    for (int v = 0; v < nV; ++v) vblk[v] = vblock(v);
     std::stable_sort(r.perm_v.begin(), r.perm_v.end(), [&](int a, int b) {
+        if (vblk[a] != vblk[b]) return vblk[a] < vblk[b];
         if (r.vband[a] != r.vband[b]) return r.vband[a] < r.vband[b];
         return vkey(a) < vkey(b);
     });
@@ -182,6 +257,32 @@ int compute_regions(const HostMesh& m, const int8_t* fine, int layers, int order
         r.cb[k + 1] += r.cb[k];
         r.eb[k + 1] += r.eb[k];
         r.vb[k + 1] += r.vb[k];
+    }
+    // ---- band offsets of every block as the planner of that block sees them
+    //      (several regions only; a single region uses cb, eb, vb)
+    r.mcb.clear();
+    r.meb.clear();
+    r.mvb.clear();
+    if (rid) {
+        const int nb = nreg + 1;
+        auto offsets = [&](const std::vector<int8_t>& band, const std::vector<int>& blk, int n,
+                           std::vector<std::vector<int>>& out) {
+            // count[b][k], then prefix in (block, band) order
+            std::vector<std::vector<int>> cnt(nb, std::vector<int>(NBANDS, 0));
+            for (int x = 0; x < n; ++x) cnt[blk[x]][band[x]]++;
+            out.assign(nb, std::vector<int>(NBANDS + 1, 0));
+            int pos = 0;
+            for (int b = 0; b < nb; ++b) {
+                for (int k = 0; k < NBANDS; ++k) {
+                    out[b][k] = pos;
+                    pos += cnt[b][k];
+                }
+                out[b][NBANDS] = pos;
+            }
+        };
+        offsets(r.cband, cblock, nC, r.mcb);
+        offsets(r.eband, eblk, nE, r.meb);
+        offsets(r.vband, vblk, nV, r.mvb);
     }
     // ---- connectivity in band order (host copies, for the planner's byte counts)
     const int W = m.maxE;
@@ -228,6 +329,8 @@ int compute_regions(const HostMesh& m, const int8_t* fine, int layers, int order
     }
     return LTS_OK;
 }
+}  // namespace
+
 
 // Tiles for the fused right-hand-side kernel.  Tile cells are a contiguous
 // band-order range inside one band; the tile owns the edges whose lower

@@ -21,8 +21,17 @@ struct HostMesh {
 struct RegionsHost {
     int M = 1, layers = 1;
     int order = 3;                                 // 2 = LTS2, 3 = LTS3
+    // several disjoint fine regions (nreg > 1): the cells of region r's
+    // bands F deep..C5 form block r-1 (band order inside), the far coarse
+    // cells (C rest) the last block; mb*[k] = band offsets of block k as the
+    // planner sees them (C rest empty for a region, only C rest for the
+    // last block); Mr = each region's M.
+    int nreg = 1;
+    std::vector<int> Mr;
+    std::vector<std::vector<int>> mcb, meb, mvb;   // [nreg + 1][NBANDS + 1]
     int ordering = 0;                              // 0 Hilbert inside a band, 1 mesh index order
     std::vector<int8_t> fine;                      // the fine-cell mask the labels came from
+    std::vector<int8_t> rid;                       // region of each fine cell (several regions)
     std::vector<int8_t> cband, eband, vband;      // original order
     std::vector<int> perm_c, perm_e, perm_v;      // new -> original
     std::vector<int> inv_c, inv_e, inv_v;         // original -> new
@@ -58,6 +67,11 @@ struct CoefTables {
 // Labels, bands and band-ordered connectivity.  ordering 0: Hilbert curve
 // inside each band; 1: the mesh's own index order inside each band.
 int compute_regions(const HostMesh& m, const int8_t* fine, int layers, int ordering, RegionsHost& r);
+// Several fine regions: region_of_cell[i] = r in 1..nreg for the fine cells
+// of region r, 0 elsewhere.  The regions' fine, interface, C1 and C2 cells
+// must not touch (LTS_EINVAL otherwise).
+int compute_regions_multi(const HostMesh& m, const int8_t* region_of_cell, int nreg, int layers, int ordering,
+                          RegionsHost& r);
 template <class T>
 void coefficient_tables(const HostMesh& m, const RegionsHost& r, CoefTables<T>& o);
 double derived_weight(const HostMesh& m, int c, int j, int p);

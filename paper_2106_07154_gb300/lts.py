@@ -155,6 +155,8 @@ def lib():
             L.lts_regions_counts.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
             L.lts_regions_tiling.argtypes = [C.c_void_p, C.c_int32]
             L.lts_regions_ordering.argtypes = [C.c_void_p, C.c_int32]
+            L.lts_regions_set_multi.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32,
+                                                C.c_int32, C.POINTER(C.c_void_p)]
             L.lts_autotune.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                        C.POINTER(lts_params), C.c_int32, C.c_int32,
                                        C.POINTER(lts_params), C.POINTER(lts_tune_report)]
@@ -280,6 +282,15 @@ def lts_regions_set(mesh_h, fine_mask, order: int, M: int, interface_layers: int
     fm = np.ascontiguousarray(fine_mask, dtype=np.int8)
     h = C.c_void_p()
     _check(lib().lts_regions_set(mesh_h, fm.ctypes.data, order, M, interface_layers, C.byref(h)))
+    return h
+
+
+def lts_regions_set_multi(mesh_h, region_of_cell, Ms, order: int = 3, interface_layers: int = 1):
+    rid = np.ascontiguousarray(region_of_cell, dtype=np.int8)
+    Ms = np.ascontiguousarray(Ms, dtype=np.int32)
+    h = C.c_void_p()
+    _check(lib().lts_regions_set_multi(mesh_h, rid.ctypes.data, len(Ms), Ms.ctypes.data, order,
+                                       interface_layers, C.byref(h)))
     return h
 
 
@@ -514,7 +525,10 @@ class Model:
         self.mesh_h = self.reg_h = self.state_h = None
         self.tuned = None
         self.mesh_h = lts_mesh_create(mesh)
-        self.reg_h = lts_regions_set(self.mesh_h, fine_mask, order, M, interface_layers)
+        if np.ndim(M) > 0:   # several fine regions: fine_mask holds region ids 1..len(M)
+            self.reg_h = lts_regions_set_multi(self.mesh_h, fine_mask, list(M), order, interface_layers)
+        else:
+            self.reg_h = lts_regions_set(self.mesh_h, fine_mask, order, M, interface_layers)
         if tile_cells:
             lts_regions_tiling(self.reg_h, tile_cells)
         if ordering != LTS_ORDER_HILBERT:

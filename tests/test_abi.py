@@ -128,3 +128,53 @@ def test_regions_ordering_index_keeps_mesh_order_inside_bands():
     finally:
         lts.lts_regions_destroy(rh)
         lts.lts_mesh_destroy(mh)
+
+
+def _two_disks(mesh, radius):
+    x, y = mesh["xCell"], mesh["yCell"]
+    Lx, Ly = mesh["period_x"], mesh["period_y"]
+    rid = np.zeros(mesh["nCells"], np.int8)
+    for r, (cx, cy) in enumerate([(0.25 * Lx, 0.25 * Ly), (0.75 * Lx, 0.75 * Ly)], start=1):
+        dx = (x - cx) - Lx * np.round((x - cx) / Lx)
+        dy = (y - cy) - Ly * np.round((y - cy) / Ly)
+        rid[dx * dx + dy * dy <= radius ** 2] = r
+    return rid
+
+
+def test_regions_multi_blocks_and_rejection():
+    """Several fine regions (host only): every region's near bands form one
+    contiguous block in the band-ordered arrays, the far coarse cells the
+    last; the band counts equal those of the union; regions whose fine,
+    interface and first coarse layers touch are rejected."""
+    mesh = lts.lts_build_hex_periodic(32, 32, 10e3, 1e-4)
+    rid = _two_disks(mesh, 25e3)
+    mh = lts.lts_mesh_create(mesh)
+    try:
+        r2 = lts.lts_regions_set_multi(mh, rid, [4, 2])
+        r1 = lts.lts_regions_set(mh, (rid > 0).astype(np.int8), 3, 4)
+        c2, _, _ = lts.lts_regions_counts(r2)
+        c1, _, _ = lts.lts_regions_counts(r1)
+        assert np.array_equal(c1, c2)
+        l2, _ = lts.lts_regions_labels(r2, mesh["nCells"], mesh["nEdges"])
+        l1, _ = lts.lts_regions_labels(r1, mesh["nCells"], mesh["nEdges"])
+        assert np.array_equal(l1, l2)
+        pc, _, _ = lts.lts_regions_permutation(r2, mesh["nCells"], mesh["nEdges"], mesh["nVertices"])
+        # new order: region 1's fine cells all come before region 2's
+        pos = np.empty(mesh["nCells"], np.int64)
+        pos[pc] = np.arange(mesh["nCells"])
+        assert pos[rid == 1].max() < pos[rid == 2].min()
+        lts.lts_regions_destroy(r1)
+        lts.lts_regions_destroy(r2)
+        close = _two_disks(mesh, 75e3)      # disks nearly touching
+        try:
+            lts.lts_regions_set_multi(mh, close, [4, 2])
+            assert False, "touching regions should be rejected"
+        except lts.LtsError as e:
+            assert e.code == lts.LTS_EINVAL and "too close" in str(e)
+        try:
+            lts.lts_regions_set_multi(mh, rid, [4, 0])
+            assert False, "M = 0 should be rejected"
+        except lts.LtsError as e:
+            assert e.code == lts.LTS_EINVAL
+    finally:
+        lts.lts_mesh_destroy(mh)
