@@ -168,18 +168,31 @@ def cpu_model():
     return "unknown"
 
 
+def mmax(w):
+    """The largest M of the workload (several fine regions carry one M each)."""
+    return int(max(w.M)) if np.ndim(w.M) else int(w.M)
+
+
+def oracle_lts(o, w, h, u, n, labels=None):
+    """n oracle coarse steps of the workload (several regions: or_lts3_multi)."""
+    if np.ndim(w.M):
+        return o.lts3_multi(h, u, w.fine_mask, list(w.M), w.dt, n, g=w.g)
+    cl, el = labels if labels is not None else o.regions(w.fine_mask)
+    return o.lts3(h, u, cl, el, w.M, w.dt, n, g=w.g)
+
+
 def oracle_sample(w, nsteps_cap=3, budget_s=20.0):
     """Times the FP64 oracle's LTS3 coarse step on the full workload; returns
     (cell-updates/s, steps, seconds, threads, result)."""
     import oracle
 
     o = oracle.Oracle(w.mesh)
-    cl, el = o.regions(w.fine_mask)
+    labels = None if np.ndim(w.M) else o.regions(w.fine_mask)
     h, u = w.h0, w.u0
     steps, t_total = 0, 0.0
     while steps < nsteps_cap and t_total < budget_s:
         t0 = time.perf_counter()
-        h, u = o.lts3(h, u, cl, el, w.M, w.dt, 1, g=w.g)
+        h, u = oracle_lts(o, w, h, u, 1, labels)
         t_total += time.perf_counter() - t0
         steps += 1
     return w.nCells * steps / t_total, steps, t_total, oracle.num_threads(), (h, u)
@@ -199,17 +212,17 @@ def run_reference(args):
     import oracle
 
     o = oracle.Oracle(w.mesh)
-    cl, el = o.regions(w.fine_mask)
+    labels = None if np.ndim(w.M) else o.regions(w.fine_mask)
     h, u = w.h0, w.u0
     # one oracle coarse step takes seconds; warm-up and timed steps are capped
     # so the whole arm ends within a few minutes
     warm = min(args.warmup, 1)
     for _ in range(warm):
-        h, u = o.lts3(h, u, cl, el, w.M, w.dt, 1, g=w.g)
+        h, u = oracle_lts(o, w, h, u, 1, labels)
     t0 = time.perf_counter()
     steps = 0
     while steps < args.steps:
-        h, u = o.lts3(h, u, cl, el, w.M, w.dt, 1, g=w.g)
+        h, u = oracle_lts(o, w, h, u, 1, labels)
         steps += 1
         if time.perf_counter() - t0 > 90.0:
             break
@@ -265,9 +278,14 @@ def run_reference_ensemble(args):
 
 
 def workload_config(w, precision):
-    return {"workload": f"{w.name}: spherical SCVT, {w.nCells} cells, 200 Lloyd iterations, "
-                        f"{int(w.info.get('ratio', 0))}:1 cap, LTS3 M={w.M}",
-            "nCells": w.nCells, "nEdges": int(w.mesh["nEdges"]), "M": w.M,
+    if np.ndim(w.M):
+        caps = " and ".join(f"{int(r)}:1 (M={m})" for r, m in zip(w.info["ratios"], w.M))
+        what = f"two refined caps {caps}, 32 ridges, 5 m spectral noise, LTS3"
+    else:
+        what = f"{int(w.info.get('ratio', 0))}:1 cap, LTS3 M={w.M}"
+    return {"workload": f"{w.name}: spherical SCVT, {w.nCells} cells, 200 Lloyd iterations, {what}",
+            "nCells": w.nCells, "nEdges": int(w.mesh["nEdges"]),
+            "M": list(w.M) if np.ndim(w.M) else w.M,
             "dt_coarse_s": w.dt, "precision": precision,
             "l2": "inputs larger than L2 (each coarse step streams the whole mesh)",
             "parallelism": "replicas"}
@@ -346,6 +364,9 @@ def run_lts(args):
     if L > 1:
         line["config"]["layers"] = L
         line["config"]["workload"] += f", {L} independent layers per cell (cell-layer updates)"
+    if L > 1 or np.ndim(w.M):
+        # per-kernel profiling runs single-region single-layer states only:
+        # the whole step against the roofline instead
         peak, peak_src = hbm_peak()
         bytes_step = float(sum(stats["bytes"]))
         achieved = bytes_step / (ms / args.steps * 1e-3) / 1e9
@@ -353,7 +374,21 @@ def run_lts(args):
                             "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
                             "algorithmic_bytes_per_step": bytes_step,
                             "bytes_per_cell_layer_step": bytes_step / (w.nCells * L)}
-    if not args.no_extras and rank == 0 and L == 1:
+    if np.ndim(w.M) and not args.no_extras and rank == 0:
+        # several fine regions: the oracle baseline and error of one step
+        cells_per_s, n_or, t_or, cores, (rh, ru) = oracle_sample(w, nsteps_cap=1)
+        one = lts.Model(w.mesh, w.fine_mask, w.M, w.h0, w.u0, w.dt, w.g, precision=prec,
+                        compensated=True, stream=stream.cuda_stream)
+        one.step(1)
+        h1, u1, _ = one.read()
+        one.close()
+        line["cpu_baseline"] = {"value": cells_per_s, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"{n_or} coarse step(s) of the full mesh by the FP64 C oracle "
+                                          f"(several regions, {t_or:.1f} s)", "cpu": cpu_model()}
+        line["error_vs_oracle_1step"] = {
+            "h_rel_maxnorm": float(np.max(np.abs(h1 - rh)) / np.max(np.abs(rh))),
+            "u_rel_maxnorm": float(np.max(np.abs(u1 - ru)) / np.max(np.abs(ru)))}
+    if not args.no_extras and rank == 0 and L == 1 and not np.ndim(w.M):
         args._ms = ms
         line.update(extras(args, w, model, stats, stream, h_gpu, u_gpu, diag))
     model.close()
@@ -447,28 +482,30 @@ def extras(args, w, model, stats, stream, h_gpu, u_gpu, diag):
     if not model.tuned:
         base = lts.make_params(w.g, w.dt, prec, lts.LTS_MODE_LTS3, True, True)
         mh = lts.lts_mesh_create(w.mesh)
-        rh = lts.lts_regions_set(mh, w.fine_mask, 3, w.M)
+        rh = (lts.lts_regions_set_multi(mh, w.fine_mask, list(w.M)) if np.ndim(w.M)
+              else lts.lts_regions_set(mh, w.fine_mask, 3, w.M))
         best, rep = lts.lts_autotune(mh, rh, w.h0, w.u0, base, 20, tune_ordering=True)
         lts.lts_regions_destroy(rh)
         lts.lts_mesh_destroy(mh)
         out["autotune"] = dict(lts.params_dict(best), **rep)
     # ---- the GPU's own FP64 global SSP-RK3 at the fine step (same simulated time)
-    ref = lts.Model(w.mesh, w.fine_mask, w.M, w.h0, w.u0, w.dt / w.M, w.g, precision=lts.LTS_FP64,
+    Mx = mmax(w)
+    ref = lts.Model(w.mesh, w.fine_mask, w.M, w.h0, w.u0, w.dt / Mx, w.g, precision=lts.LTS_FP64,
                     mode=lts.LTS_MODE_SSPRK3, stream=stream.cuda_stream)
-    ref.step(w.M)
+    ref.step(Mx)
     torch.cuda.synchronize()
     ncmp = max(2, min(50, args.steps // 20))
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    ref.step(ncmp * w.M)
+    ref.step(ncmp * Mx)
     e1.record(stream)
     torch.cuda.synchronize()
     ref_ms = e0.elapsed_time(e1) / ncmp
     ref.close()
     out["fp64_ssprk3_fine_dt"] = {"ms_per_coarse_interval": ref_ms,
                                   "sim_seconds_per_wall_second": w.dt / (ref_ms * 1e-3),
-                                  "note": f"FP64 SSPRK3 on the whole mesh at dt/M = {w.dt / w.M:.3f} s"}
+                                  "note": f"FP64 SSPRK3 on the whole mesh at dt/M = {w.dt / Mx:.3f} s"}
     # ---- CPU baseline (oracle on the host cores) and the error of this run's
     #      first coarse step against it
     cells_per_s, n_or, t_or, cores, (rh, ru) = oracle_sample(w, nsteps_cap=1)
@@ -513,15 +550,15 @@ def extras(args, w, model, stats, stream, h_gpu, u_gpu, diag):
             hh, uu, _ = m_.read()
         return hh, uu
 
-    hr, ur = run(lts.LTS_FP64, lts.LTS_MODE_SSPRK3, w.dt / (4 * w.M), nco * 4 * w.M)
+    hr, ur = run(lts.LTS_FP64, lts.LTS_MODE_SSPRK3, w.dt / (4 * Mx), nco * 4 * Mx)
     hl, ul = run(lts.LTS_FP32, lts.LTS_MODE_LTS3, w.dt, nco)
-    hs, us = run(lts.LTS_FP64, lts.LTS_MODE_SSPRK3, w.dt / w.M, nco * w.M)
+    hs, us = run(lts.LTS_FP64, lts.LTS_MODE_SSPRK3, w.dt / Mx, nco * Mx)
 
     def err(a, b):
         return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
 
     out["accuracy_10_coarse_steps"] = {
-        "reference": f"FP64 SSPRK3 at dt/(4M) = {w.dt / (4 * w.M):.3f} s over {nco} coarse steps",
+        "reference": f"FP64 SSPRK3 at dt/(4M) = {w.dt / (4 * Mx):.3f} s over {nco} coarse steps",
         "lts3_fp32": {"h": err(hl, hr), "u": err(ul, ur),
                       "sim_seconds_per_wall_second": w.dt * args.steps / (args._ms * 1e-3)},
         "ssprk3_fp64_fine_dt": {"h": err(hs, hr), "u": err(us, ur),

@@ -231,6 +231,82 @@ def ensemble_recipes(n_members: int = 64, seed: int = 7, min_cells: int = 2562,
     return out
 
 
+def ridges(mesh: dict, n_ridges: int = 32, seed: int = 5, h_max: float = 3000.0):
+    """Sum of anisotropic Gaussian ridges on the sphere: seeded centres
+    (uniform on the sphere), orientations, along-ridge lengths 2..15 degrees
+    (across-ridge width a quarter of that) and heights up to h_max."""
+    rng = np.random.default_rng(seed)
+    X = np.stack([mesh["xCell"], mesh["yCell"], mesh["zCell"]], 1)
+    X /= np.linalg.norm(X, axis=1, keepdims=True)
+    b = np.zeros(len(X))
+    for _ in range(n_ridges):
+        c = rng.standard_normal(3)
+        c /= np.linalg.norm(c)
+        # a tangent frame at c, turned by a seeded orientation
+        a = np.cross(c, [0.0, 0.0, 1.0] if abs(c[2]) < 0.9 else [1.0, 0.0, 0.0])
+        a /= np.linalg.norm(a)
+        t = np.cross(c, a)
+        phi = rng.uniform(0, math.pi)
+        e1 = math.cos(phi) * a + math.sin(phi) * t
+        e2 = np.cross(c, e1)
+        length = math.radians(rng.uniform(2.0, 15.0))
+        width = 0.25 * length
+        height = rng.uniform(0.2, 1.0) * h_max
+        s1 = X @ e1
+        s2 = X @ e2
+        near = X @ c > 0.0                      # the hemisphere around the centre
+        b += np.where(near, height * np.exp(-(s1 / length) ** 2 - (s2 / width) ** 2), 0.0)
+    return b
+
+
+def spectral_noise(mesh: dict, rms: float = 5.0, lmax: int = 64, slope: float = -3.0, seed: int = 6,
+                   modes_per_degree: int = 8):
+    """A random field on the sphere with power per degree l proportional to
+    l**slope for l = 1..lmax, scaled to `rms` (area-weighted) with zero
+    mean: for each l, `modes_per_degree` plane waves of wavenumber l/R in
+    seeded directions, restricted to the sphere (a tractable stand-in for a
+    spherical-harmonic synthesis)."""
+    rng = np.random.default_rng(seed)
+    X = np.stack([mesh["xCell"], mesh["yCell"], mesh["zCell"]], 1)
+    X /= np.linalg.norm(X, axis=1, keepdims=True)
+    f = np.zeros(len(X))
+    for l in range(1, lmax + 1):
+        amp = math.sqrt(l ** slope / modes_per_degree)
+        for _ in range(modes_per_degree):
+            k = rng.standard_normal(3)
+            k *= (l + 0.5) / np.linalg.norm(k)
+            f += amp * np.cos(X @ k + rng.uniform(0, 2 * math.pi))
+    A = np.asarray(mesh["areaCell"])
+    f -= np.sum(A * f) / np.sum(A)
+    f *= rms / math.sqrt(np.sum(A * f * f) / np.sum(A))
+    return f
+
+
+def two_caps(n: int = 2621442, seed: int = 5, lloyd_iters: int = 200, cfl: float = 0.5,
+             u0: float = 20.0, cache: bool = True, name: str = "scvt_2621442_2caps") -> Workload:
+    """The large single instance: a spherical SCVT with two separate refined
+    caps (8:1 with M = 8 at the Section-3 mountain position, 4:1 with M = 4
+    on the other side), 32 seeded ridges up to 3000 m, a balanced zonal flow
+    and 5 m of h noise of spectral slope -3.  fine_mask holds the region id
+    (1 or 2) of each fine cell; M is the pair (8, 4)."""
+    cap_r, cap_w = math.radians(15.0), math.radians(5.0)
+    caps = [(1.5 * math.pi, math.pi / 6, cap_r, cap_w, 8.0), (0.5 * math.pi, -math.pi / 4, cap_r, cap_w, 4.0)]
+    mesh = scvt_mesh(n, seed, caps, lloyd_iters, cache=cache)
+    h0, uu, _ = zonal_state(mesh, u0=u0, mountain_height=0.0)
+    b = ridges(mesh, seed=seed)
+    mesh["bottom"] = b
+    h0 = h0 - b + spectral_noise(mesh, seed=seed + 1)
+    lon, lat = _lonlat(mesh["xCell"], mesh["yCell"], mesh["zCell"])
+    rid = np.zeros(mesh["nCells"], np.int8)
+    for r, (lo, la, rad, wid, ratio) in enumerate(caps, start=1):
+        d = _great_circle(lon, lat, lo, la)
+        s = 1.0 / ratio + (1.0 - 1.0 / ratio) * 0.5 * (1.0 + np.tanh((d - rad) / wid))
+        rid[s < 0.9] = r
+    dt, _, _ = _cfl_dt(mesh, h0, uu, rid == 0, cfl)
+    return Workload(name, mesh, h0, uu, rid, (8, 4), dt, 2000,
+                    info={"ratios": (8.0, 4.0), "n_fine": int((rid > 0).sum()), "seed": seed})
+
+
 def workload(name: str, **kw) -> Workload:
     """The named synthetic workloads (sizes and recipes in the design notes)."""
     if name == "hex_1024":          # 32x32 periodic hexagons, M = 2, 100 coarse steps
@@ -247,6 +323,8 @@ def workload(name: str, **kw) -> Workload:
         args = dict(n=2562, ratio=4.0, M=4, nsteps=20, lloyd_iters=60, name=name)
         args.update(kw)
         return sphere_cap(**args)
+    if name == "scvt_2621442_2caps":   # two caps (8:1, M = 8 and 4:1, M = 4), ridges, noise
+        return two_caps(**kw)
     if name == "scvt_10242":        # medium test sphere
         args = dict(n=10242, ratio=4.0, M=4, nsteps=20, lloyd_iters=100, name=name)
         args.update(kw)
