@@ -8,6 +8,8 @@ dependent launch, far coarse phases on a concurrent branch, defaults).
   scvt_655362 (655,362 cells, 8:1 cap, M = 8): 2 coarse steps, FP64 (1e-12)
       and FP32 + compensation (2e-5 / 1e-4); the oracle needs about a second
       per coarse step at this size on the host cores.
+  scvt_2621442_2caps (2,621,442 cells, two fine regions with M = 8 and 4):
+      1 coarse step, FP64 and FP32 + compensation.
 """
 import numpy as np
 import pytest
@@ -73,4 +75,25 @@ def test_cfg3_fp64_2_steps(cfg3):
 def test_cfg3_fp32_2_steps(cfg3):
     w, (rh, ru) = cfg3
     h, u = gpu(w, 2, lts.LTS_FP32)
+    assert rel(h, rh) <= TOL32_H and rel(u, ru) <= TOL32_U, (rel(h, rh), rel(u, ru))
+
+
+@pytest.fixture(scope="module")
+def cfg5():
+    """2,621,442-cell sphere with two refined caps (8:1 with M = 8, 4:1 with
+    M = 4) as two fine regions sharing the coarse step, ridges and noise."""
+    w = W.workload("scvt_2621442_2caps")
+    o = oracle.Oracle(w.mesh)
+    return w, o.lts3_multi(w.h0, w.u0, w.fine_mask, list(w.M), w.dt, 1, g=w.g)
+
+
+def test_cfg5_fp64_1_step(cfg5):
+    w, (rh, ru) = cfg5
+    h, u = gpu(w, 1, lts.LTS_FP64)
+    assert rel(h, rh) <= TOL64 and rel(u, ru) <= TOL64, (rel(h, rh), rel(u, ru))
+
+
+def test_cfg5_fp32_1_step(cfg5):
+    w, (rh, ru) = cfg5
+    h, u = gpu(w, 1, lts.LTS_FP32)
     assert rel(h, rh) <= TOL32_H and rel(u, ru) <= TOL32_U, (rel(h, rh), rel(u, ru))
