@@ -43,6 +43,7 @@ UNIT = "cell-updates/s"
 PEAKS = ROOT / "MEASURED_PEAKS.json"
 HBM_FALLBACK_GBS = 6800.0
 TRAFFIC_SUMMARY = ROOT / "profiles" / "ring_kernel_scvt655362_fp32c.md"
+LAUNCH_SUMMARY = ROOT / "profiles" / "lts3_step_launches_scvt655362_fp32c.md"
 KERNEL_SRC = ROOT / "paper_2106_07154_gb300" / "csrc" / "kernels.cu"
 
 
@@ -153,6 +154,20 @@ def dram_traffic_per_launch():
         if data.get("kernels_cu_sha256_16") != kernel_hash():
             return None
         return float(data["ring_dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+def device_time_shares():
+    """Per-kind shares of device time from the committed ncu launch list, or
+    None when the kernel source changed since the capture."""
+    try:
+        text = LAUNCH_SUMMARY.read_text()
+        m = re.search(r"```json\s*(\{.*?\})\s*```", text, re.S)
+        data = json.loads(m.group(1))
+        if data.get("kernels_cu_sha256_16") != kernel_hash():
+            return None
+        return data["shares"]
     except Exception:
         return None
 
@@ -399,6 +414,24 @@ def run_lts(args):
     return 0
 
 
+def in_graph_estimate(args, bytes_kind, launches_kind, dom, peak):
+    """The dominant kernel inside the production graph, where programmatic
+    dependent launch overlaps consecutive kernels: its share of device time
+    (committed ncu launch list) times the graph's step time, per launch."""
+    shares = device_time_shares()
+    if not shares or args._ms is None:
+        return None
+    from paper_2106_07154_gb300 import lts
+
+    share = shares.get(lts.KIND_NAMES[dom])
+    if not share:
+        return None
+    t_launch = args._ms / args.steps * share / launches_kind[dom]
+    gbs = bytes_kind[dom] / launches_kind[dom] / (t_launch * 1e-3) / 1e9
+    return {"GB_per_s": float(gbs), "frac": float(gbs / peak), "share": share,
+            "method": "graph step time x the kind's ncu share of device time / its launches per step"}
+
+
 def extras(args, w, model, stats, stream, h_gpu, u_gpu, diag):
     import torch
     from paper_2106_07154_gb300 import lts
@@ -473,6 +506,7 @@ def extras(args, w, model, stats, stream, h_gpu, u_gpu, diag):
                      for k in range(lts.LTS_NKINDS) if has[k]},
         "timing": "per-kernel CUDA events: an event-record node before and after every kernel "
                   "node of the coarse-step graph (20 steps after the timed region)",
+        "in_graph_estimate": in_graph_estimate(args, bytes_kind, launches_kind, dom, peak),
         "per_kind_direct_launch_events": {
             lts.KIND_NAMES[k]: {"ms_per_step": float(ms1[k]),
                                 "GB_per_s": float(bytes_kind[k] / (ms1[k] * 1e-3) / 1e9) if ms1[k] > 0 else None}
