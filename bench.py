@@ -22,6 +22,7 @@ build) on the host cores on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import math
@@ -61,6 +62,13 @@ def parse():
     ap.add_argument("--no-pdl", action="store_true", help="no programmatic dependent launch")
     ap.add_argument("--layers", type=int, default=1,
                     help="independent layers per cell (the paper's 100-layer ocean workload)")
+    ap.add_argument("--order", type=int, default=3, choices=[2, 3],
+                    help="3 = LTS3 (default), 2 = LTS2 (Algorithm 2.2's second-order branches)")
+    ap.add_argument("--interface-layers", type=int, default=1,
+                    help="interface thickness in cells (the paper's thick-interface runs)")
+    ap.add_argument("--dt-scale", type=float, default=1.0,
+                    help="multiplies the workload's coarse step (LTS2 is not stable at the "
+                         "LTS3 step on pure gravity waves)")
     ap.add_argument("--autotune", type=int, default=0,
                     help="time the run with the configuration the library's autotuner picks "
                          "(coarse steps per candidate; 0 = library defaults)")
@@ -189,11 +197,36 @@ def mmax(w):
 
 
 def oracle_lts(o, w, h, u, n, labels=None):
-    """n oracle coarse steps of the workload (several regions: or_lts3_multi)."""
+    """n oracle coarse steps of the workload (several regions: or_lts3_multi;
+    order 2: LTS2; thicker interfaces through the labels)."""
     if np.ndim(w.M):
         return o.lts3_multi(h, u, w.fine_mask, list(w.M), w.dt, n, g=w.g)
-    cl, el = labels if labels is not None else o.regions(w.fine_mask)
+    cl, el = labels if labels is not None else oracle_labels(o, w)
+    if w.order == 2:
+        return o.lts2(h, u, cl, el, w.M, w.dt, n, g=w.g)
     return o.lts3(h, u, cl, el, w.M, w.dt, n, g=w.g)
+
+
+def load_workload(args):
+    """The named workload with the command line's scheme order, interface
+    thickness and time-step scale."""
+    from paper_2106_07154_gb300 import workloads as W
+
+    w = W.workload(args.workload)
+    if args.order == 3 and args.interface_layers == 1 and args.dt_scale == 1.0:
+        return w
+    if np.ndim(w.M) and (args.order != 3 or args.interface_layers != 1):
+        raise SystemExit("the workload with several fine regions runs LTS3 with one-cell interfaces")
+    return dataclasses.replace(w, order=args.order, interface_layers=args.interface_layers,
+                               dt=w.dt * args.dt_scale)
+
+
+def is_variant(w):
+    return w.order != 3 or w.interface_layers != 1
+
+
+def oracle_labels(o, w):
+    return None if np.ndim(w.M) else o.regions(w.fine_mask, w.interface_layers)
 
 
 def oracle_sample(w, nsteps_cap=3, budget_s=20.0):
@@ -202,7 +235,7 @@ def oracle_sample(w, nsteps_cap=3, budget_s=20.0):
     import oracle
 
     o = oracle.Oracle(w.mesh)
-    labels = None if np.ndim(w.M) else o.regions(w.fine_mask)
+    labels = oracle_labels(o, w)
     h, u = w.h0, w.u0
     steps, t_total = 0, 0.0
     while steps < nsteps_cap and t_total < budget_s:
@@ -223,11 +256,11 @@ def run_reference(args):
 
     if args.workload == "ensemble64":
         return run_reference_ensemble(args)
-    w = W.workload(args.workload)
+    w = load_workload(args)
     import oracle
 
     o = oracle.Oracle(w.mesh)
-    labels = None if np.ndim(w.M) else o.regions(w.fine_mask)
+    labels = oracle_labels(o, w)
     h, u = w.h0, w.u0
     # one oracle coarse step takes seconds; warm-up and timed steps are capped
     # so the whole arm ends within a few minutes
@@ -244,7 +277,7 @@ def run_reference(args):
     el_s = time.perf_counter() - t0
     value = w.nCells * steps / el_s
     cores = oracle.num_threads()
-    sample = (f"{steps} LTS3 coarse steps (M={w.M}) of the full {w.nCells}-cell mesh by the FP64 "
+    sample = (f"{steps} {scheme(w)} coarse steps (M={w.M}) of the full {w.nCells}-cell mesh by the FP64 "
               f"C oracle (full-mesh right-hand sides), {warm} warm-up; capped at 90 s")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": steps, "warmup": warm, "ms_per_step": 1e3 * el_s / steps,
@@ -292,13 +325,23 @@ def run_reference_ensemble(args):
     return 0
 
 
+def scheme(w):
+    s = f"LTS{w.order}"
+    if w.interface_layers != 1:
+        s += f" with {w.interface_layers}-cell interfaces"
+    return s
+
+
 def workload_config(w, precision):
     if np.ndim(w.M):
         caps = " and ".join(f"{int(r)}:1 (M={m})" for r, m in zip(w.info["ratios"], w.M))
-        what = f"two refined caps {caps}, 32 ridges, 5 m spectral noise, LTS3"
+        what = f"two refined caps {caps}, 32 ridges, 5 m spectral noise, {scheme(w)}"
+    elif "ratio" in w.info:
+        what = f"{int(w.info['ratio'])}:1 cap, {scheme(w)} M={w.M}"
     else:
-        what = f"{int(w.info.get('ratio', 0))}:1 cap, LTS3 M={w.M}"
-    return {"workload": f"{w.name}: spherical SCVT, {w.nCells} cells, 200 Lloyd iterations, {what}",
+        what = f"fine circle, {scheme(w)} M={w.M}"
+    mesh = "spherical SCVT, 200 Lloyd iterations" if w.mesh.get("on_sphere") else "doubly periodic hexagons"
+    return {"workload": f"{w.name}: {mesh}, {w.nCells} cells, {what}",
             "nCells": w.nCells, "nEdges": int(w.mesh["nEdges"]),
             "M": list(w.M) if np.ndim(w.M) else w.M,
             "dt_coarse_s": w.dt, "precision": precision,
@@ -319,12 +362,11 @@ def run_lts(args):
         raise SystemExit("bench.py needs a CUDA GPU for --impl lts")
     torch.cuda.set_device(local)
     from paper_2106_07154_gb300 import lts
-    from paper_2106_07154_gb300 import workloads as W
 
     # rank 0 builds (and caches) the mesh first, the others load it
     if world > 1 and rank != 0:
         torch.distributed.barrier()
-    w = W.workload(args.workload)
+    w = load_workload(args)
     if world > 1 and rank == 0:
         torch.distributed.barrier()
     prec = lts.LTS_FP32 if args.precision == "fp32" else lts.LTS_FP64
@@ -338,7 +380,8 @@ def run_lts(args):
         u0 = np.tile(w.u0, (L, 1)) * (1.0 + 0.01 * np.arange(L))[:, None]
     model = lts.Model(w.mesh, w.fine_mask, w.M, h0, u0, w.dt, w.g, precision=prec,
                       compensated=True, use_graph=not args.no_graph, stream=stream.cuda_stream,
-                      pdl=not args.no_pdl, autotune=tune, tune_ordering=bool(tune), layers=L)
+                      pdl=not args.no_pdl, autotune=tune, tune_ordering=bool(tune), layers=L,
+                      order=w.order, interface_layers=w.interface_layers)
     stats = model.stats()
     model.step(args.warmup)
     torch.cuda.synchronize()
@@ -379,8 +422,8 @@ def run_lts(args):
     if L > 1:
         line["config"]["layers"] = L
         line["config"]["workload"] += f", {L} independent layers per cell (cell-layer updates)"
-    if L > 1 or np.ndim(w.M):
-        # per-kernel profiling runs single-region single-layer states only:
+    if L > 1 or np.ndim(w.M) or is_variant(w):
+        # per-kernel profiling runs single-region single-layer LTS3 states only:
         # the whole step against the roofline instead
         peak, peak_src = hbm_peak()
         bytes_step = float(sum(stats["bytes"]))
@@ -389,21 +432,23 @@ def run_lts(args):
                             "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
                             "algorithmic_bytes_per_step": bytes_step,
                             "bytes_per_cell_layer_step": bytes_step / (w.nCells * L)}
-    if np.ndim(w.M) and not args.no_extras and rank == 0:
-        # several fine regions: the oracle baseline and error of one step
+    if (np.ndim(w.M) or is_variant(w)) and L == 1 and not args.no_extras and rank == 0:
+        # several fine regions, LTS2, thick interfaces: the oracle baseline
+        # and the error of one step
         cells_per_s, n_or, t_or, cores, (rh, ru) = oracle_sample(w, nsteps_cap=1)
         one = lts.Model(w.mesh, w.fine_mask, w.M, w.h0, w.u0, w.dt, w.g, precision=prec,
-                        compensated=True, stream=stream.cuda_stream)
+                        compensated=True, stream=stream.cuda_stream, order=w.order,
+                        interface_layers=w.interface_layers)
         one.step(1)
         h1, u1, _ = one.read()
         one.close()
         line["cpu_baseline"] = {"value": cells_per_s, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": f"{n_or} coarse step(s) of the full mesh by the FP64 C oracle "
-                                          f"(several regions, {t_or:.1f} s)", "cpu": cpu_model()}
+                                          f"({scheme(w)}, {t_or:.1f} s)", "cpu": cpu_model()}
         line["error_vs_oracle_1step"] = {
             "h_rel_maxnorm": float(np.max(np.abs(h1 - rh)) / np.max(np.abs(rh))),
             "u_rel_maxnorm": float(np.max(np.abs(u1 - ru)) / np.max(np.abs(ru)))}
-    if not args.no_extras and rank == 0 and L == 1 and not np.ndim(w.M):
+    if not args.no_extras and rank == 0 and L == 1 and not np.ndim(w.M) and not is_variant(w):
         args._ms = ms
         line.update(extras(args, w, model, stats, stream, h_gpu, u_gpu, diag))
     model.close()

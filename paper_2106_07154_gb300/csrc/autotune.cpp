@@ -121,10 +121,12 @@ extern "C" int lts_autotune(lts_mesh m, lts_regions r, const double* h0, const d
     for (const Candidate& c : cands)
         if (c.block == 256 && c.path == 0 && c.pdl == 1 && c.no_l2 == 0 && c.serial == LTS_COARSE_STEP4)
             default_ms = c.ms;
-    // the FP32 ring-pass occupancy variants with the winning configuration
+    // the FP32 ring-pass occupancy variants with the winning configuration;
+    // layered and multi-region states launch other kernels, so they have none
     Candidate occ_best = *win;
     std::vector<Candidate> occ_tried;
-    if (base->precision == LTS_FP32 && win->path == 0) {
+    const bool multi = r->r.nreg > 1 && base->mode == LTS_MODE_LTS;
+    if (base->precision == LTS_FP32 && win->path == 0 && base->layers <= 1 && !multi) {
         for (int occ : {6, 8}) {
             Candidate c = *win;
             c.occ = occ;

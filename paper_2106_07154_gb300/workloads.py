@@ -93,6 +93,8 @@ class Workload:
     nsteps: int
     g: float = G
     info: dict = field(default_factory=dict)
+    order: int = 3             # 3 = LTS3, 2 = LTS2
+    interface_layers: int = 1  # interface thickness in cells (Eqs. 3-5 with thicker I1, I2)
 
     @property
     def nCells(self) -> int:
