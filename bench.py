@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--dt-scale", type=float, default=1.0,
                     help="multiplies the workload's coarse step (LTS2 is not stable at the "
                          "LTS3 step on pure gravity waves)")
+    ap.add_argument("--elems-per-thread", type=int, default=0, choices=[0, 1, 2],
+                    help="elements per thread of the vertex and edge launches (0 = library default)")
     ap.add_argument("--autotune", type=int, default=0,
                     help="time the run with the configuration the library's autotuner picks "
                          "(coarse steps per candidate; 0 = library defaults)")
@@ -381,7 +383,8 @@ def run_lts(args):
     model = lts.Model(w.mesh, w.fine_mask, w.M, h0, u0, w.dt, w.g, precision=prec,
                       compensated=True, use_graph=not args.no_graph, stream=stream.cuda_stream,
                       pdl=not args.no_pdl, autotune=tune, tune_ordering=bool(tune), layers=L,
-                      order=w.order, interface_layers=w.interface_layers)
+                      order=w.order, interface_layers=w.interface_layers,
+                      elems_per_thread=args.elems_per_thread)
     stats = model.stats()
     model.step(args.warmup)
     torch.cuda.synchronize()
@@ -506,7 +509,8 @@ def extras(args, w, model, stats, stream, h_gpu, u_gpu, diag):
     #      node before and after every kernel node, on the state's stream
     tuned = model.tuned or {}
     knobs = {k: tuned[k] for k in ("block_size", "kernel_path", "l2_hints", "coarse_schedule",
-                                   "ring_occupancy") if k in tuned}
+                                   "ring_occupancy", "elems_per_thread") if k in tuned}
+    knobs.setdefault("elems_per_thread", args.elems_per_thread)
     if "ordering" in tuned:
         knobs["ordering"] = tuned["ordering"]
     prof = lts.Model(w.mesh, w.fine_mask, w.M, w.h0, w.u0, w.dt, w.g, precision=prec,

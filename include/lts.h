@@ -252,6 +252,10 @@ typedef struct lts_params {
                                coarse bands (C5+ for Step 1, C3+ for Steps 2 and 4)
                                form that branch; LTS_COARSE_SERIAL: step order on one
                                stream                                                  */
+    int32_t elems_per_thread;/* vertex and edge launches of single-layer states on the
+                               three-launch path: 1 or 2 elements per thread (2: half
+                               the blocks, both elements' loads in flight together);
+                               0 = library default.  Results are identical.            */
 } lts_params;
 
 /* Allocates the device state (band order) and uploads (h0, u0), given in the
@@ -275,7 +279,8 @@ int lts_step(lts_state s, int32_t n_coarse);
  * LTS_COARSE_STEP4, _FAR or _SERIAL).  Each is timed over `steps` coarse
  * steps after 3 warm-up steps; the three fastest are timed twice more and
  * the best of three wins.  With the winner, FP32 states also try the ring
- * occupancy variants 6 and 8 (best of two timings each).  With
+ * occupancy variants 6 and 8, and single-region single-layer states the
+ * other elems_per_thread (best of two timings each).  With
  * flags & LTS_TUNE_ORDERING and no state using r, the other cell ordering
  * (lts_regions_ordering) is tried with the winner and r keeps the faster.
  * No configuration changes a result bit; the tuner only chooses speed.  The
@@ -285,7 +290,8 @@ int lts_step(lts_state s, int32_t n_coarse);
  * LTS_ECUDA. */
 #define LTS_TUNE_ORDERING 1
 typedef struct lts_tune_entry {
-    int32_t block_size, kernel_path, pdl, l2_hints, coarse_schedule, ordering, ring_occupancy;
+    int32_t block_size, kernel_path, pdl, l2_hints, coarse_schedule, ordering, ring_occupancy,
+            elems_per_thread;
     double ms;              /* ms per coarse step (best of its timings; inf = not buildable) */
 } lts_tune_entry;
 typedef struct lts_tune_report {

@@ -25,6 +25,7 @@ struct Candidate {
     int block, path, pdl, no_l2, serial;   // serial: the coarse schedule
     double ms = INFINITY;
     int occ = 0;                           // ring occupancy variant
+    int ept = 0;                           // elements per thread (0: the base's)
 };
 
 lts_params apply(const lts_params& base, const Candidate& c) {
@@ -35,6 +36,7 @@ lts_params apply(const lts_params& base, const Candidate& c) {
     p.no_l2_hints = c.no_l2;
     p.coarse_schedule = c.serial;
     p.ring_occupancy = c.occ;
+    if (c.ept) p.elems_per_thread = c.ept;
     p.use_graph = 1;
     p.profile = 0;
     p.stream = nullptr;
@@ -141,6 +143,23 @@ extern "C" int lts_autotune(lts_mesh m, lts_regions r, const double* h0, const d
         }
     }
     win = &occ_best;
+    // the other number of elements per thread of the vertex and edge launches
+    const int ept0 = base->elems_per_thread ? base->elems_per_thread : LTS_DEFAULT_EPT;
+    Candidate ept_best = *win;
+    std::vector<Candidate> ept_tried;
+    if (win->path == 0 && base->layers <= 1 && !multi) {
+        Candidate c = *win;
+        c.ept = 3 - ept0;
+        for (int rep_k = 0; rep_k < 2; ++rep_k) {
+            double ms = INFINITY;
+            int rc = time_config(m, r, h0, u0, apply(*base, c), steps, &ms);
+            if (rc != LTS_OK) return rc;
+            c.ms = rep_k == 0 ? ms : std::min(c.ms, ms);
+        }
+        ept_tried.push_back(c);
+        if (c.ms < ept_best.ms) ept_best = c;
+    }
+    win = &ept_best;
     *best = apply(*base, *win);
     best->stream = base->stream;
     double best_ms = win->ms;
@@ -166,7 +185,8 @@ extern "C" int lts_autotune(lts_mesh m, lts_regions r, const double* h0, const d
         }
     }
     if (rep) {
-        rep->candidates = static_cast<int32_t>(cands.size() + occ_tried.size()) + (tried_orderings - 1);
+        rep->candidates = static_cast<int32_t>(cands.size() + occ_tried.size() + ept_tried.size()) +
+                          (tried_orderings - 1);
         rep->best_ms = best_ms;
         rep->default_ms = default_ms;
         rep->ordering = ordering;
@@ -174,13 +194,17 @@ extern "C" int lts_autotune(lts_mesh m, lts_regions r, const double* h0, const d
         int n = 0;
         for (const Candidate& c : cands) {
             if (n >= 32) break;
-            rep->entry[n++] = {c.block, c.path, c.pdl, 1 - c.no_l2, c.serial, ordering0, 0, c.ms};
+            rep->entry[n++] = {c.block, c.path, c.pdl, 1 - c.no_l2, c.serial, ordering0, 0, ept0, c.ms};
         }
         for (const Candidate& c : occ_tried)
-            if (n < 32) rep->entry[n++] = {c.block, c.path, c.pdl, 1 - c.no_l2, c.serial, ordering0, c.occ, c.ms};
+            if (n < 32)
+                rep->entry[n++] = {c.block, c.path, c.pdl, 1 - c.no_l2, c.serial, ordering0, c.occ, ept0, c.ms};
+        for (const Candidate& c : ept_tried)
+            if (n < 32)
+                rep->entry[n++] = {c.block, c.path, c.pdl, 1 - c.no_l2, c.serial, ordering0, c.occ, c.ept, c.ms};
         if (tried_orderings == 2 && n < 32)
             rep->entry[n++] = {win->block, win->path, win->pdl, 1 - win->no_l2, win->serial, 1 - ordering0,
-                               win->occ, other_ms};
+                               win->occ, win->ept ? win->ept : ept0, other_ms};
     }
     return LTS_OK;
 }

@@ -239,19 +239,37 @@ __device__ __forceinline__ void epi_load(const Ld& ld, const DevSeg<T>& s, int m
 
 // q_v = (zeta_v + f_v) / h_v with zeta_v = sum t_{e,v} (d_e/A_v) u_e and
 // h_v = sum (A_{i,v}/A_v) h_i.
+// The vertex's mesh-table operands (loaded before the dependency wait).
+template <class T>
+struct VertStat {
+    int e0, e1, e2, c0, c1, c2;
+    T d0, d1, d2, k0, k1, k2, f;
+};
+
+template <class T>
+__device__ __forceinline__ void vertex_stat(const Tables<T>& t, const Ld& ld, int v, VertStat<T>& s) {
+    s.e0 = ld.stat(t.ve0 + v), s.e1 = ld.stat(t.ve1 + v), s.e2 = ld.stat(t.ve2 + v);
+    s.c0 = ld.stat(t.vc0 + v), s.c1 = ld.stat(t.vc1 + v), s.c2 = ld.stat(t.vc2 + v);
+    s.d0 = ld.stat(t.vd0 + v), s.d1 = ld.stat(t.vd1 + v), s.d2 = ld.stat(t.vd2 + v);
+    s.k0 = ld.stat(t.vk0 + v), s.k1 = ld.stat(t.vk1 + v), s.k2 = ld.stat(t.vk2 + v);
+    s.f = ld.stat(t.f + v);
+}
+
+// Gathers u and h (after the wait) and returns q_v.
+template <class T, bool LY>
+__device__ __forceinline__ T vertex_q(const DevArgs<T>& a, const Ld& ld, const VertStat<T>& s, const Lay<LY>& y) {
+    T zeta = s.d0 * ld(a.in_u + y(s.e0)) + s.d1 * ld(a.in_u + y(s.e1)) + s.d2 * ld(a.in_u + y(s.e2));
+    T hv = s.k0 * ld(a.in_h + y(s.c0)) + s.k1 * ld(a.in_h + y(s.c1)) + s.k2 * ld(a.in_h + y(s.c2));
+    return (zeta + s.f) / hv;
+}
+
 template <class T, bool LY>
 __device__ __forceinline__ void vertex_pv(const DevArgs<T>& a, int v, const Lay<LY>& y) {
-    const Tables<T>& t = a.t;
     const Ld ld(a.l2);
-    const int e0 = ld.stat(t.ve0 + v), e1 = ld.stat(t.ve1 + v), e2 = ld.stat(t.ve2 + v);
-    const int c0 = ld.stat(t.vc0 + v), c1 = ld.stat(t.vc1 + v), c2 = ld.stat(t.vc2 + v);
-    const T d0 = ld.stat(t.vd0 + v), d1 = ld.stat(t.vd1 + v), d2 = ld.stat(t.vd2 + v);
-    const T k0 = ld.stat(t.vk0 + v), k1 = ld.stat(t.vk1 + v), k2 = ld.stat(t.vk2 + v);
-    const T f = ld.stat(t.f + v);
+    VertStat<T> s;
+    vertex_stat(a.t, ld, v, s);
     griddep_wait();
-    T zeta = d0 * ld(a.in_u + y(e0)) + d1 * ld(a.in_u + y(e1)) + d2 * ld(a.in_u + y(e2));
-    T hv = k0 * ld(a.in_h + y(c0)) + k1 * ld(a.in_h + y(c1)) + k2 * ld(a.in_h + y(c2));
-    a.q[y(v)] = (zeta + f) / hv;
+    a.q[y(v)] = vertex_q<T, LY>(a, ld, s, y);
 }
 
 // --------------------------------------------------------------- kind 1: ring
@@ -372,26 +390,45 @@ __device__ __forceinline__ T ring_pass(const DevArgs<T>& a, int c, const Lay<LY>
 // --------------------------------------------------------------- kind 2: edge
 // U_e = -(1/d_e) [ (C_{c1,p1} - C_{c0,p0})/2 + g((h1 - h0) + (b1 - b0)) + K1 - K0 ]
 // (-n_{e,c0} = -1, -n_{e,c1} = +1 carry the signs of the two ring shares).
+// The edge's mesh-table operands (loaded before the dependency wait).
+template <class T>
+struct EdgeStat {
+    int c0, c1, p0, p1;
+    T rdc, db;
+};
+
+template <class T>
+__device__ __forceinline__ void edge_stat(const Tables<T>& t, const Ld& ld, int e, EdgeStat<T>& s) {
+    s.c0 = ld.stat(t.ec0 + e), s.c1 = ld.stat(t.ec1 + e);
+    const uint32_t pp = ld.stat(t.ep + e);
+    s.p0 = pp & 0xff, s.p1 = (pp >> 8) & 0xff;
+    s.rdc = ld.stat(t.rdc + e);
+    s.db = ld.stat(t.b + s.c1) - ld.stat(t.b + s.c0);
+}
+
+// Gathers the two cells' ring results and thicknesses (after the wait) and
+// returns U_e.
+template <class T, bool COMP, bool LY>
+__device__ __forceinline__ T edge_value(const DevArgs<T>& a, const Ld& ld, const EdgeStat<T>& s, const Lay<LY>& y) {
+    const int N = a.t.nC;
+    const T C0 = ld(a.ring_c + y(s.p0 * N + s.c0)), C1 = ld(a.ring_c + y(s.p1 * N + s.c1));
+    // h1 - h0 is exact for nearby thicknesses (Sterbenz); with COMP the
+    // compensation words restore the digits the FP32 thickness dropped.
+    T dh = ld(a.in_h + y(s.c1)) - ld(a.in_h + y(s.c0));
+    if (COMP) dh += ld(a.in_hl + y(s.c1)) - ld(a.in_hl + y(s.c0));
+    const T grad = a.g * (dh + s.db) + (ld(a.ring_k + y(s.c1)) - ld(a.ring_k + y(s.c0)));
+    return -s.rdc * (T(0.5) * (C1 - C0) + grad);
+}
+
 template <class T, bool COMP, bool LY>
 __device__ __forceinline__ T edge_tendency(const DevArgs<T>& a, int e, const DevSeg<T>& seg, int epi,
                                            EpiOps<T>& eo, const Lay<LY>& y) {
-    const Tables<T>& t = a.t;
     const Ld ld(a.l2);
-    const int N = t.nC;
-    const int c0 = ld.stat(t.ec0 + e), c1 = ld.stat(t.ec1 + e);
-    const uint32_t pp = ld.stat(t.ep + e);
-    const int p0 = pp & 0xff, p1 = (pp >> 8) & 0xff;
-    const T rdc = ld.stat(t.rdc + e);
-    const T db = ld.stat(t.b + c1) - ld.stat(t.b + c0);
+    EdgeStat<T> s;
+    edge_stat(a.t, ld, e, s);
     griddep_wait();
     epi_load<T, COMP, LY>(ld, seg, epi, e, a.in_u, eo, y);
-    const T C0 = ld(a.ring_c + y(p0 * N + c0)), C1 = ld(a.ring_c + y(p1 * N + c1));
-    // h1 - h0 is exact for nearby thicknesses (Sterbenz); with COMP the
-    // compensation words restore the digits the FP32 thickness dropped.
-    T dh = ld(a.in_h + y(c1)) - ld(a.in_h + y(c0));
-    if (COMP) dh += ld(a.in_hl + y(c1)) - ld(a.in_hl + y(c0));
-    const T grad = a.g * (dh + db) + (ld(a.ring_k + y(c1)) - ld(a.ring_k + y(c0)));
-    return -rdc * (T(0.5) * (C1 - C0) + grad);
+    return edge_value<T, COMP, LY>(a, ld, s, y);
 }
 
 template <class T, bool COMP, bool LY>
@@ -737,6 +774,57 @@ __global__ void __launch_bounds__(256) kernel_phase(const __grid_constant__ DevA
     phase_block<T, COMP, MAXR, KIND, LY>(a, a.seg[sidx], blockIdx.x);
 }
 
+// Two elements per thread (vertex and edge kinds, single-layer states):
+// thread t of block b of a segment handles elements 2 b blockDim + t and
+// that + blockDim, with the table loads of both before the dependency wait
+// and the gathers of both in flight before either value is formed.  Half the
+// blocks, so a fine-region launch fits in one wave; each element's
+// arithmetic is the one-element code's, so results are bit-identical.
+template <class T, bool COMP, int KIND>
+__device__ __forceinline__ void phase_block2(const DevArgs<T>& a, const DevSeg<T>& s, int vblk) {
+    const int bd = static_cast<int>(blockDim.x);
+    const int i0 = s.begin + (vblk - s.block0) * 2 * bd + static_cast<int>(threadIdx.x);
+    if (i0 >= s.end) return;
+    const bool two = i0 + bd < s.end;
+    const int i1 = two ? i0 + bd : i0;   // a lone element repeats its loads and stores once
+    const Lay<false> y;
+    const Ld ld(a.l2);
+    if (KIND == 0 && s.type == SEG_VERT) {
+        VertStat<T> s0, s1;
+        vertex_stat(a.t, ld, i0, s0);
+        vertex_stat(a.t, ld, i1, s1);
+        griddep_wait();
+        const T q0 = vertex_q<T, false>(a, ld, s0, y);
+        const T q1 = vertex_q<T, false>(a, ld, s1, y);
+        a.q[i0] = q0;
+        if (two) a.q[i1] = q1;
+    } else if (KIND == 2 && (s.type == SEG_EDGE_UPD || s.type == SEG_EDGE_ACC)) {
+        const int epi = s.type == SEG_EDGE_ACC ? EPI_ACC : EPI_UPD;
+        EdgeStat<T> s0, s1;
+        edge_stat(a.t, ld, i0, s0);
+        edge_stat(a.t, ld, i1, s1);
+        griddep_wait();
+        EpiOps<T> o0, o1;
+        epi_load<T, COMP, false>(ld, s, epi, i0, a.in_u, o0, y);
+        epi_load<T, COMP, false>(ld, s, epi, i1, a.in_u, o1, y);
+        const T U0 = edge_value<T, COMP, false>(a, ld, s0, y);
+        const T U1 = edge_value<T, COMP, false>(a, ld, s1, y);
+        epilogue<T, COMP, false, false>(a, s, epi, i0, U0, o0, y);
+        if (two) epilogue<T, COMP, false, false>(a, s, epi, i1, U1, o1, y);
+    } else {
+        griddep_wait();
+        pointwise<T, COMP, false>(s, i0, y);
+        if (two) pointwise<T, COMP, false>(s, i1, y);
+    }
+}
+
+template <class T, bool COMP, int KIND>
+__global__ void __launch_bounds__(256) kernel_phase2(const __grid_constant__ DevArgs<T> a) {
+    griddep_launch_dependents();
+    const int sidx = find_seg(a, blockIdx.x);
+    phase_block2<T, COMP, KIND>(a, a.seg[sidx], blockIdx.x);
+}
+
 // The FP32 ring pass compiled for MINB resident 256-thread blocks per SM
 // (fewer registers, possibly spills): a fine-region launch then leaves block
 // slots free, where the next launch's blocks prefetch their tables.
@@ -832,16 +920,17 @@ void fill_args(DevArgs<T>& a, const LaunchDesc& d, const void* tables, int smem,
 
 template <class T, bool COMP, int MAXR>
 cudaError_t launch_t(const LaunchDesc& d, const void* tables, int block, bool pdl, int smem, int* flag,
-                     cudaStream_t st, int layers, int ring_occ) {
+                     cudaStream_t st, int layers, int ring_occ, int ept) {
     DevArgs<T> a;
     fill_args(a, d, tables, smem, flag);
     a.L = layers;
+    const bool two = ept == 2 && layers == 1 && (d.kind == 0 || d.kind == 2);
     int blocks = 0, ns = 0;
     for (int k = 0; k < d.nseg; ++k) {
         const SegDesc& s = d.seg[k];
         if (s.end <= s.begin) continue;
         a.seg[ns++] = to_dev<T>(s, blocks);
-        blocks += seg_blocks(s, block, layers);
+        blocks += seg_blocks(s, two ? 2 * block : block, layers);
     }
     a.nseg = ns;
     for (int k = ns; k < MAXSEG; ++k) {
@@ -864,6 +953,9 @@ cudaError_t launch_t(const LaunchDesc& d, const void* tables, int block, bool pd
             default: return launch_kernel(kernel_phase<T, COMP, MAXR, 2, true>, blocks, block, pdl, st, a);
         }
     }
+    if (two)
+        return d.kind == 0 ? launch_kernel(kernel_phase2<T, COMP, 0>, blocks, block, pdl, st, a)
+                           : launch_kernel(kernel_phase2<T, COMP, 2>, blocks, block, pdl, st, a);
     if constexpr (sizeof(T) == 4 && MAXR == 8) {
         if (d.kind == 1 && ring_occ == 6) return launch_kernel(kernel_ring_occ<COMP, 6>, blocks, block, pdl, st, a);
         if (d.kind == 1 && ring_occ == 8) return launch_kernel(kernel_ring_occ<COMP, 8>, blocks, block, pdl, st, a);
@@ -994,8 +1086,8 @@ cudaError_t launch_any(const LaunchDesc& d, const void* tables, const KernelConf
                        cudaStream_t s) {
     const int L = kc.layers > 1 ? kc.layers : 1;
     if (kc.maxdeg <= 8)
-        return launch_t<T, COMP, 8>(d, tables, kc.block, kc.pdl, kc.tile_smem, flag, s, L, kc.ring_occ);
-    return launch_t<T, COMP, MAX_DEGREE>(d, tables, kc.block, kc.pdl, kc.tile_smem, flag, s, L, 0);
+        return launch_t<T, COMP, 8>(d, tables, kc.block, kc.pdl, kc.tile_smem, flag, s, L, kc.ring_occ, kc.ept);
+    return launch_t<T, COMP, MAX_DEGREE>(d, tables, kc.block, kc.pdl, kc.tile_smem, flag, s, L, 0, kc.ept);
 }
 
 }  // namespace

@@ -1356,6 +1356,9 @@ int lts_state_create(lts_mesh mesh, lts_regions reg, const double* h0, const dou
     if (p->ring_occupancy != 0 && p->ring_occupancy != 6 && p->ring_occupancy != 8)
         return set_error(LTS_EINVAL, "ring_occupancy must be 0, 6 or 8");
     S->kc.ring_occ = p->ring_occupancy;
+    if (p->elems_per_thread < 0 || p->elems_per_thread > 2)
+        return set_error(LTS_EINVAL, "elems_per_thread must be 0, 1 or 2");
+    S->kc.ept = p->elems_per_thread == 0 ? LTS_DEFAULT_EPT : p->elems_per_thread;
     S->tables = which ? static_cast<const void*>(&reg->t64) : static_cast<const void*>(&reg->t32);
     if (p->stream) {
         S->stream = static_cast<cudaStream_t>(p->stream);

@@ -133,6 +133,10 @@ struct LaunchDesc {
 // 3 * stage + kind.
 constexpr int KEY_STEP1 = 0, KEY_STEP2 = 3, KEY_SIDE = 10, KEY_STEP3 = 100, KEY_TAIL = 1000000;
 
+// Elements per thread of the vertex and edge launches when the caller
+// leaves the choice to the library.
+constexpr int LTS_DEFAULT_EPT = 1;
+
 struct KernelConfig {
     int precision;   // 0 FP32, 1 FP64
     bool comp;       // FP32 compensated
@@ -143,6 +147,7 @@ struct KernelConfig {
     bool pdl;        // programmatic dependent launch
     int layers = 1;  // layers per element (multi-layer states)
     int ring_occ = 0;  // FP32 ring pass built for 6 or 8 resident blocks per SM (0: default)
+    int ept = 1;       // elements per thread of the vertex and edge kinds (1 or 2)
 };
 
 // kernels.cu

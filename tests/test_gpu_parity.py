@@ -212,12 +212,37 @@ def test_options_do_not_change_results(sphw):
     a = run_gpu(sphw, 6, lts.LTS_FP32)
     for kw in ({"ordering": lts.LTS_ORDER_INDEX}, {"l2_hints": False},
                {"coarse_schedule": lts.LTS_COARSE_FAR}, {"coarse_schedule": lts.LTS_COARSE_SERIAL},
-               {"ring_occupancy": 6}, {"ring_occupancy": 8}):
+               {"ring_occupancy": 6}, {"ring_occupancy": 8}, {"elems_per_thread": 1},
+               {"elems_per_thread": 2}, {"elems_per_thread": 2, "block_size": 128}):
         with lts.Model(sphw.mesh, sphw.fine_mask, sphw.M, sphw.h0, sphw.u0, sphw.dt,
                        precision=lts.LTS_FP32, **kw) as m:
             m.step(6)
             h, u, _ = m.read()
         assert np.array_equal(h, a[0]) and np.array_equal(u, a[1]), kw
+
+
+@pytest.mark.parametrize("precision", [lts.LTS_FP64, lts.LTS_FP32])
+@pytest.mark.parametrize("mode,order", [(lts.LTS_MODE_LTS, 3), (lts.LTS_MODE_LTS, 2),
+                                        (lts.LTS_MODE_SSPRK3, 3)])
+def test_two_elements_per_thread_bitwise(sphw, precision, mode, order):
+    """Vertex and edge launches with two elements per thread (every segment
+    size, so lone last elements too) equal the one-element launches bit for
+    bit, with the graph and with direct launches."""
+    dt = sphw.dt if mode == lts.LTS_MODE_LTS and order == 3 else sphw.dt / (2 * sphw.M)
+    out = []
+    for ept, graph in ((1, True), (2, True), (2, False)):
+        with lts.Model(sphw.mesh, sphw.fine_mask, sphw.M, sphw.h0, sphw.u0, dt, precision=precision,
+                       mode=mode, order=order, elems_per_thread=ept, use_graph=graph) as m:
+            m.step(5)
+            out.append(m.read()[:2])
+    for h, u in out[1:]:
+        assert np.array_equal(h, out[0][0]) and np.array_equal(u, out[0][1])
+
+
+def test_elems_per_thread_is_checked(sphw):
+    with pytest.raises(lts.LtsError) as ei:
+        lts.Model(sphw.mesh, sphw.fine_mask, sphw.M, sphw.h0, sphw.u0, sphw.dt, elems_per_thread=3)
+    assert ei.value.code == lts.LTS_EINVAL
 
 
 def test_autotune_picks_a_valid_config(sphw):
