@@ -1031,8 +1031,19 @@ __global__ void __launch_bounds__(DIAG_THREADS) diag_kernel(const Tables<T> t, c
          x += static_cast<long long>(gridDim.x) * blockDim.x) {
         const int c = static_cast<int>(x / L), l = static_cast<int>(x - static_cast<long long>(c) * L);
         double h = static_cast<double>(hh[x]) + (COMP ? static_cast<double>(hl[x]) : 0.0);
+        const int n = t.cn[c];
         double K = 0.0;
-        for (int j = 0; j < t.cn[c]; ++j) {
+        // the first 8 slots unrolled, so their index loads and gathers are in
+        // flight together; higher degrees continue in order
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (j < n) {
+                const long long e = static_cast<long long>(t.se[j * N + c]) * L + l;
+                double u = static_cast<double>(uh[e]) + (COMP ? static_cast<double>(ul[e]) : 0.0);
+                K += t.sK64[j * N + c] * u * u;
+            }
+        }
+        for (int j = 8; j < n; ++j) {
             const long long e = static_cast<long long>(t.se[j * N + c]) * L + l;
             double u = static_cast<double>(uh[e]) + (COMP ? static_cast<double>(ul[e]) : 0.0);
             K += t.sK64[j * N + c] * u * u;

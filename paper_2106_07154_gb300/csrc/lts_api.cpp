@@ -982,7 +982,8 @@ int state_alloc(lts_state_s* S) {
     S->flag = static_cast<int*>(S->arena.alloc(sizeof(int), err));
     S->stage_c = static_cast<double*>(S->arena.alloc(sizeof(double) * m.nC * Ly, err));
     S->stage_e = static_cast<double*>(S->arena.alloc(sizeof(double) * m.nE * Ly, err));
-    S->diag_blocks = std::max(1, std::min(1024, (m.nC + 255) / 256));
+    // one (cell, layer) per thread up to 8192 blocks, then grid-stride
+    S->diag_blocks = static_cast<int>(std::max<size_t>(1, std::min<size_t>(8192, (m.nC * Ly + 255) / 256)));
     S->diag_partial = static_cast<double*>(S->arena.alloc(sizeof(double) * 2 * S->diag_blocks, err));
     S->diag_out = static_cast<double*>(S->arena.alloc(sizeof(double) * 2, err));
     if (err != cudaSuccess)
