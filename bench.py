@@ -231,6 +231,22 @@ def oracle_labels(o, w):
     return None if np.ndim(w.M) else o.regions(w.fine_mask, w.interface_layers)
 
 
+def predicted_speedup(counts, M):
+    """Work-count prediction of the LTS3 speed-up over global SSP-RK3 at the
+    fine step (the paper's optimal-ratio estimate of Section 3.3, extended by
+    the interface corrections): cell right-hand-side evaluations per coarse
+    step, 3 M N for global SSP-RK3 against
+    3 N_C + (2 + 3M) N_I + N_Fbar + 3M N_F for LTS3.  Band counts in library
+    band order: F deep, F3, F2, F1 (fine), I1, I2 (interface), C1.. (coarse);
+    Fbar = F2 and F1, the fine cells Step 1 also evaluates."""
+    c = np.asarray(counts, np.float64)
+    nF, nFbar, nI, nC = c[0:4].sum(), c[2:4].sum(), c[4:6].sum(), c[6:].sum()
+    n = c.sum()
+    lts_work = 3 * nC + (2 + 3 * M) * nI + nFbar + 3 * M * nF
+    return {"predicted": float(3 * M * n / lts_work), "cells": {"fine": int(nF), "interface": int(nI),
+                                                                "coarse": int(nC)}}
+
+
 def oracle_sample(w, nsteps_cap=3, budget_s=20.0):
     """Times the FP64 oracle's LTS3 coarse step on the full workload; returns
     (cell-updates/s, steps, seconds, threads, result)."""
@@ -589,6 +605,24 @@ def extras(args, w, model, stats, stream, h_gpu, u_gpu, diag):
     out["fp64_ssprk3_fine_dt"] = {"ms_per_coarse_interval": ref_ms,
                                   "sim_seconds_per_wall_second": w.dt / (ref_ms * 1e-3),
                                   "note": f"FP64 SSPRK3 on the whole mesh at dt/M = {w.dt / Mx:.3f} s"}
+    # ---- the LTS speed-up at equal precision: global FP32 SSP-RK3 at dt/M
+    #      against this run's coarse step, beside the work-count prediction
+    ref32 = lts.Model(w.mesh, w.fine_mask, w.M, w.h0, w.u0, w.dt / Mx, w.g, precision=prec,
+                      compensated=True, mode=lts.LTS_MODE_SSPRK3, stream=stream.cuda_stream)
+    ref32.step(Mx)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    ref32.step(ncmp * Mx)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ref32_ms = e0.elapsed_time(e1) / ncmp
+    counts, _, _ = lts.lts_regions_counts(model.reg_h)
+    out["lts_speedup"] = dict(predicted_speedup(counts, Mx),
+                              measured=ref32_ms / (args._ms / args.steps),
+                              ssprk3_fine_dt_ms_per_coarse_interval=ref32_ms,
+                              note="global SSPRK3 (same precision) at dt/M over dt, divided by one LTS3 "
+                                   "coarse step; predicted = RHS cell-evaluations of the two")
+    ref32.close()
     # ---- CPU baseline (oracle on the host cores) and the error of this run's
     #      first coarse step against it
     cells_per_s, n_or, t_or, cores, (rh, ru) = oracle_sample(w, nsteps_cap=1)

@@ -39,7 +39,7 @@ LTS_COARSE_FAR = 1
 LTS_COARSE_SERIAL = 2
 
 NBANDS = 12
-BAND_NAMES = ("F_deep", "F3", "F2", "F1", "I1", "I2", "C1", "C2", "C_rest")
+BAND_NAMES = ("F_deep", "F3", "F2", "F1", "I1", "I2", "C1", "C2", "C3", "C4", "C5", "C_rest")
 
 _DP = C.POINTER(C.c_double)
 _IP = C.POINTER(C.c_int32)

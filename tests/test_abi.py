@@ -83,7 +83,8 @@ def test_regions_labels_match_band_counts():
         cl, el = lts.lts_regions_labels(rh, mesh["nCells"], mesh["nEdges"])
         c, e, v = lts.lts_regions_counts(rh)
         assert c.sum() == mesh["nCells"] and e.sum() == mesh["nEdges"] and v.sum() == mesh["nVertices"]
-        # label 5 (coarse) = bands C1, C2, C rest; label 3 = I1; 4 = I2
+        assert len(c) == lts.NBANDS == len(lts.BAND_NAMES)
+        # label 5 (coarse) = bands C1..C5 and C rest; label 3 = I1; 4 = I2
         assert (cl == 3).sum() == c[4] and (cl == 4).sum() == c[5] and (cl == 5).sum() == c[6:].sum()
         pc, pe, pv = lts.lts_regions_permutation(rh, mesh["nCells"], mesh["nEdges"], mesh["nVertices"])
         assert sorted(pc.tolist()) == list(range(mesh["nCells"]))
