@@ -998,9 +998,17 @@ int write_state(lts_state_s* S, const double* h, const double* u) {
     const HostMesh& m = S->reg->mesh->m;
     const SV& X = S->buf[S->parity];
     const size_t Ly = static_cast<size_t>(S->kc.layers);
-    CUDA_TRY(cudaMemcpyAsync(S->stage_c, h, sizeof(double) * m.nC * Ly, cudaMemcpyHostToDevice, S->stream));
-    CUDA_TRY(cudaMemcpyAsync(S->stage_e, u, sizeof(double) * m.nE * Ly, cudaMemcpyHostToDevice, S->stream));
+    // the copies go on the I/O stream after everything enqueued so far; each
+    // scatter waits for its copy, so the h scatter overlaps the u copy
+    CUDA_TRY(cudaEventRecord(S->ev_io[0], S->stream));
+    CUDA_TRY(cudaStreamWaitEvent(S->io_stream, S->ev_io[0], 0));
+    CUDA_TRY(cudaMemcpyAsync(S->stage_c, h, sizeof(double) * m.nC * Ly, cudaMemcpyHostToDevice, S->io_stream));
+    CUDA_TRY(cudaEventRecord(S->ev_io[0], S->io_stream));
+    CUDA_TRY(cudaMemcpyAsync(S->stage_e, u, sizeof(double) * m.nE * Ly, cudaMemcpyHostToDevice, S->io_stream));
+    CUDA_TRY(cudaEventRecord(S->ev_io[1], S->io_stream));
+    CUDA_TRY(cudaStreamWaitEvent(S->stream, S->ev_io[0], 0));
     CUDA_TRY(launch_scatter_state(S->kc, m.nC, S->reg->d_perm_c, S->stage_c, X.hh, X.hl, S->stream));
+    CUDA_TRY(cudaStreamWaitEvent(S->stream, S->ev_io[1], 0));
     CUDA_TRY(launch_scatter_state(S->kc, m.nE, S->reg->d_perm_e, S->stage_e, X.uh, X.ul, S->stream));
     return LTS_OK;
 }
@@ -1034,6 +1042,9 @@ lts_state_s::~lts_state_s() {
     if (own_stream && stream) cudaStreamDestroy(stream);
     if (capture_stream) cudaStreamDestroy(capture_stream);
     if (side_stream) cudaStreamDestroy(side_stream);
+    if (io_stream) cudaStreamDestroy(io_stream);
+    for (auto ev : ev_io)
+        if (ev) cudaEventDestroy(ev);
     if (capture_side) cudaStreamDestroy(capture_side);
     if (ev_fork) cudaEventDestroy(ev_fork);
     if (ev_join) cudaEventDestroy(ev_join);
@@ -1370,6 +1381,8 @@ int lts_state_create(lts_mesh mesh, lts_regions reg, const double* h0, const dou
     CUDA_TRY(cudaStreamCreateWithFlags(&S->capture_stream, cudaStreamNonBlocking));
     CUDA_TRY(cudaStreamCreateWithFlags(&S->capture_side, cudaStreamNonBlocking));
     CUDA_TRY(cudaStreamCreateWithFlags(&S->side_stream, cudaStreamNonBlocking));
+    CUDA_TRY(cudaStreamCreateWithFlags(&S->io_stream, cudaStreamNonBlocking));
+    for (auto& ev : S->ev_io) CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     CUDA_TRY(cudaEventCreateWithFlags(&S->ev_fork, cudaEventDisableTiming));
     CUDA_TRY(cudaEventCreateWithFlags(&S->ev_join, cudaEventDisableTiming));
     reg->ref++;
@@ -1518,15 +1531,21 @@ int lts_read(lts_state s, double* h, double* u, lts_diag* d) {
     if (!s) return set_error(LTS_EINVAL, "null state");
     const HostMesh& m = s->reg->mesh->m;
     const SV& X = s->buf[s->parity];
+    // each copy goes on the I/O stream once its gather is done, so it
+    // overlaps the next gather and the diagnostics
     if (h) {
         CUDA_TRY(launch_gather_state(s->kc, m.nC, s->reg->d_perm_c, X.hh, X.hl, s->stage_c, s->stream));
+        CUDA_TRY(cudaEventRecord(s->ev_io[0], s->stream));
+        CUDA_TRY(cudaStreamWaitEvent(s->io_stream, s->ev_io[0], 0));
         CUDA_TRY(cudaMemcpyAsync(h, s->stage_c, sizeof(double) * m.nC * s->kc.layers, cudaMemcpyDeviceToHost,
-                                 s->stream));
+                                 s->io_stream));
     }
     if (u) {
         CUDA_TRY(launch_gather_state(s->kc, m.nE, s->reg->d_perm_e, X.uh, X.ul, s->stage_e, s->stream));
+        CUDA_TRY(cudaEventRecord(s->ev_io[1], s->stream));
+        CUDA_TRY(cudaStreamWaitEvent(s->io_stream, s->ev_io[1], 0));
         CUDA_TRY(cudaMemcpyAsync(u, s->stage_e, sizeof(double) * m.nE * s->kc.layers, cudaMemcpyDeviceToHost,
-                                 s->stream));
+                                 s->io_stream));
     }
     double diag[2] = {0, 0};
     if (d) {
@@ -1538,6 +1557,7 @@ int lts_read(lts_state s, double* h, double* u, lts_diag* d) {
     CUDA_TRY(cudaMemcpyAsync(&flag, s->flag, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
     CUDA_TRY(cudaMemsetAsync(s->flag, 0, sizeof(int), s->stream));
     CUDA_TRY(cudaStreamSynchronize(s->stream));
+    CUDA_TRY(cudaStreamSynchronize(s->io_stream));
     if (d) {
         d->mass = diag[0];
         d->energy = diag[1];

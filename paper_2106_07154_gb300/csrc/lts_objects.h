@@ -102,6 +102,10 @@ struct lts_state_s {
     cudaStream_t side_stream = nullptr;          // concurrent branch (direct launches)
     cudaStream_t capture_side = nullptr;         // concurrent branch during capture
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // host I/O: copies run on io_stream, overlapping the gather, scatter and
+    // diagnostics kernels on the state's stream
+    cudaStream_t io_stream = nullptr;
+    cudaEvent_t ev_io[2] = {nullptr, nullptr};
     DeviceArena arena;
     const void* tables = nullptr;
     SV buf[4];            // [parity] = x_old, [1-parity] = x_new, [2] = x_1st, [3] = x_2nd
