@@ -515,12 +515,49 @@ def extras(args, w, model, stats, stream, h_gpu, u_gpu, diag):
         model.step(1)
         model.read(hb, ub)
     e2e_s = time.perf_counter() - t0
-    out["e2e"] = {"value": nC * args.e2e_steps / e2e_s, "unit": UNIT,
+    round_trip = {"value": nC * args.e2e_steps / e2e_s, "unit": UNIT,
                   "h2d_bytes_per_step": 8 * (nC + nE),
                   "d2h_bytes_per_step": 8 * (nC + nE) + 16 + 4,
                   "steps": args.e2e_steps,
                   "note": "lts_write (H2D of h,u) + lts_step(1) + lts_read (D2H of h,u, FP64 "
-                          "mass/energy), pinned host buffers, wall clock"}
+                          "mass/energy) per step, each step resuming from the state read back; "
+                          "pinned host buffers, wall clock"}
+    # ---- streamed: every step uploads a state, advances it one coarse step
+    #      and reads it back with its diagnostics (lts_write, lts_step,
+    #      lts_read_async), one lts_sync per `depth` steps, so the copies of
+    #      neighbouring steps overlap the steps
+    depth = 16
+    hin = [torch.empty(nC, dtype=torch.float64, pin_memory=True).numpy() for _ in range(depth)]
+    uin = [torch.empty(nE, dtype=torch.float64, pin_memory=True).numpy() for _ in range(depth)]
+    hout = [torch.empty(nC, dtype=torch.float64, pin_memory=True).numpy() for _ in range(depth)]
+    uout = [torch.empty(nE, dtype=torch.float64, pin_memory=True).numpy() for _ in range(depth)]
+    for j in range(depth):
+        hin[j][:] = w.h0
+        uin[j][:] = w.u0
+    nstream = depth * max(1, args.e2e_steps // depth)
+    for j in range(depth):      # one untimed group
+        model.write(hin[j], uin[j])
+        model.step(1)
+        model.read_async(hout[j], uout[j], diag=True)
+    model.sync()
+    t0 = time.perf_counter()
+    for k in range(nstream):
+        j = k % depth
+        model.write(hin[j], uin[j])
+        model.step(1)
+        model.read_async(hout[j], uout[j], diag=True)
+        if j == depth - 1:
+            model.sync()
+    e2e_s = time.perf_counter() - t0
+    out["e2e"] = {"value": nC * nstream / e2e_s, "unit": UNIT,
+                  "h2d_bytes_per_step": 8 * (nC + nE),
+                  "d2h_bytes_per_step": 8 * (nC + nE) + 16 + 4,
+                  "steps": nstream,
+                  "note": f"streamed through the C ABI: per step lts_write (H2D of h,u from pinned "
+                          f"memory), lts_step(1), lts_read_async (D2H of h,u and FP64 mass/energy); "
+                          f"one lts_sync per {depth} steps, so copies overlap neighbouring steps; "
+                          f"wall clock",
+                  "round_trip": round_trip}
     # ---- per-kernel timing: the same coarse-step graph with an event-record
     #      node before and after every kernel node, on the state's stream
     tuned = model.tuned or {}

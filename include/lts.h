@@ -315,12 +315,32 @@ typedef struct lts_diag {
 /* Synchronises the state's stream and copies the state to the caller in the
  * original order and orientation (h [nCells], u [nEdges], FP64; either may
  * be NULL), plus diagnostics (d may be NULL).  Returns LTS_ENONFINITE if any
- * stage produced a thickness <= 0 or a non-finite value since the last read. */
+ * stage produced a thickness <= 0 or a non-finite value since the last read
+ * or lts_sync.  Equivalent to lts_read_async followed by lts_sync. */
 int lts_read(lts_state s, double* h, double* u, lts_diag* d);
 
 /* Replaces the state (original order, FP64 host arrays), e.g. to resume from
- * a saved lts_read; `time`/`steps` set the clock.  Enqueued on the stream. */
+ * a saved lts_read; `time`/`steps` set the clock.  Enqueued: the copies run
+ * on a host-to-device stream of the state as soon as the previous write's
+ * staging is free (they may overlap coarse steps enqueued earlier), and the
+ * state is replaced in stream order.  From pageable memory the call returns
+ * once the data is staged; from pinned memory it returns at once, and the
+ * caller keeps h and u unchanged until the next lts_sync or lts_read. */
 int lts_write(lts_state s, const double* h, const double* u, double time, int64_t steps);
+
+/* Streaming host I/O (the paper has no counterpart; an interface for moving
+ * a state in and out every step, e.g. many independent states through one
+ * solver).  lts_read_async enqueues the copy of the state as it stands after
+ * everything enqueued so far into h, u (original order, FP64; either may be
+ * NULL) and, with d, its diagnostics, and returns at once.  The state is
+ * gathered on the state's stream and copied on a device-to-host stream, so
+ * the copy overlaps coarse steps enqueued after it.  h, u and *d are valid
+ * after the next lts_sync (or lts_read); use pinned memory for the overlap.
+ * At most 16 reads with diagnostics between two syncs (LTS_EINVAL beyond).
+ * lts_sync waits for all the state's work and copies, and returns
+ * LTS_ENONFINITE as lts_read does.  Errors: LTS_EINVAL, LTS_ECUDA. */
+int lts_read_async(lts_state s, double* h, double* u, lts_diag* d);
+int lts_sync(lts_state s);
 
 /* Launch statistics of one coarse step: number of kernel launches, and per
  * launch kind k (0 = vertex PV, 1 = cell ring pass with the thickness

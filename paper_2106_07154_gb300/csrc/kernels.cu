@@ -1002,14 +1002,18 @@ __global__ void scatter_kernel(int n, int L, const int* perm, const double* src,
     if (COMP) lo[i] = static_cast<T>(x - static_cast<double>(h));
 }
 
+// snap (may be null): the same FP64 values in band order, for diagnostics
+// that run beside the following steps
 template <class T, bool COMP>
-__global__ void gather_kernel(int n, int L, const int* perm, const T* hi, const T* lo, double* dst) {
+__global__ void gather_kernel(int n, int L, const int* perm, const T* hi, const T* lo, double* dst,
+                              double* snap) {
     const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= static_cast<long long>(n) * L) return;
     const int e = static_cast<int>(i / L), l = static_cast<int>(i - static_cast<long long>(e) * L);
     double x = static_cast<double>(hi[i]);
     if (COMP) x += static_cast<double>(lo[i]);
     dst[static_cast<long long>(l) * n + perm[e]] = x;
+    if (snap) snap[i] = x;
 }
 
 // ------------------------------------------------------------ FP64 diagnostics
@@ -1019,9 +1023,11 @@ constexpr int DIAG_THREADS = 256;
 
 // (summed over the layers of a multi-layer state: element-major, layers
 // innermost)
-template <class T, bool COMP>
-__global__ void __launch_bounds__(DIAG_THREADS) diag_kernel(const Tables<T> t, const T* hh, const T* hl,
-                                                           const T* uh, const T* ul, double g,
+// TT: the tables' precision; TS: the state's (FP64 for a band-order
+// snapshot of an FP32 state, which gives the same values as the state)
+template <class TT, class TS, bool COMP>
+__global__ void __launch_bounds__(DIAG_THREADS) diag_kernel(const Tables<TT> t, const TS* hh, const TS* hl,
+                                                           const TS* uh, const TS* ul, double g,
                                                            double* partial, int L) {
     __shared__ double sm[2][DIAG_THREADS];
     const int N = t.nC;
@@ -1185,17 +1191,17 @@ cudaError_t launch_scatter_state(const KernelConfig& kc, int n, const int* perm,
 }
 
 cudaError_t launch_gather_state(const KernelConfig& kc, int n, const int* perm, const void* hi,
-                                const void* lo, double* dst, cudaStream_t s) {
+                                const void* lo, double* dst, cudaStream_t s, double* snap) {
     if (n <= 0) return cudaSuccess;
     const int L = kc.layers > 1 ? kc.layers : 1;
     const int b = 256;
     const long long g = (static_cast<long long>(n) * L + b - 1) / b;
     if (kc.precision == 1)
-        gather_kernel<double, false><<<g, b, 0, s>>>(n, L, perm, (const double*)hi, nullptr, dst);
+        gather_kernel<double, false><<<g, b, 0, s>>>(n, L, perm, (const double*)hi, nullptr, dst, snap);
     else if (kc.comp)
-        gather_kernel<float, true><<<g, b, 0, s>>>(n, L, perm, (const float*)hi, (const float*)lo, dst);
+        gather_kernel<float, true><<<g, b, 0, s>>>(n, L, perm, (const float*)hi, (const float*)lo, dst, snap);
     else
-        gather_kernel<float, false><<<g, b, 0, s>>>(n, L, perm, (const float*)hi, nullptr, dst);
+        gather_kernel<float, false><<<g, b, 0, s>>>(n, L, perm, (const float*)hi, nullptr, dst, snap);
     return cudaGetLastError();
 }
 
@@ -1205,18 +1211,32 @@ cudaError_t launch_diagnostics(const KernelConfig& kc, const void* tables, const
     const int L = kc.layers > 1 ? kc.layers : 1;
     if (kc.precision == 1) {
         const Tables<double>& t = *static_cast<const Tables<double>*>(tables);
-        diag_kernel<double, false><<<nblocks, DIAG_THREADS, 0, s>>>(
+        diag_kernel<double, double, false><<<nblocks, DIAG_THREADS, 0, s>>>(
             t, (const double*)h_hi, nullptr, (const double*)u_hi, nullptr, g, partial, L);
     } else {
         const Tables<float>& t = *static_cast<const Tables<float>*>(tables);
         if (kc.comp)
-            diag_kernel<float, true><<<nblocks, DIAG_THREADS, 0, s>>>(
+            diag_kernel<float, float, true><<<nblocks, DIAG_THREADS, 0, s>>>(
                 t, (const float*)h_hi, (const float*)h_lo, (const float*)u_hi, (const float*)u_lo, g,
                 partial, L);
         else
-            diag_kernel<float, false><<<nblocks, DIAG_THREADS, 0, s>>>(
+            diag_kernel<float, float, false><<<nblocks, DIAG_THREADS, 0, s>>>(
                 t, (const float*)h_hi, nullptr, (const float*)u_hi, nullptr, g, partial, L);
     }
+    diag_final<<<1, DIAG_THREADS, 0, s>>>(partial, nblocks, out2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_diagnostics_snapshot(const KernelConfig& kc, const void* tables, const double* h,
+                                        const double* u, double g, double* partial, int nblocks, double* out2,
+                                        cudaStream_t s) {
+    const int L = kc.layers > 1 ? kc.layers : 1;
+    if (kc.precision == 1)
+        diag_kernel<double, double, false><<<nblocks, DIAG_THREADS, 0, s>>>(
+            *static_cast<const Tables<double>*>(tables), h, nullptr, u, nullptr, g, partial, L);
+    else
+        diag_kernel<float, double, false><<<nblocks, DIAG_THREADS, 0, s>>>(
+            *static_cast<const Tables<float>*>(tables), h, nullptr, u, nullptr, g, partial, L);
     diag_final<<<1, DIAG_THREADS, 0, s>>>(partial, nblocks, out2);
     return cudaGetLastError();
 }

@@ -982,6 +982,10 @@ int state_alloc(lts_state_s* S) {
     S->flag = static_cast<int*>(S->arena.alloc(sizeof(int), err));
     S->stage_c = static_cast<double*>(S->arena.alloc(sizeof(double) * m.nC * Ly, err));
     S->stage_e = static_cast<double*>(S->arena.alloc(sizeof(double) * m.nE * Ly, err));
+    S->out_c = static_cast<double*>(S->arena.alloc(sizeof(double) * m.nC * Ly, err));
+    S->out_e = static_cast<double*>(S->arena.alloc(sizeof(double) * m.nE * Ly, err));
+    S->snap_c = static_cast<double*>(S->arena.alloc(sizeof(double) * m.nC * Ly, err));
+    S->snap_e = static_cast<double*>(S->arena.alloc(sizeof(double) * m.nE * Ly, err));
     // one (cell, layer) per thread up to 8192 blocks, then grid-stride
     S->diag_blocks = static_cast<int>(std::max<size_t>(1, std::min<size_t>(8192, (m.nC * Ly + 255) / 256)));
     S->diag_partial = static_cast<double*>(S->arena.alloc(sizeof(double) * 2 * S->diag_blocks, err));
@@ -998,18 +1002,89 @@ int write_state(lts_state_s* S, const double* h, const double* u) {
     const HostMesh& m = S->reg->mesh->m;
     const SV& X = S->buf[S->parity];
     const size_t Ly = static_cast<size_t>(S->kc.layers);
-    // the copies go on the I/O stream after everything enqueued so far; each
-    // scatter waits for its copy, so the h scatter overlaps the u copy
-    CUDA_TRY(cudaEventRecord(S->ev_io[0], S->stream));
-    CUDA_TRY(cudaStreamWaitEvent(S->io_stream, S->ev_io[0], 0));
-    CUDA_TRY(cudaMemcpyAsync(S->stage_c, h, sizeof(double) * m.nC * Ly, cudaMemcpyHostToDevice, S->io_stream));
-    CUDA_TRY(cudaEventRecord(S->ev_io[0], S->io_stream));
-    CUDA_TRY(cudaMemcpyAsync(S->stage_e, u, sizeof(double) * m.nE * Ly, cudaMemcpyHostToDevice, S->io_stream));
-    CUDA_TRY(cudaEventRecord(S->ev_io[1], S->io_stream));
-    CUDA_TRY(cudaStreamWaitEvent(S->stream, S->ev_io[0], 0));
+    // The copies wait only until the input staging is free (the previous
+    // write's scatters have run), so they overlap whatever the state's stream
+    // is still doing; the scatters replace the state in stream order, and the
+    // h scatter overlaps the u copy.
+    CUDA_TRY(cudaStreamWaitEvent(S->h2d_stream, S->ev_in_free, 0));
+    CUDA_TRY(cudaMemcpyAsync(S->stage_c, h, sizeof(double) * m.nC * Ly, cudaMemcpyHostToDevice, S->h2d_stream));
+    CUDA_TRY(cudaEventRecord(S->ev_in_h, S->h2d_stream));
+    CUDA_TRY(cudaMemcpyAsync(S->stage_e, u, sizeof(double) * m.nE * Ly, cudaMemcpyHostToDevice, S->h2d_stream));
+    CUDA_TRY(cudaEventRecord(S->ev_in_u, S->h2d_stream));
+    CUDA_TRY(cudaStreamWaitEvent(S->stream, S->ev_in_h, 0));
     CUDA_TRY(launch_scatter_state(S->kc, m.nC, S->reg->d_perm_c, S->stage_c, X.hh, X.hl, S->stream));
-    CUDA_TRY(cudaStreamWaitEvent(S->stream, S->ev_io[1], 0));
+    CUDA_TRY(cudaStreamWaitEvent(S->stream, S->ev_in_u, 0));
     CUDA_TRY(launch_scatter_state(S->kc, m.nE, S->reg->d_perm_e, S->stage_e, X.uh, X.ul, S->stream));
+    CUDA_TRY(cudaEventRecord(S->ev_in_free, S->stream));
+    return LTS_OK;
+}
+
+// Enqueues the copy of the current state (and its diagnostics) to the host:
+// gathers into the output staging on the state's stream once the previous
+// read's copies are done, then the device-to-host copies on d2h_stream.
+int read_state(lts_state_s* S, double* h, double* u, lts_diag* d) {
+    const HostMesh& m = S->reg->mesh->m;
+    const SV& X = S->buf[S->parity];
+    const size_t Ly = static_cast<size_t>(S->kc.layers);
+    if (d && static_cast<int>(S->pending_diag.size()) >= lts_state_s::kDiagSlots)
+        return set_error(LTS_EINVAL, "more than %d reads with diagnostics before lts_sync",
+                         lts_state_s::kDiagSlots);
+    CUDA_TRY(cudaStreamWaitEvent(S->stream, S->ev_out_free, 0));
+    if (d) CUDA_TRY(cudaStreamWaitEvent(S->stream, S->ev_snap_free, 0));
+    // with diagnostics both fields are gathered (for the snapshot), whether
+    // or not the caller copies them
+    if (h || d) {
+        CUDA_TRY(launch_gather_state(S->kc, m.nC, S->reg->d_perm_c, X.hh, X.hl, S->out_c, S->stream,
+                                     d ? S->snap_c : nullptr));
+        CUDA_TRY(cudaEventRecord(S->ev_out_h, S->stream));
+        CUDA_TRY(cudaStreamWaitEvent(S->d2h_stream, S->ev_out_h, 0));
+        if (h)
+            CUDA_TRY(cudaMemcpyAsync(h, S->out_c, sizeof(double) * m.nC * Ly, cudaMemcpyDeviceToHost,
+                                     S->d2h_stream));
+    }
+    if (u || d)
+        CUDA_TRY(launch_gather_state(S->kc, m.nE, S->reg->d_perm_e, X.uh, X.ul, S->out_e, S->stream,
+                                     d ? S->snap_e : nullptr));
+    CUDA_TRY(cudaEventRecord(S->ev_out_u, S->stream));
+    CUDA_TRY(cudaStreamWaitEvent(S->d2h_stream, S->ev_out_u, 0));
+    if (u)
+        CUDA_TRY(cudaMemcpyAsync(u, S->out_e, sizeof(double) * m.nE * Ly, cudaMemcpyDeviceToHost, S->d2h_stream));
+    CUDA_TRY(cudaEventRecord(S->ev_out_free, S->d2h_stream));
+    if (d) {
+        const int slot = static_cast<int>(S->pending_diag.size());
+        CUDA_TRY(cudaStreamWaitEvent(S->diag_stream, S->ev_out_u, 0));
+        CUDA_TRY(launch_diagnostics_snapshot(S->kc, S->tables, S->snap_c, S->snap_e, S->p.g, S->diag_partial,
+                                             S->diag_blocks, S->diag_out, S->diag_stream));
+        CUDA_TRY(cudaMemcpyAsync(S->diag_host + 2 * slot, S->diag_out, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                                 S->diag_stream));
+        CUDA_TRY(cudaEventRecord(S->ev_snap_free, S->diag_stream));
+        S->pending_diag.push_back({d, S->time, S->steps});
+    }
+    return LTS_OK;
+}
+
+// Waits for everything enqueued on the state and its copy streams, fills
+// the pending diagnostics and reports (and clears) the error flag.
+int sync_state(lts_state_s* S) {
+    CUDA_TRY(cudaMemcpyAsync(S->flag_host, S->flag, sizeof(int), cudaMemcpyDeviceToHost, S->stream));
+    CUDA_TRY(cudaMemsetAsync(S->flag, 0, sizeof(int), S->stream));
+    CUDA_TRY(cudaStreamSynchronize(S->stream));
+    CUDA_TRY(cudaStreamSynchronize(S->h2d_stream));
+    CUDA_TRY(cudaStreamSynchronize(S->d2h_stream));
+    CUDA_TRY(cudaStreamSynchronize(S->diag_stream));
+    for (size_t k = 0; k < S->pending_diag.size(); ++k) {
+        lts_diag* d = S->pending_diag[k].d;
+        d->mass = S->diag_host[2 * k];
+        d->energy = S->diag_host[2 * k + 1];
+        d->time = S->pending_diag[k].time;
+        d->steps = S->pending_diag[k].steps;
+    }
+    S->pending_diag.clear();
+    const int flag = *S->flag_host;
+    if (flag & 4) return set_error(LTS_ECUDA, "internal error: a tile exceeded its shared memory (skipped)");
+    if (flag)
+        return set_error(LTS_ENONFINITE, "a stage produced %s",
+                         (flag & 1) ? "a thickness <= 0 or non-finite" : "a non-finite velocity");
     return LTS_OK;
 }
 
@@ -1042,9 +1117,13 @@ lts_state_s::~lts_state_s() {
     if (own_stream && stream) cudaStreamDestroy(stream);
     if (capture_stream) cudaStreamDestroy(capture_stream);
     if (side_stream) cudaStreamDestroy(side_stream);
-    if (io_stream) cudaStreamDestroy(io_stream);
-    for (auto ev : ev_io)
+    if (h2d_stream) cudaStreamDestroy(h2d_stream);
+    if (d2h_stream) cudaStreamDestroy(d2h_stream);
+    if (diag_stream) cudaStreamDestroy(diag_stream);
+    for (auto ev : {ev_in_h, ev_in_u, ev_in_free, ev_out_h, ev_out_u, ev_out_free, ev_snap_free})
         if (ev) cudaEventDestroy(ev);
+    if (flag_host) cudaFreeHost(flag_host);
+    if (diag_host) cudaFreeHost(diag_host);
     if (capture_side) cudaStreamDestroy(capture_side);
     if (ev_fork) cudaEventDestroy(ev_fork);
     if (ev_join) cudaEventDestroy(ev_join);
@@ -1381,8 +1460,15 @@ int lts_state_create(lts_mesh mesh, lts_regions reg, const double* h0, const dou
     CUDA_TRY(cudaStreamCreateWithFlags(&S->capture_stream, cudaStreamNonBlocking));
     CUDA_TRY(cudaStreamCreateWithFlags(&S->capture_side, cudaStreamNonBlocking));
     CUDA_TRY(cudaStreamCreateWithFlags(&S->side_stream, cudaStreamNonBlocking));
-    CUDA_TRY(cudaStreamCreateWithFlags(&S->io_stream, cudaStreamNonBlocking));
-    for (auto& ev : S->ev_io) CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    CUDA_TRY(cudaStreamCreateWithFlags(&S->h2d_stream, cudaStreamNonBlocking));
+    CUDA_TRY(cudaStreamCreateWithFlags(&S->d2h_stream, cudaStreamNonBlocking));
+    CUDA_TRY(cudaStreamCreateWithFlags(&S->diag_stream, cudaStreamNonBlocking));
+    for (cudaEvent_t* ev : {&S->ev_in_h, &S->ev_in_u, &S->ev_in_free, &S->ev_out_h, &S->ev_out_u, &S->ev_out_free,
+                            &S->ev_snap_free})
+        CUDA_TRY(cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
+    CUDA_TRY(cudaHostAlloc(reinterpret_cast<void**>(&S->flag_host), sizeof(int), cudaHostAllocDefault));
+    CUDA_TRY(cudaHostAlloc(reinterpret_cast<void**>(&S->diag_host), sizeof(double) * 2 * lts_state_s::kDiagSlots,
+                           cudaHostAllocDefault));
     CUDA_TRY(cudaEventCreateWithFlags(&S->ev_fork, cudaEventDisableTiming));
     CUDA_TRY(cudaEventCreateWithFlags(&S->ev_join, cudaEventDisableTiming));
     reg->ref++;
@@ -1529,44 +1615,19 @@ int lts_step(lts_state s, int32_t n) {
 
 int lts_read(lts_state s, double* h, double* u, lts_diag* d) {
     if (!s) return set_error(LTS_EINVAL, "null state");
-    const HostMesh& m = s->reg->mesh->m;
-    const SV& X = s->buf[s->parity];
-    // each copy goes on the I/O stream once its gather is done, so it
-    // overlaps the next gather and the diagnostics
-    if (h) {
-        CUDA_TRY(launch_gather_state(s->kc, m.nC, s->reg->d_perm_c, X.hh, X.hl, s->stage_c, s->stream));
-        CUDA_TRY(cudaEventRecord(s->ev_io[0], s->stream));
-        CUDA_TRY(cudaStreamWaitEvent(s->io_stream, s->ev_io[0], 0));
-        CUDA_TRY(cudaMemcpyAsync(h, s->stage_c, sizeof(double) * m.nC * s->kc.layers, cudaMemcpyDeviceToHost,
-                                 s->io_stream));
-    }
-    if (u) {
-        CUDA_TRY(launch_gather_state(s->kc, m.nE, s->reg->d_perm_e, X.uh, X.ul, s->stage_e, s->stream));
-        CUDA_TRY(cudaEventRecord(s->ev_io[1], s->stream));
-        CUDA_TRY(cudaStreamWaitEvent(s->io_stream, s->ev_io[1], 0));
-        CUDA_TRY(cudaMemcpyAsync(u, s->stage_e, sizeof(double) * m.nE * s->kc.layers, cudaMemcpyDeviceToHost,
-                                 s->io_stream));
-    }
-    double diag[2] = {0, 0};
-    if (d) {
-        CUDA_TRY(launch_diagnostics(s->kc, s->tables, X.hh, X.hl, X.uh, X.ul, s->p.g, s->diag_partial,
-                                    s->diag_blocks, s->diag_out, s->stream));
-        CUDA_TRY(cudaMemcpyAsync(diag, s->diag_out, sizeof(diag), cudaMemcpyDeviceToHost, s->stream));
-    }
-    int flag = 0;
-    CUDA_TRY(cudaMemcpyAsync(&flag, s->flag, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
-    CUDA_TRY(cudaMemsetAsync(s->flag, 0, sizeof(int), s->stream));
-    CUDA_TRY(cudaStreamSynchronize(s->stream));
-    CUDA_TRY(cudaStreamSynchronize(s->io_stream));
-    if (d) {
-        d->mass = diag[0];
-        d->energy = diag[1];
-        d->time = s->time;
-        d->steps = s->steps;
-    }
-    if (flag & 4) return set_error(LTS_ECUDA, "internal error: a tile exceeded its shared memory (skipped)");
-    if (flag) return set_error(LTS_ENONFINITE, "a stage produced %s", (flag & 1) ? "a thickness <= 0 or non-finite" : "a non-finite velocity");
-    return LTS_OK;
+    int rc = read_state(s, h, u, d);
+    const int rs = sync_state(s);
+    return rc != LTS_OK ? rc : rs;
+}
+
+int lts_read_async(lts_state s, double* h, double* u, lts_diag* d) {
+    if (!s) return set_error(LTS_EINVAL, "null state");
+    return read_state(s, h, u, d);
+}
+
+int lts_sync(lts_state s) {
+    if (!s) return set_error(LTS_EINVAL, "null state");
+    return sync_state(s);
 }
 
 int lts_write(lts_state s, const double* h, const double* u, double time, int64_t steps) {

@@ -156,10 +156,15 @@ cudaError_t launch_phase(const LaunchDesc& d, const void* tables, const KernelCo
 cudaError_t launch_scatter_state(const KernelConfig& kc, int n, const int* perm, const double* src,
                                  void* hi, void* lo, cudaStream_t s);
 cudaError_t launch_gather_state(const KernelConfig& kc, int n, const int* perm, const void* hi,
-                                const void* lo, double* dst, cudaStream_t s);
+                                const void* lo, double* dst, cudaStream_t s, double* snap = nullptr);
 cudaError_t launch_diagnostics(const KernelConfig& kc, const void* tables, const void* h_hi,
                                const void* h_lo, const void* u_hi, const void* u_lo, double g,
                                double* partial, int nblocks, double* out2, cudaStream_t s);
+// The same reduction over a band-order FP64 snapshot of the state (written
+// by launch_gather_state), equal to the state's own to the last bit.
+cudaError_t launch_diagnostics_snapshot(const KernelConfig& kc, const void* tables, const double* h,
+                                        const double* u, double g, double* partial, int nblocks, double* out2,
+                                        cudaStream_t s);
 int kernel_registers(const KernelConfig& kc, int kind);
 // Segment-table launches (ensembles).  encode_segment_table converts the
 // non-empty segments of `segs` into the device records of kc's precision

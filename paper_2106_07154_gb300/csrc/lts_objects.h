@@ -102,10 +102,31 @@ struct lts_state_s {
     cudaStream_t side_stream = nullptr;          // concurrent branch (direct launches)
     cudaStream_t capture_side = nullptr;         // concurrent branch during capture
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-    // host I/O: copies run on io_stream, overlapping the gather, scatter and
-    // diagnostics kernels on the state's stream
-    cudaStream_t io_stream = nullptr;
-    cudaEvent_t ev_io[2] = {nullptr, nullptr};
+    // host I/O: host-to-device copies run on h2d_stream, device-to-host
+    // copies on d2h_stream, so they overlap the kernels on the state's stream
+    // (and, with lts_write_async / lts_read_async, the coarse steps).  Input
+    // staging (stage_c, stage_e) is free again once its scatter has run
+    // (ev_in_free); output staging (out_c, out_e, diag_out) once its copy to
+    // the host is done (ev_out_free).
+    // The diagnostics of a read run on diag_stream over a band-order FP64
+    // snapshot (snap_c, snap_e) that the gathers write, so they too overlap
+    // the following steps; the snapshot is free again after them
+    // (ev_snap_free).
+    cudaStream_t h2d_stream = nullptr, d2h_stream = nullptr, diag_stream = nullptr;
+    cudaEvent_t ev_in_h = nullptr, ev_in_u = nullptr, ev_in_free = nullptr;
+    cudaEvent_t ev_out_h = nullptr, ev_out_u = nullptr, ev_out_free = nullptr;
+    cudaEvent_t ev_snap_free = nullptr;
+    // pinned host words: the error flag and the diagnostics of the reads
+    // since the last lts_sync, with the caller's lts_diag each belongs to
+    static constexpr int kDiagSlots = 16;
+    int* flag_host = nullptr;
+    double* diag_host = nullptr;     // [kDiagSlots][2]
+    struct PendingDiag {
+        lts_diag* d;
+        double time;
+        int64_t steps;
+    };
+    std::vector<PendingDiag> pending_diag;
     DeviceArena arena;
     const void* tables = nullptr;
     SV buf[4];            // [parity] = x_old, [1-parity] = x_new, [2] = x_1st, [3] = x_2nd
@@ -121,8 +142,12 @@ struct lts_state_s {
     void* ring_c_side = nullptr;
     void* ring_k_side = nullptr;
     int* flag = nullptr;
-    double* stage_c = nullptr;   // FP64 staging for I/O (original order)
+    double* stage_c = nullptr;   // FP64 input staging (original order)
     double* stage_e = nullptr;
+    double* out_c = nullptr;     // FP64 output staging (original order)
+    double* out_e = nullptr;
+    double* snap_c = nullptr;    // FP64 snapshot of the state (band order)
+    double* snap_e = nullptr;
     double* diag_partial = nullptr;
     double* diag_out = nullptr;
     int diag_blocks = 0;

@@ -169,6 +169,8 @@ def lib():
             L.lts_step.argtypes = [C.c_void_p, C.c_int32]
             L.lts_read.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(lts_diag)]
             L.lts_write.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int64]
+            L.lts_read_async.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(lts_diag)]
+            L.lts_sync.argtypes = [C.c_void_p]
             L.lts_step_stats.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                          C.c_void_p]
             L.lts_diagnostics_noalloc.argtypes = [C.c_void_p, C.c_void_p]
@@ -406,6 +408,27 @@ def lts_write(state_h, h, u, time: float = 0.0, steps: int = 0):
                            int(steps)))
 
 
+def _ptr(a):
+    if a is None:
+        return None
+    if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"] or not a.flags["WRITEABLE"]:
+        raise ValueError("output arrays must be writeable, C-contiguous float64")
+    return a.ctypes.data
+
+
+def lts_read_async(state_h, h_out=None, u_out=None, diag: bool = False):
+    """Enqueues the copy of the state into h_out / u_out (float64 arrays the
+    caller keeps alive; pinned for overlap).  Returns the lts_diag that the
+    next lts_sync fills (None without diagnostics)."""
+    d = lts_diag() if diag else None
+    _check(lib().lts_read_async(state_h, _ptr(h_out), _ptr(u_out), C.byref(d) if d is not None else None))
+    return d
+
+
+def lts_sync(state_h):
+    _check(lib().lts_sync(state_h))
+
+
 def lts_step_stats(state_h):
     n = C.c_int32()
     b = np.zeros(LTS_NKINDS)
@@ -525,6 +548,7 @@ class Model:
         self.nV = int(mesh["nVertices"])
         self.mesh_h = self.reg_h = self.state_h = None
         self.tuned = None
+        self._pending = []
         self.mesh_h = lts_mesh_create(mesh)
         if np.ndim(M) > 0:   # several fine regions: fine_mask holds region ids 1..len(M)
             self.reg_h = lts_regions_set_multi(self.mesh_h, fine_mask, list(M), order, interface_layers)
@@ -552,9 +576,33 @@ class Model:
     def read(self, h_out=None, u_out=None):
         L = self.layers
         h, u, d = lts_read(self.state_h, L * self.nC, L * self.nE, h_out, u_out)
+        self._pending = []          # lts_read also completes earlier asynchronous reads
         if L > 1 and h_out is None:
             h, u = h.reshape(L, self.nC), u.reshape(L, self.nE)
         return h, u, d
+
+    def read_async(self, h_out=None, u_out=None, diag: bool = False):
+        """Enqueues the copy of the state as it stands after the work enqueued
+        so far into h_out / u_out (float64, layers x nCells / layers x nEdges
+        values; pinned memory overlaps the copy with the following steps).
+        The arrays (and the returned diagnostics record) are valid after
+        sync()."""
+        L = self.layers
+        if h_out is not None and h_out.size != L * self.nC:
+            raise ValueError("h_out must hold layers x nCells values")
+        if u_out is not None and u_out.size != L * self.nE:
+            raise ValueError("u_out must hold layers x nEdges values")
+        d = lts_read_async(self.state_h, h_out, u_out, diag)
+        if d is not None:
+            self._pending.append(d)
+        return d
+
+    def sync(self):
+        """Waits for the state's work and copies; returns the diagnostics of
+        the asynchronous reads since the last sync, in order."""
+        pending, self._pending = self._pending, []
+        lts_sync(self.state_h)
+        return [{"mass": d.mass, "energy": d.energy, "time": d.time, "steps": d.steps} for d in pending]
 
     def write(self, h, u, time=0.0, steps=0):
         lts_write(self.state_h, np.ascontiguousarray(h, np.float64).reshape(-1),
