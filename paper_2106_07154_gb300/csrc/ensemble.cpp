@@ -83,7 +83,7 @@ namespace {
 // single-mesh tables), so every slot may still be loaded unconditionally.
 template <class T>
 int build_union_tables(lts_ensemble_s* E, Tables<T>& t) {
-    const size_t NC = E->NC, NE = E->NE, NV = E->NV, W = E->MAXE;
+    const size_t NC = E->NC, NE = E->NE, NV = E->NV, W = slot_rows(E->MAXE);
     std::vector<uint8_t> cn(NC);
     std::vector<int> se(W * NC), sn(W * NC), sv(W * NC);
     std::vector<T> snl(W * NC), sR(W * NC), sK(W * NC), rA(NC), b(NC);
@@ -509,14 +509,15 @@ int lts_ensemble_create(const lts_state* members, int32_t n, const lts_ensemble_
     E->oI1e.assign(n + 1, 0);
     E->oIe.assign(n + 1, 0);
     int64_t tc = 0, te = 0, tv = 0;
-    int maxdeg = 0, mindeg = 1 << 30;
+    int maxdeg = 0, mindeg = 1 << 30, maxe_all = 0;
     for (int m = 0; m < n; ++m) {
         const HostMesh& hm = E->members[m]->reg->mesh->m;
         const RegionsHost& r = E->members[m]->reg->r;
         tc += hm.nC;
         te += hm.nE;
         tv += hm.nV;
-        if (static_cast<int64_t>(hm.maxE) * tc > 0x7fffffffLL || te > 0x7fffffffLL)
+        maxe_all = std::max(maxe_all, hm.maxE);
+        if (static_cast<int64_t>(slot_rows(maxe_all)) * tc > 0x7fffffffLL || te > 0x7fffffffLL)
             return set_error(LTS_EINVAL, "ensemble too large for 32-bit indices");
         E->offC[m + 1] = static_cast<int>(tc);
         E->offE[m + 1] = static_cast<int>(te);

@@ -289,8 +289,12 @@ __device__ __forceinline__ void vertex_pv(const DevArgs<T>& a, int v, const Lay<
 // and B the same with G_j qt_j: the weight sum regrouped into O(n) work.
 // The first UNCOND slots are loaded without waiting for the cell's degree
 // (padding slots are valid copies of slot 0), so the table loads and the
-// state gathers of a thread are issued as two independent waves.
-constexpr int UNCOND = 6;
+// state gathers of a thread are issued as two independent waves.  Seven
+// slots cover the heptagons of variable-resolution Voronoi meshes (about one
+// cell in eleven, so nearly every warp has one), whose last slot would
+// otherwise cost the warp a further round trip.
+constexpr int UNCOND = 7;
+static_assert(UNCOND <= kSlotRowsMin, "the slot tables must hold the unconditional slots");
 
 template <class T, bool COMP, int MAXR, bool LY>
 __device__ __forceinline__ T ring_pass(const DevArgs<T>& a, int c, const Lay<LY>& y) {

@@ -1430,7 +1430,8 @@ int lts_state_create(lts_mesh mesh, lts_regions reg, const double* h0, const dou
     if (layers > 1 && p->kernel_path != 0)
         return set_error(LTS_EINVAL, "multi-layer states run the three-launch path only (kernel_path 0)");
     if (static_cast<long long>(mesh->m.maxE) * mesh->m.nC * layers > 0x7fffffffLL * 8LL ||
-        static_cast<long long>(mesh->m.nE) * layers > 0x7fffffffLL)
+        static_cast<long long>(mesh->m.nE) * layers > 0x7fffffffLL ||
+        static_cast<long long>(slot_rows(mesh->m.maxE)) * mesh->m.nC > 0x7fffffffLL)
         return set_error(LTS_EINVAL, "mesh x layers too large");
     if (p->coarse_schedule < LTS_COARSE_STEP4 || p->coarse_schedule > LTS_COARSE_SERIAL)
         return set_error(LTS_EINVAL, "coarse_schedule must be LTS_COARSE_STEP4, _FAR or _SERIAL");

@@ -133,6 +133,13 @@ struct LaunchDesc {
 // 3 * stage + kind.
 constexpr int KEY_STEP1 = 0, KEY_STEP2 = 3, KEY_SIDE = 10, KEY_STEP3 = 100, KEY_TAIL = 1000000;
 
+// Slot-major cell tables (ring slots, their coefficients, the tiles' local
+// vertex ids) hold at least this many rows, the extra rows repeating slot 0
+// (indices) or zero (coefficients), so the ring kernels may load their first
+// slots without knowing the cell's degree.
+constexpr int kSlotRowsMin = 8;
+inline int slot_rows(int maxE) { return maxE > kSlotRowsMin ? maxE : kSlotRowsMin; }
+
 // Elements per thread of the vertex and edge launches when the caller
 // leaves the choice to the library.
 constexpr int LTS_DEFAULT_EPT = 1;

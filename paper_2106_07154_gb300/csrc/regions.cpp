@@ -285,16 +285,16 @@ int regions_impl(const HostMesh& m, const int8_t* fine, int layers, int ordering
         offsets(r.vband, vblk, nV, r.mvb);
     }
     // ---- connectivity in band order (host copies, for the planner's byte counts)
-    const int W = m.maxE;
+    const int W = m.maxE, WR = slot_rows(W);
     r.cn.assign(nC, 0);
-    r.se.assign(static_cast<size_t>(W) * nC, 0);
-    r.sn.assign(static_cast<size_t>(W) * nC, 0);
-    r.sv.assign(static_cast<size_t>(W) * nC, 0);
+    r.se.assign(static_cast<size_t>(WR) * nC, 0);
+    r.sn.assign(static_cast<size_t>(WR) * nC, 0);
+    r.sv.assign(static_cast<size_t>(WR) * nC, 0);
     for (int k = 0; k < nC; ++k) {
         int c = r.perm_c[k];
         int n = m.nEoC[c];
         r.cn[k] = static_cast<uint8_t>(n);
-        for (int j = 0; j < W; ++j) {
+        for (int j = 0; j < WR; ++j) {
             int jj = j < n ? j : 0;     // padding slots repeat slot 0 (never read)
             r.se[static_cast<size_t>(j) * nC + k] = r.inv_e[m.EoC[static_cast<size_t>(c) * W + jj]];
             r.sn[static_cast<size_t>(j) * nC + k] = r.inv_c[m.CoC[static_cast<size_t>(c) * W + jj]];
@@ -339,7 +339,7 @@ int regions_impl(const HostMesh& m, const int8_t* fine, int layers, int ordering
 // local cells are its own cells followed by its halo (the other cell of owned
 // edges); its local vertices are all ring vertices of its local cells.
 int build_tiles(const HostMesh& m, RegionsHost& r, int tile_cells) {
-    const int nC = m.nC, nE = m.nE, W = m.maxE;
+    const int nC = m.nC, nE = m.nE, WR = slot_rows(m.maxE);
     if (tile_cells < 32 || tile_cells > 4096) return set_error(LTS_EINVAL, "tile size out of range");
     r.tile_cells = tile_cells;
     r.tile_a.clear();
@@ -402,7 +402,7 @@ int build_tiles(const HostMesh& m, RegionsHost& r, int tile_cells) {
             // lsv block, slot-major over the local cells
             r.tile_lsv_off.push_back(static_cast<int>(r.lsv.size()));
             const size_t base = r.lsv.size();
-            r.lsv.resize(base + static_cast<size_t>(W) * nl, 0);
+            r.lsv.resize(base + static_cast<size_t>(WR) * nl, 0);
             for (int k = 0; k < nl; ++k) {
                 int c = cells[k];
                 for (int j = 0; j < r.cn[c]; ++j)
@@ -425,11 +425,11 @@ int build_tiles(const HostMesh& m, RegionsHost& r, int tile_cells) {
 // once to T.
 template <class T>
 void coefficient_tables(const HostMesh& m, const RegionsHost& r, CoefTables<T>& o) {
-    const int nC = m.nC, nE = m.nE, nV = m.nV, W = m.maxE;
-    o.snl.assign(static_cast<size_t>(W) * nC, T(0));
-    o.sR.assign(static_cast<size_t>(W) * nC, T(0));
-    o.sK.assign(static_cast<size_t>(W) * nC, T(0));
-    o.sK64.assign(static_cast<size_t>(W) * nC, 0.0);
+    const int nC = m.nC, nE = m.nE, nV = m.nV, W = m.maxE, WR = slot_rows(W);
+    o.snl.assign(static_cast<size_t>(WR) * nC, T(0));
+    o.sR.assign(static_cast<size_t>(WR) * nC, T(0));
+    o.sK.assign(static_cast<size_t>(WR) * nC, T(0));
+    o.sK64.assign(static_cast<size_t>(WR) * nC, 0.0);
     o.rA.resize(nC);
     o.b.resize(nC);
     o.area.resize(nC);
