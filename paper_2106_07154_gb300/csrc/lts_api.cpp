@@ -1066,20 +1066,24 @@ int read_state(lts_state_s* S, double* h, double* u, lts_diag* d) {
 // Waits for everything enqueued on the state and its copy streams, fills
 // the pending diagnostics and reports (and clears) the error flag.
 int sync_state(lts_state_s* S) {
+    // the callers' records are filled only on success; on any error they are
+    // dropped, so no later call writes through a pointer the caller may have
+    // released
+    std::vector<lts_state_s::PendingDiag> pending;
+    pending.swap(S->pending_diag);
     CUDA_TRY(cudaMemcpyAsync(S->flag_host, S->flag, sizeof(int), cudaMemcpyDeviceToHost, S->stream));
     CUDA_TRY(cudaMemsetAsync(S->flag, 0, sizeof(int), S->stream));
     CUDA_TRY(cudaStreamSynchronize(S->stream));
     CUDA_TRY(cudaStreamSynchronize(S->h2d_stream));
     CUDA_TRY(cudaStreamSynchronize(S->d2h_stream));
     CUDA_TRY(cudaStreamSynchronize(S->diag_stream));
-    for (size_t k = 0; k < S->pending_diag.size(); ++k) {
-        lts_diag* d = S->pending_diag[k].d;
+    for (size_t k = 0; k < pending.size(); ++k) {
+        lts_diag* d = pending[k].d;
         d->mass = S->diag_host[2 * k];
         d->energy = S->diag_host[2 * k + 1];
-        d->time = S->pending_diag[k].time;
-        d->steps = S->pending_diag[k].steps;
+        d->time = pending[k].time;
+        d->steps = pending[k].steps;
     }
-    S->pending_diag.clear();
     const int flag = *S->flag_host;
     if (flag & 4) return set_error(LTS_ECUDA, "internal error: a tile exceeded its shared memory (skipped)");
     if (flag)
@@ -1109,6 +1113,10 @@ double plan_launch_bytes(const LaunchDesc& d, const RegionsHost& r, int nC, int 
 }  // namespace lts
 
 lts_state_s::~lts_state_s() {
+    // copies may still be in flight into pinned or caller memory: finish them
+    // before anything they use is released
+    for (cudaStream_t st : {stream, side_stream, h2d_stream, d2h_stream, diag_stream})
+        if (st) cudaStreamSynchronize(st);
     for (auto& e : exec)
         if (e) cudaGraphExecDestroy(e);
     for (auto ev : events) cudaEventDestroy(ev);
