@@ -12,7 +12,10 @@ either test ends it.  Host logic over the C ABI only.
 """
 from __future__ import annotations
 
+import argparse
+import json
 import math
+import time
 
 from . import lts
 
@@ -77,3 +80,35 @@ def max_dt_protocol(mesh: dict, fine_mask, h0, u0, g: float, dt_guess: float, T:
             break
         best = M
     return {"dt_fine": dt_f, "M_max_stable": best, "dt_coarse": best * dt_f, "tried": tried}
+
+
+def main(argv=None) -> int:
+    """python -m paper_2106_07154_gb300.maxdt [--workload NAME] [--layers 1 2 3]:
+    the protocol on a named synthetic workload for each interface thickness,
+    one JSON line each."""
+    from . import workloads as W
+
+    ap = argparse.ArgumentParser(description=main.__doc__)
+    ap.add_argument("--workload", default="scvt_40962")
+    ap.add_argument("--layers", type=int, nargs="+", default=[1, 2, 3],
+                    help="interface thicknesses (cells) to run the protocol for")
+    ap.add_argument("--coarse-steps", type=float, default=100.0,
+                    help="simulated time T in units of the workload's coarse step")
+    ap.add_argument("--M-max", type=int, default=32)
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    args = ap.parse_args(argv)
+    w = W.workload(args.workload)
+    T = args.coarse_steps * w.dt
+    prec = lts.LTS_FP32 if args.precision == "fp32" else lts.LTS_FP64
+    for L in args.layers:
+        t0 = time.perf_counter()
+        res = max_dt_protocol(w.mesh, w.fine_mask, w.h0, w.u0, w.g, w.dt / w.M, T, M_max=args.M_max,
+                              precision=prec, layers=L)
+        res.update({"workload": w.name, "interface_layers": L, "T_s": T,
+                    "workload_dt_fine_s": w.dt / w.M, "seconds": time.perf_counter() - t0})
+        print(json.dumps(res), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())
