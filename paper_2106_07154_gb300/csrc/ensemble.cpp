@@ -90,7 +90,7 @@ int build_union_tables(lts_ensemble_s* E, Tables<T>& t) {
     std::vector<double> sK64(W * NC), area(NC), bd(NC);
     std::vector<int> ec0(NE), ec1(NE);
     std::vector<uint32_t> ep(NE);
-    std::vector<T> rdc(NE);
+    std::vector<T> rdc(NE), db(NE);
     std::vector<int> vc(3 * NV), ve(3 * NV);
     std::vector<T> vk(3 * NV), vd(3 * NV), f(NV);
     for (size_t m = 0; m < E->members.size(); ++m) {
@@ -125,6 +125,7 @@ int build_union_tables(lts_ensemble_s* E, Tables<T>& t) {
             ec1[oe + e] = r.ec1[e] + static_cast<int>(oc);
             ep[oe + e] = r.ep[e];
             rdc[oe + e] = co.rdc[e];
+            db[oe + e] = co.db[e];
         }
         for (size_t k = 0; k < 3; ++k)
             for (size_t v = 0; v < nV; ++v) {
@@ -155,6 +156,7 @@ int build_union_tables(lts_ensemble_s* E, Tables<T>& t) {
     t.ec1 = up(ec1);
     t.ep = up(ep);
     t.rdc = up(rdc);
+    t.db = up(db);
     const int* dvc = up(vc);
     const int* dve = up(ve);
     const T* dvk = up(vk);

@@ -407,7 +407,7 @@ __device__ __forceinline__ void edge_stat(const Tables<T>& t, const Ld& ld, int 
     const uint32_t pp = ld.stat(t.ep + e);
     s.p0 = pp & 0xff, s.p1 = (pp >> 8) & 0xff;
     s.rdc = ld.stat(t.rdc + e);
-    s.db = ld.stat(t.b + s.c1) - ld.stat(t.b + s.c0);
+    s.db = ld.stat(t.db + e);
 }
 
 // Gathers the two cells' ring results and thicknesses (after the wait) and
@@ -613,7 +613,7 @@ __device__ __forceinline__ void tile_pass(const DevArgs<T>& a, const DevSeg<T>& 
         const T C0 = rc_s[p0 * nl + l0], C1 = rc_s[p1 * nl + l1];
         T dh = ld(a.in_h + c1) - ld(a.in_h + c0);
         if (COMP) dh += ld(a.in_hl + c1) - ld(a.in_hl + c0);
-        const T db = ld.stat(t.b + c1) - ld.stat(t.b + c0);
+        const T db = ld.stat(t.db + e);
         const T grad = a.g * (dh + db) + (K_s[l1] - K_s[l0]);
         const T U = -ld.stat(t.rdc + e) * (T(0.5) * (C1 - C0) + grad);
         if (acc) {

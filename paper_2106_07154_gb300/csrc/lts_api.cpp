@@ -76,6 +76,7 @@ int build_tables(lts_regions_s* R, int which, Tables<T>& t) {
     t.ec1 = up(r.ec1);
     t.ep = up(r.ep);
     t.rdc = up(co.rdc);
+    t.db = up(co.db);
     const int* vc = up(r.vc);
     const int* ve = up(r.ve);
     const T* vk = up(co.vk);
@@ -112,7 +113,7 @@ int build_tables(lts_regions_s* R, int which, Tables<T>& t) {
 // read once per element; state and intermediates once per layer.
 double launch_bytes(const LaunchDesc& d, const RegionsHost& r, int nC, int nE, int nV, size_t T,
                     bool comp, int layers) {
-    std::vector<char> mh(nC, 0), mhl(nC, 0), mu(nE, 0), mq(nV, 0), mk(nC, 0), mb(nC, 0);
+    std::vector<char> mh(nC, 0), mhl(nC, 0), mu(nE, 0), mq(nV, 0), mk(nC, 0);
     std::vector<char> mrow(nC, 0), mvert(nV, 0);   // fused tiles: ring rows and vertices read
     double tab = 0.0, st = 0.0;   // table bytes, state bytes per layer
     const double c = comp ? 1.0 : 0.0;
@@ -148,11 +149,11 @@ double launch_bytes(const LaunchDesc& d, const RegionsHost& r, int nC, int nE, i
                 break;
             case SEG_EDGE_UPD:
             case SEG_EDGE_ACC:
-                tab += n * (12.0 + T);                       // ec0, ec1, ep, rdc
+                tab += n * (12.0 + 2.0 * T);                 // ec0, ec1, ep, rdc, db
                 for (int e = g.begin; e < g.end; ++e) {
                     mu[e] = 1;
                     for (int cc : {r.ec0[e], r.ec1[e]}) {
-                        mh[cc] = mk[cc] = mb[cc] = 1;
+                        mh[cc] = mk[cc] = 1;
                         if (comp) mhl[cc] = 1;
                     }
                 }
@@ -174,10 +175,11 @@ double launch_bytes(const LaunchDesc& d, const RegionsHost& r, int nC, int nE, i
                         mrow[cc] = 1;
                     }
                     for (int k = 0; k < tb.w; ++k) mvert[r.tverts[tb.z + k]] = 1;
+                    tab += static_cast<double>(tb.y - tb.x) * T;   // db of the owned edges
                     for (int e = tb.x; e < tb.y; ++e) {
                         mu[e] = 1;
                         for (int cc : {r.ec0[e], r.ec1[e]}) {
-                            mh[cc] = mb[cc] = 1;
+                            mh[cc] = 1;
                             if (comp) mhl[cc] = 1;
                         }
                     }
@@ -213,14 +215,11 @@ double launch_bytes(const LaunchDesc& d, const RegionsHost& r, int nC, int nE, i
             mu[r.ve[static_cast<size_t>(q) * nV + v]] = 1;
         }
     }
-    double cnt = 0.0, cntb = 0.0;
-    for (int k = 0; k < nC; ++k) {
-        cnt += mh[k] + mhl[k] + mk[k];
-        cntb += mb[k];
-    }
+    double cnt = 0.0;
+    for (int k = 0; k < nC; ++k) cnt += mh[k] + mhl[k] + mk[k];
     for (char x : mu) cnt += x;
     for (char x : mq) cnt += x;
-    return tab + cntb * T + layers * (st + cnt * T);
+    return tab + layers * (st + cnt * T);
 }
 
 // ------------------------------------------------------------ phase plans

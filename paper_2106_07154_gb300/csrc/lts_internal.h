@@ -40,6 +40,7 @@ struct Tables {
     const int* ec1;      // [nE]       cell n_e points into
     const uint32_t* ep;  // [nE]       slot of e in ec0 (bits 0-7) and in ec1 (bits 8-15)
     const T* rdc;        // [nE]       1 / d_e
+    const T* db;         // [nE]       b_{c1} - b_{c0}, formed in T from the T copies of b
     // vertices
     const int* vc0; const int* vc1; const int* vc2;   // [nV] cells on vertex
     const int* ve0; const int* ve1; const int* ve2;   // [nV] edges on vertex

@@ -459,6 +459,14 @@ void coefficient_tables(const HostMesh& m, const RegionsHost& r, CoefTables<T>& 
     }
     o.rdc.resize(nE);
     for (int k = 0; k < nE; ++k) o.rdc[k] = static_cast<T>(1.0 / m.dc[r.perm_e[k]]);
+    // the bottom difference across each edge, subtracted in T exactly as a
+    // kernel would subtract the two cells' T values (so the edge pass needs
+    // no dependent gather of b)
+    o.db.resize(nE);
+    for (int k = 0; k < nE; ++k) {
+        const T b1 = o.b[r.ec1[k]], b0 = o.b[r.ec0[k]];
+        o.db[k] = b1 - b0;
+    }
     o.vk.assign(3 * static_cast<size_t>(nV), T(0));
     o.vd.assign(3 * static_cast<size_t>(nV), T(0));
     o.f.resize(nV);

@@ -60,7 +60,7 @@ int build_tiles(const HostMesh& m, RegionsHost& r, int tile_cells);
 
 template <class T>
 struct CoefTables {
-    std::vector<T> snl, sR, sK, rA, b, rdc, vk, vd, f;
+    std::vector<T> snl, sR, sK, rA, b, rdc, db, vk, vd, f;
     std::vector<double> sK64, area, bd;
 };
 
