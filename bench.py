@@ -844,10 +844,25 @@ def run_ensemble(args):
             for i, (hb, ub) in enumerate(bufs):
                 ens.read(i, hb, ub)
         e2e_s = time.perf_counter() - t0
+        round_trip = {"value": my_cells * n_e2e / e2e_s, "unit": UNIT, "steps": n_e2e,
+                      "note": "per step: lts_ensemble_write of every member, one ensemble step, "
+                              "lts_ensemble_read of every member (pinned host buffers, wall clock)"}
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            for i, (hb, ub) in enumerate(bufs):
+                ens.write(i, hb, ub)
+            ens.step(1)
+            for i, (hb, ub) in enumerate(bufs):
+                ens.read_async(i, hb, ub, diag=True)
+            ens.sync()
+        e2e_s = time.perf_counter() - t0
         line["e2e"] = {"value": my_cells * n_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": h2d + 36 * len(bufs), "steps": n_e2e,
                        "note": "per step: lts_ensemble_write of every member, one ensemble step, "
-                               "lts_ensemble_read of every member (pinned host buffers, wall clock)"}
+                               "lts_ensemble_read_async of every member with its FP64 diagnostics, "
+                               "one lts_ensemble_sync (pinned host buffers, wall clock)",
+                       "round_trip": round_trip}
         # CPU baseline: the oracle on the two smallest members, one coarse step each
         import oracle
 

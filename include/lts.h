@@ -335,7 +335,8 @@ int lts_write(lts_state s, const double* h, const double* u, double time, int64_
  * NULL) and, with d, its diagnostics, and returns at once.  The state is
  * gathered on the state's stream and copied on a device-to-host stream, so
  * the copy overlaps coarse steps enqueued after it.  h, u and *d are valid
- * after the next lts_sync (or lts_read); use pinned memory for the overlap.
+ * after the next lts_sync (or lts_read), and must stay allocated until then
+ * (the library writes them); use pinned memory for the overlap.
  * At most 16 reads with diagnostics between two syncs (LTS_EINVAL beyond).
  * lts_sync waits for all the state's work and copies, and returns
  * LTS_ENONFINITE as lts_read does.  Errors: LTS_EINVAL, LTS_ECUDA. */
@@ -416,9 +417,22 @@ int lts_ensemble_step(lts_ensemble e, int32_t n_coarse);
  * value since the last ensemble read (the flag is shared by all members). */
 int lts_ensemble_read(lts_ensemble e, int32_t i, double* h, double* u, lts_diag* d);
 
+/* Asynchronous member read (as lts_read_async on the member): enqueues the
+ * unpacking of member i and the copy of its state to h, u (and *d), which
+ * are valid after lts_ensemble_sync and must stay allocated until then;
+ * pinned memory overlaps the copies with
+ * later work.  lts_ensemble_sync waits for the ensemble and every member,
+ * and returns LTS_ENONFINITE as lts_ensemble_read does.  Keep host buffers
+ * that a later lts_ensemble_write reads unchanged until the sync. */
+int lts_ensemble_read_async(lts_ensemble e, int32_t i, double* h, double* u, lts_diag* d);
+int lts_ensemble_sync(lts_ensemble e);
+
 /* Replaces member i's state (original order, FP64 host arrays, as
  * lts_write) inside the ensemble, e.g. to restart one member; `time` and
- * `steps` set that member's clock.  Synchronises the member's stream. */
+ * `steps` set that member's clock.  Enqueued: the ensemble's stream waits
+ * for the member's copy (an event, no host synchronisation); from pinned
+ * memory the caller keeps h and u unchanged until the next
+ * lts_ensemble_read. */
 int lts_ensemble_write(lts_ensemble e, int32_t i, const double* h, const double* u, double time,
                        int64_t steps);
 

@@ -58,12 +58,20 @@ struct lts_ensemble_s {
     bool own_stream = false;
     cudaStream_t capture_stream = nullptr, capture_side = nullptr, side_stream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // member I/O is ordered against the ensemble's stream by events, not by
+    // host synchronisation; the shared error flag is read into pinned memory
+    cudaEvent_t ev_io = nullptr;
+    int* flag_host = nullptr;
     int parity = 0;
     int64_t steps = 0;
     int launches = 0;
     int segments = 0;
     double bytes[NKINDS] = {};
     ~lts_ensemble_s() {
+        // a caller's stream may already be gone: only the library's own is
+        // waited for (every flag copy into pinned memory completes inside
+        // the lts_ensemble_read that issued it)
+        if (own_stream && stream) cudaStreamSynchronize(stream);
         for (auto& e : exec)
             if (e) cudaGraphExecDestroy(e);
         if (own_stream && stream) cudaStreamDestroy(stream);
@@ -72,6 +80,8 @@ struct lts_ensemble_s {
         if (side_stream) cudaStreamDestroy(side_stream);
         if (ev_fork) cudaEventDestroy(ev_fork);
         if (ev_join) cudaEventDestroy(ev_join);
+        if (ev_io) cudaEventDestroy(ev_io);
+        if (flag_host) cudaFreeHost(flag_host);
     }
 };
 
@@ -562,6 +572,8 @@ int lts_ensemble_create(const lts_state* members, int32_t n, const lts_ensemble_
     CUDA_TRY(cudaStreamCreateWithFlags(&E->side_stream, cudaStreamNonBlocking));
     CUDA_TRY(cudaEventCreateWithFlags(&E->ev_fork, cudaEventDisableTiming));
     CUDA_TRY(cudaEventCreateWithFlags(&E->ev_join, cudaEventDisableTiming));
+    CUDA_TRY(cudaEventCreateWithFlags(&E->ev_io, cudaEventDisableTiming));
+    CUDA_TRY(cudaHostAlloc(reinterpret_cast<void**>(&E->flag_host), sizeof(int), cudaHostAllocDefault));
     // the members' current states become the packed state
     for (int m = 0; m < n; ++m) CUDA_TRY(cudaStreamSynchronize(E->members[m]->stream));
     for (int m = 0; m < n; ++m) {
@@ -604,16 +616,55 @@ int lts_ensemble_read(lts_ensemble e, int32_t i, double* h, double* u, lts_diag*
     if (i < 0 || i >= static_cast<int32_t>(e->members.size()))
         return set_error(LTS_EINVAL, "member index %d out of range", i);
     lts_state_s* S = e->members[i];
+    // unpack only after the member's previous gathers (an asynchronous read)
+    CUDA_TRY(cudaStreamWaitEvent(e->stream, S->ev_out_u, 0));
     int rc = copy_member(e, i, true);
     if (rc != LTS_OK) return rc;
-    int flag = 0;
-    CUDA_TRY(cudaMemcpyAsync(&flag, e->flag, sizeof(int), cudaMemcpyDeviceToHost, e->stream));
+    // the flag copy and the unpacking happen on the ensemble's stream; the
+    // member's read waits for them there and synchronises its own streams
+    CUDA_TRY(cudaMemcpyAsync(e->flag_host, e->flag, sizeof(int), cudaMemcpyDeviceToHost, e->stream));
     CUDA_TRY(cudaMemsetAsync(e->flag, 0, sizeof(int), e->stream));
-    CUDA_TRY(cudaStreamSynchronize(e->stream));
+    CUDA_TRY(cudaEventRecord(e->ev_io, e->stream));
+    CUDA_TRY(cudaStreamWaitEvent(S->stream, e->ev_io, 0));
     S->steps = e->steps0[i] + e->steps;
     S->time = e->t0[i] + static_cast<double>(e->steps) * S->p.dt;
     rc = lts_read(S, h, u, d);
     if (rc != LTS_OK) return rc;
+    const int flag = *e->flag_host;
+    if (flag & 4) return set_error(LTS_ECUDA, "internal error: a tile exceeded its shared memory (skipped)");
+    if (flag)
+        return set_error(LTS_ENONFINITE, "an ensemble stage produced %s",
+                         (flag & 1) ? "a thickness <= 0 or non-finite" : "a non-finite velocity");
+    return LTS_OK;
+}
+
+int lts_ensemble_read_async(lts_ensemble e, int32_t i, double* h, double* u, lts_diag* d) {
+    if (!e) return set_error(LTS_EINVAL, "null ensemble");
+    if (i < 0 || i >= static_cast<int32_t>(e->members.size()))
+        return set_error(LTS_EINVAL, "member index %d out of range", i);
+    lts_state_s* S = e->members[i];
+    CUDA_TRY(cudaStreamWaitEvent(e->stream, S->ev_out_u, 0));
+    int rc = copy_member(e, i, true);
+    if (rc != LTS_OK) return rc;
+    CUDA_TRY(cudaEventRecord(e->ev_io, e->stream));
+    CUDA_TRY(cudaStreamWaitEvent(S->stream, e->ev_io, 0));
+    S->steps = e->steps0[i] + e->steps;
+    S->time = e->t0[i] + static_cast<double>(e->steps) * S->p.dt;
+    return lts_read_async(S, h, u, d);
+}
+
+int lts_ensemble_sync(lts_ensemble e) {
+    if (!e) return set_error(LTS_EINVAL, "null ensemble");
+    CUDA_TRY(cudaMemcpyAsync(e->flag_host, e->flag, sizeof(int), cudaMemcpyDeviceToHost, e->stream));
+    CUDA_TRY(cudaMemsetAsync(e->flag, 0, sizeof(int), e->stream));
+    CUDA_TRY(cudaStreamSynchronize(e->stream));
+    int rc = LTS_OK;
+    for (lts_state_s* S : e->members) {
+        const int r = lts_sync(S);
+        if (r != LTS_OK && rc == LTS_OK) rc = r;
+    }
+    if (rc != LTS_OK) return rc;
+    const int flag = *e->flag_host;
     if (flag & 4) return set_error(LTS_ECUDA, "internal error: a tile exceeded its shared memory (skipped)");
     if (flag)
         return set_error(LTS_ENONFINITE, "an ensemble stage produced %s",
@@ -629,7 +680,9 @@ int lts_ensemble_write(lts_ensemble e, int32_t i, const double* h, const double*
     lts_state_s* S = e->members[i];
     int rc = lts_write(S, h, u, time, steps);
     if (rc != LTS_OK) return rc;
-    CUDA_TRY(cudaStreamSynchronize(S->stream));
+    // packing waits for the member's scatter on the ensemble's stream
+    CUDA_TRY(cudaEventRecord(e->ev_io, S->stream));
+    CUDA_TRY(cudaStreamWaitEvent(e->stream, e->ev_io, 0));
     rc = copy_member(e, i, false);
     if (rc != LTS_OK) return rc;
     // the member's clock restarts here; later reads add the ensemble's steps

@@ -1113,8 +1113,12 @@ double plan_launch_bytes(const LaunchDesc& d, const RegionsHost& r, int nC, int 
 
 lts_state_s::~lts_state_s() {
     // copies may still be in flight into pinned or caller memory: finish them
-    // before anything they use is released
-    for (cudaStream_t st : {stream, side_stream, h2d_stream, d2h_stream, diag_stream})
+    // before anything they use is released.  Only the library's own streams
+    // are waited for (a caller's stream may already be gone); the copy
+    // streams wait on the caller's stream through events, and the device
+    // buffers are freed by calls that synchronise.
+    if (own_stream && stream) cudaStreamSynchronize(stream);
+    for (cudaStream_t st : {side_stream, h2d_stream, d2h_stream, diag_stream})
         if (st) cudaStreamSynchronize(st);
     for (auto& e : exec)
         if (e) cudaGraphExecDestroy(e);

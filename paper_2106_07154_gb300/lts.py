@@ -179,6 +179,9 @@ def lib():
             L.lts_ensemble_destroy.argtypes = [C.c_void_p]
             L.lts_ensemble_destroy.restype = None
             L.lts_ensemble_step.argtypes = [C.c_void_p, C.c_int32]
+            L.lts_ensemble_read_async.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
+                                                  C.POINTER(lts_diag)]
+            L.lts_ensemble_sync.argtypes = [C.c_void_p]
             L.lts_ensemble_read.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
                                             C.POINTER(lts_diag)]
             L.lts_ensemble_write.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
@@ -419,7 +422,8 @@ def _ptr(a):
 def lts_read_async(state_h, h_out=None, u_out=None, diag: bool = False):
     """Enqueues the copy of the state into h_out / u_out (float64 arrays the
     caller keeps alive; pinned for overlap).  Returns the lts_diag that the
-    next lts_sync fills (None without diagnostics)."""
+    next lts_sync fills (None without diagnostics); the caller keeps it alive
+    until then (Model.read_async does)."""
     d = lts_diag() if diag else None
     _check(lib().lts_read_async(state_h, _ptr(h_out), _ptr(u_out), C.byref(d) if d is not None else None))
     return d
@@ -472,6 +476,20 @@ def lts_ensemble_read(ens_h, i: int, nCells: int, nEdges: int, h_out=None, u_out
     return h, u, {"mass": d.mass, "energy": d.energy, "time": d.time, "steps": d.steps}
 
 
+def lts_ensemble_read_async(ens_h, i: int, h_out=None, u_out=None, diag: bool = False):
+    """Enqueues member i's copy into h_out / u_out (float64 arrays the caller
+    keeps alive); returns the lts_diag the next lts_ensemble_sync fills, which
+    the caller keeps alive until then (Ensemble.read_async does)."""
+    d = lts_diag() if diag else None
+    _check(lib().lts_ensemble_read_async(ens_h, int(i), _ptr(h_out), _ptr(u_out),
+                                         C.byref(d) if d is not None else None))
+    return d
+
+
+def lts_ensemble_sync(ens_h):
+    _check(lib().lts_ensemble_sync(ens_h))
+
+
 def lts_ensemble_write(ens_h, i: int, h, u, time: float = 0.0, steps: int = 0):
     _check(lib().lts_ensemble_write(ens_h, int(i), _f64(h).ctypes.data, _f64(u).ctypes.data,
                                     float(time), int(steps)))
@@ -493,6 +511,7 @@ class Ensemble:
     def __init__(self, models, use_graph: bool = True, pdl: bool = True, persistent: bool = True,
                  stream: int | None = None):
         self.models = list(models)
+        self._pending = []
         self.h = None
         self.h = lts_ensemble_create([m.state_h for m in self.models], use_graph, pdl, persistent,
                                      stream)
@@ -506,6 +525,26 @@ class Ensemble:
 
     def write(self, i: int, h, u, time=0.0, steps=0):
         lts_ensemble_write(self.h, i, h, u, time, steps)
+
+    def read_async(self, i: int, h_out=None, u_out=None, diag: bool = False):
+        """Enqueues member i's copy; h_out, u_out (and the returned record)
+        are valid after sync()."""
+        m = self.models[i]
+        if h_out is not None and h_out.size != m.nC:
+            raise ValueError("h_out must hold nCells values")
+        if u_out is not None and u_out.size != m.nE:
+            raise ValueError("u_out must hold nEdges values")
+        d = lts_ensemble_read_async(self.h, i, h_out, u_out, diag)
+        if d is not None:
+            self._pending.append(d)   # the library writes it at the sync: keep it alive
+        return d
+
+    def sync(self):
+        """Waits for the ensemble and its members; returns the diagnostics of
+        the asynchronous reads since the last sync, in order."""
+        pending, self._pending = self._pending, []
+        lts_ensemble_sync(self.h)
+        return [{"mass": d.mass, "energy": d.energy, "time": d.time, "steps": d.steps} for d in pending]
 
     def stats(self):
         return lts_ensemble_stats(self.h)

@@ -130,3 +130,85 @@ def test_ensemble_write_restarts_one_member(members):
         assert d0["steps"] == 5
     for m in ms:
         m.close()
+
+
+def test_ensemble_pinned_round_trips(members):
+    """Every member written from pinned memory, stepped, read back into the
+    same buffers and written again (I/O is ordered by events, not host
+    synchronisation): the results equal the standalone runs bit for bit."""
+    torch = pytest.importorskip("torch")
+    ref2 = alone(members, lts.LTS_FP64, 2)
+    ref3 = alone(members, lts.LTS_FP64, 3)
+    bufs = []
+    for w in members:
+        hb = torch.empty(w.nCells, dtype=torch.float64, pin_memory=True).numpy()
+        ub = torch.empty(int(w.mesh["nEdges"]), dtype=torch.float64, pin_memory=True).numpy()
+        hb[:] = w.h0
+        ub[:] = w.u0
+        bufs.append((hb, ub))
+    ms = models(members, lts.LTS_FP64)
+    with lts.Ensemble(ms) as e:
+        e.step(4)                                # state to be replaced
+        for i, (hb, ub) in enumerate(bufs):
+            e.write(i, hb, ub, 0.0, 0)
+        e.step(2)
+        for i, (hb, ub) in enumerate(bufs):
+            e.read(i, hb, ub)
+            assert np.array_equal(hb, ref2[i][0]) and np.array_equal(ub, ref2[i][1]), i
+        for i, (hb, ub) in enumerate(bufs):
+            e.write(i, hb, ub, 0.0, 2)
+        e.step(1)
+        for i, (hb, ub) in enumerate(bufs):
+            e.read(i, hb, ub)
+            assert np.array_equal(hb, ref3[i][0]) and np.array_equal(ub, ref3[i][1]), i
+    for m in ms:
+        m.close()
+
+
+def test_ensemble_async_reads(members):
+    """lts_ensemble_read_async + lts_ensemble_sync: each read sees its member
+    as it stood when the read was enqueued, even when the same member is
+    read again after more steps before the sync; the values and diagnostics
+    equal synchronous reads bit for bit."""
+    torch = pytest.importorskip("torch")
+    ms = models(members, lts.LTS_FP64)
+    ref = alone(members, lts.LTS_FP64, 2)
+    ref3 = alone(members, lts.LTS_FP64, 3)
+    pin = lambda n: torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
+    with lts.Ensemble(ms) as e:
+        e.step(2)
+        outs, diags = [], []
+        for i, w in enumerate(members):
+            hb, ub = pin(w.nCells), pin(int(w.mesh["nEdges"]))
+            diags.append(e.read_async(i, hb, ub, diag=True))
+            outs.append((hb, ub))
+        e.step(1)
+        h3, u3 = pin(members[0].nCells), pin(int(members[0].mesh["nEdges"]))
+        e.read_async(0, h3, u3)
+        e.sync()
+        for i in range(len(members)):
+            assert np.array_equal(outs[i][0], ref[i][0]) and np.array_equal(outs[i][1], ref[i][1]), i
+            assert diags[i].mass == ref[i][2]["mass"] and diags[i].energy == ref[i][2]["energy"]
+            assert diags[i].steps == 2
+        assert np.array_equal(h3, ref3[0][0]) and np.array_equal(u3, ref3[0][1])
+    for m in ms:
+        m.close()
+
+
+def test_ensemble_async_diagnostics_kept_by_the_binding(members):
+    """The binding keeps each asynchronous read's diagnostics record alive
+    until the sync (the library writes it then), so a caller may drop it."""
+    ms = models(members, lts.LTS_FP64)
+    ref = alone(members, lts.LTS_FP64, 1)
+    with lts.Ensemble(ms) as e:
+        e.step(1)
+        for i in range(len(members)):
+            e.read_async(i, diag=True)        # return value dropped
+        import gc
+        gc.collect()
+        ds = e.sync()
+        assert len(ds) == len(members)
+        for i, d in enumerate(ds):
+            assert d["mass"] == ref[i][2]["mass"] and d["energy"] == ref[i][2]["energy"], i
+    for m in ms:
+        m.close()

@@ -132,3 +132,16 @@ def test_snapshot_diagnostics_equal_state_diagnostics(sphw, precision):
         _, _, d = m.read()
         got = out.cpu().numpy()
     assert got[0] == d["mass"] and got[1] == d["energy"]
+
+
+def test_async_diagnostics_kept_by_the_binding(sphw):
+    """Model.read_async keeps the diagnostics record alive until sync()."""
+    with model(sphw, lts.LTS_FP64) as m:
+        m.step(2)
+        _, _, ref = m.read()
+        for _ in range(3):
+            m.read_async(diag=True)           # return value dropped
+        import gc
+        gc.collect()
+        ds = m.sync()
+    assert len(ds) == 3 and all(d["mass"] == ref["mass"] and d["energy"] == ref["energy"] for d in ds)
