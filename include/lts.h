@@ -208,8 +208,8 @@ int lts_regions_permutation(lts_regions r, int32_t* perm_cell, int32_t* perm_edg
 #define LTS_MODE_SSPRK3 1   /* Algorithm 2.1 (SSPRK3) on the whole mesh, step dt    */
 #define LTS_MODE_SSPRK2 2   /* Algorithm 2.1 (SSPRK2) on the whole mesh, step dt    */
 
-#define LTS_COARSE_STEP4  0
-#define LTS_COARSE_FAR    1
+#define LTS_COARSE_FAR    0   /* the default */
+#define LTS_COARSE_STEP4  1
 #define LTS_COARSE_SERIAL 2
 
 typedef struct lts_params {
@@ -246,12 +246,12 @@ typedef struct lts_params {
                                SM (fewer registers, some spills), leaving block slots
                                for the next launch's table prefetch                   */
     int32_t coarse_schedule;/* order of the coarse phases (results are identical):
-                               LTS_COARSE_STEP4 (default): Step 4 on the coarse bands
-                               C3 and beyond runs as a concurrent graph branch beside
-                               Step 3; LTS_COARSE_FAR: Steps 1, 2 and 4 on the far
+                               LTS_COARSE_FAR (default): Steps 1, 2 and 4 on the far
                                coarse bands (C5+ for Step 1, C3+ for Steps 2 and 4)
-                               form that branch; LTS_COARSE_SERIAL: step order on one
-                               stream                                                  */
+                               run as a concurrent graph branch beside Step 3 (LTS2
+                               and the fused path: Step 4 / the last coarse stage
+                               only); LTS_COARSE_STEP4: only Step 4 on C3+ forms that
+                               branch; LTS_COARSE_SERIAL: step order on one stream     */
     int32_t elems_per_thread;/* vertex and edge launches of single-layer states on the
                                three-launch path: 1 or 2 elements per thread (2: half
                                the blocks, both elements' loads in flight together);
@@ -276,7 +276,7 @@ int lts_step(lts_state s, int32_t n_coarse);
  * fastest as *best (base's g, dt, precision, mode, compensation and stream
  * kept; use_graph = 1).  Candidates: block_size 128 or 256, kernel_path 0
  * or 1, pdl on or off, L2 hints on or off, the coarse schedule (LTS3:
- * LTS_COARSE_STEP4, _FAR or _SERIAL).  Each is timed over `steps` coarse
+ * LTS_COARSE_FAR, _STEP4 or _SERIAL; LTS2: _FAR or _SERIAL).  Each is timed over `steps` coarse
  * steps after 3 warm-up steps; the three fastest are timed twice more and
  * the best of three wins.  With the winner, FP32 states also try the ring
  * occupancy variants 6 and 8, and single-region single-layer states the

@@ -86,18 +86,21 @@ extern "C" int lts_autotune(lts_mesh m, lts_regions r, const double* h0, const d
     const bool lts = base->mode == LTS_MODE_LTS;
     const bool fused_ok = base->mode == LTS_MODE_SSPRK3 || lts3;
     // three-launch path: every combination; fused tiles (one block per
-    // 256-cell tile): with PDL, without the FAR schedule
+    // 256-cell tile): with PDL, concurrent (the fused plans branch Step 4
+    // only) or serial
+    // coarse schedules: LTS2 has no far Steps 1/2 (its FAR is the Step-4
+    // branch), the global SSP-RK modes have no coarse phases at all
+    std::vector<int> scheds = {LTS_COARSE_FAR};
+    if (lts3) scheds = {LTS_COARSE_FAR, LTS_COARSE_STEP4, LTS_COARSE_SERIAL};
+    else if (lts) scheds = {LTS_COARSE_FAR, LTS_COARSE_SERIAL};
     for (int block : {128, 256})
         for (int pdl = 1; pdl >= 0; --pdl)
             for (int no_l2 = 0; no_l2 <= 1; ++no_l2)
-                for (int sched = 0; sched <= (lts ? 2 : 0); ++sched) {
-                    if (sched == LTS_COARSE_FAR && !lts3) continue;   // LTS2: no far Steps 1/2
-                    cands.push_back({block, 0, pdl, no_l2, sched});
-                }
+                for (int sched : scheds) cands.push_back({block, 0, pdl, no_l2, sched});
     if (fused_ok)
         for (int no_l2 = 0; no_l2 <= 1; ++no_l2)
-            for (int sched : {LTS_COARSE_STEP4, LTS_COARSE_SERIAL})
-                if (lts3 || sched == LTS_COARSE_STEP4) cands.push_back({256, 1, 1, no_l2, sched});
+            for (int sched : {LTS_COARSE_FAR, LTS_COARSE_SERIAL})
+                if (lts3 || sched == LTS_COARSE_FAR) cands.push_back({256, 1, 1, no_l2, sched});
     // every candidate once, then the three fastest twice more (best of three)
     for (Candidate& c : cands) {
         int rc = time_config(m, r, h0, u0, apply(*base, c), steps, &c.ms);
@@ -121,7 +124,7 @@ extern "C" int lts_autotune(lts_mesh m, lts_regions r, const double* h0, const d
     if (!std::isfinite(win->ms)) return set_error(LTS_EINVAL, "no configuration could be built");
     double default_ms = INFINITY;
     for (const Candidate& c : cands)
-        if (c.block == 256 && c.path == 0 && c.pdl == 1 && c.no_l2 == 0 && c.serial == LTS_COARSE_STEP4)
+        if (c.block == 256 && c.path == 0 && c.pdl == 1 && c.no_l2 == 0 && c.serial == LTS_COARSE_FAR)
             default_ms = c.ms;
     // the FP32 ring-pass occupancy variants with the winning configuration;
     // layered and multi-region states launch other kernels, so they have none

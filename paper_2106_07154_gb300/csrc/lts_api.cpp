@@ -1444,8 +1444,8 @@ int lts_state_create(lts_mesh mesh, lts_regions reg, const double* h0, const dou
         static_cast<long long>(mesh->m.nE) * layers > 0x7fffffffLL ||
         static_cast<long long>(slot_rows(mesh->m.maxE)) * mesh->m.nC > 0x7fffffffLL)
         return set_error(LTS_EINVAL, "mesh x layers too large");
-    if (p->coarse_schedule < LTS_COARSE_STEP4 || p->coarse_schedule > LTS_COARSE_SERIAL)
-        return set_error(LTS_EINVAL, "coarse_schedule must be LTS_COARSE_STEP4, _FAR or _SERIAL");
+    if (p->coarse_schedule < LTS_COARSE_FAR || p->coarse_schedule > LTS_COARSE_SERIAL)
+        return set_error(LTS_EINVAL, "coarse_schedule must be LTS_COARSE_FAR, _STEP4 or _SERIAL");
     if (p->kernel_path != 0 && p->kernel_path != 1)
         return set_error(LTS_EINVAL, "kernel_path must be 0 (three launches) or 1 (fused tiles)");
     {

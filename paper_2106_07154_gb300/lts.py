@@ -34,8 +34,8 @@ PATH_FUSED = 1
 LTS_ORDER_HILBERT = 0
 LTS_ORDER_INDEX = 1
 LTS_TUNE_ORDERING = 1
-LTS_COARSE_STEP4 = 0
-LTS_COARSE_FAR = 1
+LTS_COARSE_FAR = 0      # the default
+LTS_COARSE_STEP4 = 1
 LTS_COARSE_SERIAL = 2
 
 NBANDS = 12
