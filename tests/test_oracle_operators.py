@@ -1,7 +1,9 @@
 """Pins of the oracle's TRiSK operators (Appendix B) against what the
 mathematics fixes: closed forms on regular hexagons, antisymmetry of the
 weights, discrete adjointness, curl of a gradient, energy neutrality of the
-potential-vorticity flux, the lake at rest, and the sign of the vorticity."""
+potential-vorticity flux, the lake at rest, the sign of the vorticity, and the
+energy diagnostic (a closed form and the conservation the semi-discrete
+system has)."""
 import math
 
 import numpy as np
@@ -166,3 +168,53 @@ def test_geostrophic_balance_pv_vs_gradient():
     # ... whereas the PV flux with the opposite sign would double the tendency
     assert np.abs(U + 2 * pv).max() > 1.5 * np.abs(g_term).max()
     assert np.abs(H).max() * 3600 < 5.0    # < 5 m/hour thickness tendency
+
+
+@pytest.mark.parametrize("bottom", [0.0, 250.0])
+def test_energy_uniform_flow_closed_form(hexm, bottom):
+    """Energy (reading R8) of a uniform flow U at constant thickness h over a
+    constant bottom b on regular hexagons: K = |U|^2/2 in every cell, so
+    E = (total area) h (|U|^2/2 + g (h/2 + b)), a single number the per-cell
+    sum must reproduce.  A missing 1/2, a wrong g or a wrong area weighting
+    fails it."""
+    m = dict(hexm)
+    m["bottom"] = np.full(hexm["nCells"], bottom)
+    o = oracle.Oracle(m)
+    nrm = _normals_plane(hexm)
+    U = np.array([3.0, -4.0])
+    h0, g = 800.0, 9.81
+    area = hexm["period_x"] * hexm["period_y"]
+    assert abs(np.sum(hexm["areaCell"]) - area) < 1e-9 * area
+    E = o.energy(np.full(hexm["nCells"], h0), nrm @ U, g)
+    exact = area * h0 * (0.5 * 25.0 + g * (0.5 * h0 + bottom))
+    assert abs(E - exact) < 1e-13 * exact
+
+
+def test_energy_conserved_along_the_flow(sph):
+    """The TRiSK system of Eq. (1) conserves the energy of reading R8 in
+    continuous time (Appendix B: the PV flux does no work and the divergence
+    is the negative adjoint of the gradient).  So the derivative of the
+    oracle's energy along its own right-hand side, taken by a centred
+    difference, vanishes relative to the rate at which potential and kinetic
+    energy trade.  Negative controls: doubling K or the g h term in the
+    energy breaks it by orders of magnitude."""
+    o = oracle.Oracle(sph)
+    rng = np.random.default_rng(5)
+    b = sph["bottom"]
+    h = 5000.0 - b + rng.uniform(-20.0, 20.0, sph["nCells"])
+    u = rng.normal(0.0, 10.0, sph["nEdges"])
+    g = 9.81
+    H, U = o.rhs(h, u, g)
+    A = sph["areaCell"]
+    # the rate of exchange between the two energy forms (the scale)
+    exchange = abs(np.sum(A * (o.kinetic(u) + g * (h + b)) * H))
+    eps = 1.0
+
+    def ddt(energy):
+        return (energy(h + eps * H, u + eps * U) - energy(h - eps * H, u - eps * U)) / (2 * eps)
+
+    assert abs(ddt(lambda hh, uu: o.energy(hh, uu, g))) < 1e-6 * exchange
+    twice_k = lambda hh, uu: np.sum(A * hh * (2.0 * o.kinetic(uu) + g * (0.5 * hh + b)))
+    full_gh = lambda hh, uu: np.sum(A * hh * (o.kinetic(uu) + g * (hh + b)))
+    assert abs(ddt(twice_k)) > 0.1 * exchange
+    assert abs(ddt(full_gh)) > 0.1 * exchange
