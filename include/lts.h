@@ -103,7 +103,8 @@ int lts_build_hex_periodic(int32_t nx, int32_t ny, double dc, double f0,
                            lts_mesh_desc* out);
 
 /* Spherical centroidal Voronoi tessellation (SCVT) with n generators on a
- * sphere of `radius`, made by `lloyd_iters` Lloyd iterations from a seeded
+ * sphere of `radius` (the variable-resolution SCVT meshes of the test cases
+ * in Section 3, which the paper takes from MPAS; seeded stand-ins here), made by `lloyd_iters` Lloyd iterations from a seeded
  * random start drawn with point density rho^(1/2) (rho from `rho`, NULL =
  * uniform).  Voronoi vertices are circumcentres of the spherical Delaunay
  * triangles; kite areas are signed spherical areas of (x_i, x_e1, x_v, x_e2);
@@ -112,7 +113,8 @@ int lts_build_hex_periodic(int32_t nx, int32_t ny, double dc, double f0,
 int lts_build_scvt(int64_t n, uint64_t seed, const lts_density* rho,
                    int32_t lloyd_iters, double radius, lts_mesh_desc* out);
 
-/* Frees the arrays a builder allocated and zeroes the struct. */
+/* Frees the arrays a builder allocated and zeroes the struct (memory
+ * management; the paper has no counterpart). */
 void lts_mesh_desc_free(lts_mesh_desc* d);
 
 /* ------------------------------------------------------------------------
@@ -122,8 +124,9 @@ typedef struct lts_mesh_s* lts_mesh;
 typedef struct lts_regions_s* lts_regions;
 typedef struct lts_state_s* lts_state;
 
-/* Validates and copies the mesh (FP64 master copies stay on the host until
- * regions are set).  Checks index ranges, orientation consistency, positive
+/* Validates and copies the mesh of Appendix B (its arrays, the orientation
+ * rule of its Remark, and the weights of its Eq. (weights)); the FP64
+ * master copies stay on the host until regions are set.  Checks index ranges, orientation consistency, positive
  * areas and lengths, kite sums (sum over a cell = A_i, over a vertex = A_v,
  * relative 1e-9) and, if given, weightsOnEdge against the kite-derived
  * weights (absolute 1e-9).  Errors: LTS_EINVAL, LTS_ENOMEM. */
@@ -168,18 +171,22 @@ int lts_regions_set_multi(lts_mesh m, const int8_t* region_of_cell, int32_t nreg
                           const int32_t* M, int32_t order, int32_t interface_layers,
                           lts_regions* out);
 
-/* Region labels in the caller's original order (host arrays):
+/* Region labels of Eqs. (3)-(5) in the caller's original order (host
+ * arrays):
  *   cell_label [nCells]: 0 F \ Fbar, 1 F2, 2 F1, 3 I1, 4 I2, 5 C
  *   edge_label [nEdges]: 0 F^e, 1 Fbar^e, 3 I1^e, 4 I2^e, 5 C^e
  * Either pointer may be NULL. */
 int lts_regions_labels(lts_regions r, int8_t* cell_label, int8_t* edge_label);
 
 /* Re-tiles the regions for the fused kernel (kernel_path = 1): tiles of at
- * most tile_cells consecutive band-order cells (32..4096; default 256).
+ * most tile_cells consecutive band-order cells (32..4096; default 256).  A
+ * GPU layout choice; the paper has no counterpart.
  * Only while no state uses the regions.  Errors: LTS_EINVAL. */
 int lts_regions_tiling(lts_regions r, int32_t tile_cells);
 
-/* Order of the cells inside each band (the bands themselves are fixed):
+/* Order of the cells inside each band (the bands themselves are fixed; a
+ * memory layout choice that replaces the paper's METIS partitioning of
+ * Section 3.1, so the paper has no counterpart):
  *   LTS_ORDER_HILBERT (default): along a Hilbert curve through the cell
  *     centres, so neighbours sit close in memory;
  *   LTS_ORDER_INDEX: the mesh's own index order (the naive layout, for
@@ -192,11 +199,13 @@ int lts_regions_tiling(lts_regions r, int32_t tile_cells);
 #define LTS_ORDER_INDEX   1
 int lts_regions_ordering(lts_regions r, int32_t ordering);
 
-/* Number of cells, edges and vertices per band (arrays of LTS_NBANDS). */
+/* Number of cells, edges and vertices per band (arrays of LTS_NBANDS): the
+ * sizes of the index sets of Eqs. (3)-(5) split by band. */
 #define LTS_NBANDS 12
 int lts_regions_counts(lts_regions r, int64_t* cells, int64_t* edges, int64_t* vertices);
 
-/* Band-order permutations: perm_cell[new] = original index (any may be NULL). */
+/* Band-order permutations: perm_cell[new] = original index (any may be
+ * NULL).  A memory layout; the paper has no counterpart. */
 int lts_regions_permutation(lts_regions r, int32_t* perm_cell, int32_t* perm_edge,
                             int32_t* perm_vertex);
 
@@ -258,8 +267,10 @@ typedef struct lts_params {
                                0 = library default.  Results are identical.            */
 } lts_params;
 
-/* Allocates the device state (band order) and uploads (h0, u0), given in the
- * caller's original order ([nCells], [nEdges], FP64 host arrays).  Captures
+/* Allocates the device state (band order) and uploads (h0, u0), the
+ * thickness and normal velocity of Eq. (1), given in the caller's original
+ * order ([nCells], [nEdges], FP64 host arrays), for the integrator p->mode
+ * selects (Algorithm 2.2, or Algorithm 2.1 on the whole mesh).  Captures
  * the CUDA graphs of one coarse step when use_graph = 1 (so create the state
  * outside any stream capture).  Errors: LTS_EINVAL (dt <= 0, g <= 0, bad
  * precision/mode), LTS_ENOMEM, LTS_ECUDA. */
@@ -267,8 +278,12 @@ int lts_state_create(lts_mesh m, lts_regions r, const double* h0, const double* 
                      const lts_params* p, lts_state* out);
 void lts_state_destroy(lts_state s);
 
-/* Enqueues n_coarse coarse steps (LTS3) or steps (SSPRK3) on the state's
- * stream.  Asynchronous: returns after enqueueing.  n_coarse >= 0. */
+/* Enqueues n_coarse coarse steps (Algorithm 2.2, Steps 1-5, with the
+ * regions' M fine substeps in Step 3; its LTS2 branches for order-2 regions)
+ * or steps (Algorithm 2.1: SSPRK3 or SSPRK2) on the state's stream.  Every
+ * stage evaluates the right-hand side of Eq. (1) with the operators of
+ * Appendix B on the sets the step names.  Asynchronous: returns after
+ * enqueueing.  n_coarse >= 0. */
 int lts_step(lts_state s, int32_t n_coarse);
 
 /* Autotuner: times candidate launch configurations of one coarse step on
@@ -312,15 +327,15 @@ typedef struct lts_diag {
     int64_t steps;          /* coarse steps taken                                                  */
 } lts_diag;
 
-/* Synchronises the state's stream and copies the state to the caller in the
- * original order and orientation (h [nCells], u [nEdges], FP64; either may
+/* Synchronises the state's stream and copies the state (h, u) of Eq. (1)
+ * to the caller in the original order and orientation (h [nCells], u [nEdges], FP64; either may
  * be NULL), plus diagnostics (d may be NULL).  Returns LTS_ENONFINITE if any
  * stage produced a thickness <= 0 or a non-finite value since the last read
  * or lts_sync.  Equivalent to lts_read_async followed by lts_sync. */
 int lts_read(lts_state s, double* h, double* u, lts_diag* d);
 
 /* Replaces the state (original order, FP64 host arrays), e.g. to resume from
- * a saved lts_read; `time`/`steps` set the clock.  Enqueued: the copies run
+ * a saved lts_read (checkpoint and restart; the paper has no counterpart); `time`/`steps` set the clock.  Enqueued: the copies run
  * on a host-to-device stream of the state as soon as the previous write's
  * staging is free (they may overlap coarse steps enqueued earlier), and the
  * state is replaced in stream order.  From pageable memory the call returns
@@ -343,7 +358,8 @@ int lts_write(lts_state s, const double* h, const double* u, double time, int64_
 int lts_read_async(lts_state s, double* h, double* u, lts_diag* d);
 int lts_sync(lts_state s);
 
-/* Launch statistics of one coarse step: number of kernel launches, and per
+/* Launch statistics of one coarse step (measurement; the paper has no
+ * counterpart): number of kernel launches, and per
  * launch kind k (0 = vertex PV, 1 = cell ring pass with the thickness
  * update, 2 = edge pass with the velocity update, 3 = fused tile kernel
  * doing all three for a tile) the algorithmic bytes
@@ -355,21 +371,23 @@ int lts_step_stats(lts_state s, int32_t* launches_per_step, double* bytes, doubl
                    int32_t* launches_per_kind);
 
 /* Mass and energy of the current state (the FP64 reduction lts_read
- * performs), for callers that cannot allocate device memory when they need
- * them, e.g. while a stream is being captured into a CUDA graph, or when
- * device memory comes from a pool that must not grow.  The paper has no
- * counterpart; this is an interface convenience.
+ * performs, with the same blocking, so the sums agree to the last bit), for
+ * callers that cannot allocate device memory when they need them: hosts
+ * whose device memory comes from a fixed pool that must not grow, or time
+ * loops that forbid allocation because cudaMalloc may synchronise the
+ * device.  The paper has no counterpart; this is an interface convenience.
  *   d_out: device memory owned by the caller, 2 doubles: {mass, energy}.
  * Allocates nothing: the per-block partial sums live in one fixed device
  * array of 4096 x 2 doubles (64 KiB) inside liblts.so, which every GPU that
- * loads the library keeps until the process exits; meshes of more than
- * 4096 * 256 = 1,048,576 cells are rejected with LTS_EINVAL.  The first call
- * on a device looks the array's address up (cudaGetSymbolAddress), so make
- * that first call before any stream capture.  Enqueued on the state's
- * stream, no synchronisation.  All calls share the array, and every call
- * overwrites the partial sums it reads, so calls that overlap on the GPU
- * (different streams, unordered) race and must not be issued.
- * Errors: LTS_EINVAL (null argument, mesh too large, state on another
+ * loads the library keeps until the process exits; states of more than
+ * 4096 * 256 = 1,048,576 cells x layers are rejected with LTS_EINVAL before
+ * anything is enqueued.  The first call on a device looks the array's
+ * address up (cudaGetSymbolAddress), so make that first call before any
+ * stream capture.  Enqueued on the state's stream, no synchronisation.  All
+ * calls share the array, and every call overwrites the partial sums it
+ * reads, so calls that overlap on the GPU (different streams, unordered)
+ * race and must not be issued.
+ * Errors: LTS_EINVAL (null argument, state too large, state on another
  * device), LTS_ECUDA. */
 int lts_diagnostics_noalloc(lts_state s, double* d_out);
 
@@ -395,7 +413,7 @@ typedef struct lts_ensemble_params {
     void* stream;           /* cudaStream_t to enqueue on; NULL = a library stream     */
 } lts_ensemble_params;
 
-/* Builds an ensemble of n >= 1 distinct states that live on the current
+/* Builds an ensemble (the paper has no counterpart) of n >= 1 distinct states that live on the current
  * device and share precision, compensation, mode, g, block size and
  * kernel_path 0.  Copies each member's current state in (the members'
  * streams are synchronised first).  p may be NULL (graph, PDL, persistent).
@@ -408,16 +426,19 @@ int lts_ensemble_create(const lts_state* members, int32_t n, const lts_ensemble_
 void lts_ensemble_destroy(lts_ensemble e);
 
 /* Enqueues n_coarse coarse steps of every member (each with its own dt and
- * M) on the ensemble's stream; asynchronous.  n_coarse >= 0. */
+ * M; Algorithm 2.2 or 2.1 per member, as lts_step) on the ensemble's
+ * stream; asynchronous.  n_coarse >= 0. */
 int lts_ensemble_step(lts_ensemble e, int32_t n_coarse);
 
-/* Copies member i's packed state into the member (its clock advanced by
+/* Ensemble I/O (the paper has no counterpart).
+ * Copies member i's packed state into the member (its clock advanced by
  * the ensemble's steps), then behaves as lts_read on that member.  Returns
  * LTS_ENONFINITE if any member produced a thickness <= 0 or a non-finite
  * value since the last ensemble read (the flag is shared by all members). */
 int lts_ensemble_read(lts_ensemble e, int32_t i, double* h, double* u, lts_diag* d);
 
-/* Asynchronous member read (as lts_read_async on the member): enqueues the
+/* Asynchronous member read (as lts_read_async on the member; the paper has
+ * no counterpart): enqueues the
  * unpacking of member i and the copy of its state to h, u (and *d), which
  * are valid after lts_ensemble_sync and must stay allocated until then;
  * pinned memory overlaps the copies with
@@ -428,7 +449,7 @@ int lts_ensemble_read_async(lts_ensemble e, int32_t i, double* h, double* u, lts
 int lts_ensemble_sync(lts_ensemble e);
 
 /* Replaces member i's state (original order, FP64 host arrays, as
- * lts_write) inside the ensemble, e.g. to restart one member; `time` and
+ * lts_write; the paper has no counterpart) inside the ensemble, e.g. to restart one member; `time` and
  * `steps` set that member's clock.  Enqueued: the ensemble's stream waits
  * for the member's copy (an event, no host synchronisation); from pinned
  * memory the caller keeps h and u unchanged until the next
@@ -436,12 +457,15 @@ int lts_ensemble_sync(lts_ensemble e);
 int lts_ensemble_write(lts_ensemble e, int32_t i, const double* h, const double* u, double time,
                        int64_t steps);
 
-/* Launches and segment records per ensemble coarse step, algorithmic bytes
+/* Launches and segment records per ensemble coarse step (measurement; the
+ * paper has no counterpart), algorithmic bytes
  * per launch kind (array of LTS_NKINDS, summed over members), and the total
  * number of cells.  Any pointer may be NULL. */
 int lts_ensemble_stats(lts_ensemble e, int32_t* launches_per_step, double* bytes, int64_t* cells,
                        int32_t* segments_per_step);
 
+/* Message of the calling thread's last failure (error reporting; the paper
+ * has no counterpart). */
 const char* lts_last_error(void);
 
 #ifdef __cplusplus

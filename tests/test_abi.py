@@ -179,3 +179,31 @@ def test_regions_multi_blocks_and_rejection():
             assert e.code == lts.LTS_EINVAL
     finally:
         lts.lts_mesh_destroy(mh)
+
+
+CITATION = re.compile(r"Eq\.|Eqs\.|Algorithm|Appendix|Section|Remark|no\s+(?:\*\s+)?counterpart")
+
+
+def declaration_comments():
+    """Each declared function with the comment block nearest above it (a
+    comment documents the declarations that follow it up to the next one)."""
+    text = HEADER.read_text()
+    out, last = {}, ""
+    # block comments that open a line (field comments inside structs do not)
+    for m in re.finditer(r"^/\*.*?\*/|^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*(lts_[a-z0-9_]+)\s*\(",
+                         text, re.S | re.M):
+        if m.group(0).lstrip().startswith("/*"):
+            last = m.group(0)
+        else:
+            out[m.group(1)] = last
+    return out
+
+
+def test_every_entry_point_cites_its_passage():
+    """Every function include/lts.h declares names the passage of the paper
+    it implements (equation, algorithm, section, appendix) or says that the
+    paper has no counterpart."""
+    docs = declaration_comments()
+    assert set(docs) == set(declared_functions())
+    missing = sorted(n for n, c in docs.items() if not CITATION.search(c))
+    assert not missing, missing
