@@ -58,10 +58,16 @@ struct DevArgs {
 };
 
 // ------------------------------------------------------------- L2 residency
-// The fine substeps revisit the same ~100 MB (fine-region tables and state)
-// 3M times per coarse step while the coarse-band launches stream the rest of
-// the mesh once; read-only loads carry an L2 eviction-priority policy so the
-// streamed data leaves L2 first.  Hints only: results do not depend on them.
+// The fine substeps revisit the fine region's mesh tables (~65 MB on a
+// 655k-cell mesh with an 8:1 cap) 3M times per coarse step, and again every
+// coarse step, while its state (~25 MB per right-hand side) is rewritten by
+// every stage and the coarse-band launches stream the rest of the mesh
+// once.  Loads and stores carry an L2 eviction-priority policy per launch
+// mode: fine launches (1) keep their tables (evict_last) and let their state
+// go first (evict_first); coarse launches (2) stream both (evict_first).
+// Measured on GB300, this beats keeping everything of the fine launches
+// (the fine working set as a whole is about as large as the L2 holds).
+// Hints only: results do not depend on them.
 __device__ __forceinline__ uint64_t l2_policy(int mode) {
     uint64_t p;
     if (mode == 1)
@@ -88,7 +94,26 @@ __device__ __forceinline__ uint64_t l2_policy(int mode) {
 #define LTS_R(x) "=r"(x)
 #define LTS_F(x) "=f"(x)
 #define LTS_D(x) "=d"(x)
+#define LTS_L(x) "=l"(x)
 LTS_LD_HINT(int, "b32", LTS_R)
+LTS_LD_HINT(unsigned long long, "b64", LTS_L)
+// State loads issued only where p holds (0 otherwise), as one predicated
+// instruction: the load goes out in the same wave as unconditional ones
+// instead of behind a branch.
+__device__ __forceinline__ float ld_state_if(bool p, const float* q, uint64_t pol) {
+    float x = 0.0f;
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t"
+                 "@q ld.global.nc.L2::cache_hint.f32 %0, [%1], %3;\n\t}"
+                 : "+f"(x) : "l"(q), "r"(static_cast<int>(p)), "l"(pol) : "memory");
+    return x;
+}
+__device__ __forceinline__ double ld_state_if(bool p, const double* q, uint64_t pol) {
+    double x = 0.0;
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t"
+                 "@q ld.global.nc.L2::cache_hint.f64 %0, [%1], %3;\n\t}"
+                 : "+d"(x) : "l"(q), "r"(static_cast<int>(p)), "l"(pol) : "memory");
+    return x;
+}
 LTS_LD_HINT(uint32_t, "b32", LTS_R)
 LTS_LD_HINT(float, "f32", LTS_F)
 LTS_LD_HINT(double, "f64", LTS_D)
@@ -97,15 +122,36 @@ __device__ __forceinline__ uint8_t ld_static(const uint8_t* q, uint64_t p) {
     asm("ld.global.nc.L2::cache_hint.u8 %0, [%1], %2;" : "=r"(x) : "l"(q), "l"(p));
     return static_cast<uint8_t>(x);
 }
+// Stores with an L2 eviction-priority policy: a launch's results carry the
+// priority of its state loads (see above).
+__device__ __forceinline__ void st_hint(float* q, float v, uint64_t p) {
+    asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(q), "f"(v), "l"(p) : "memory");
+}
+__device__ __forceinline__ void st_hint(double* q, double v, uint64_t p) {
+    asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(q), "d"(v), "l"(p) : "memory");
+}
+// Policy of a launch mode's state accesses (see above): the fine launches'
+// state goes first, like the coarse launches' data.
+__device__ __forceinline__ int state_mode(int m) { return m == 1 ? 2 : m; }
+
+struct St {
+    uint64_t pol;
+    __device__ __forceinline__ explicit St(int m) : pol(l2_policy(state_mode(m))) {}
+    template <class V>
+    __device__ __forceinline__ void operator()(V* q, V v) const { st_hint(q, v, pol); }
+};
+
 // Read-only loads with the launch's L2 policy: `stat` for mesh tables, `operator()`
 // for state written by earlier kernels (ordered after griddep_wait).
 struct Ld {
-    uint64_t pol;
-    __device__ __forceinline__ explicit Ld(int m) : pol(l2_policy(m)) {}
+    uint64_t pol, spol;   // tables, state
+    __device__ __forceinline__ explicit Ld(int m) : pol(l2_policy(m)), spol(l2_policy(state_mode(m))) {}
     template <class V>
     __device__ __forceinline__ V stat(const V* q) const { return ld_static(q, pol); }
     template <class V>
-    __device__ __forceinline__ V operator()(const V* q) const { return ld_state(q, pol); }
+    __device__ __forceinline__ V operator()(const V* q) const { return ld_state(q, spol); }
+    template <class V>
+    __device__ __forceinline__ V when(bool p, const V* q) const { return ld_state_if(p, q, spol); }
 };
 
 // ------------------------------------------------------------------ layers
@@ -255,12 +301,23 @@ __device__ __forceinline__ void vertex_stat(const Tables<T>& t, const Ld& ld, in
     s.f = ld.stat(t.f + v);
 }
 
+// q_v from the vertex's three edge velocities and cell thicknesses, with the
+// roundings spelled out, so every pass that forms q (vertex, vertex-edge,
+// fused tiles) gets the same bits.
+template <class T>
+__device__ __forceinline__ T q_value(T d0, T d1, T d2, T u0, T u1, T u2, T k0, T k1, T k2, T h0, T h1, T h2,
+                                     T f) {
+    const T zeta = fma_rn(d2, u2, fma_rn(d1, u1, mul_rn(d0, u0)));
+    const T hv = fma_rn(k2, h2, fma_rn(k1, h1, mul_rn(k0, h0)));
+    return (zeta + f) / hv;
+}
+
 // Gathers u and h (after the wait) and returns q_v.
 template <class T, bool LY>
 __device__ __forceinline__ T vertex_q(const DevArgs<T>& a, const Ld& ld, const VertStat<T>& s, const Lay<LY>& y) {
-    T zeta = s.d0 * ld(a.in_u + y(s.e0)) + s.d1 * ld(a.in_u + y(s.e1)) + s.d2 * ld(a.in_u + y(s.e2));
-    T hv = s.k0 * ld(a.in_h + y(s.c0)) + s.k1 * ld(a.in_h + y(s.c1)) + s.k2 * ld(a.in_h + y(s.c2));
-    return (zeta + s.f) / hv;
+    const T u0 = ld(a.in_u + y(s.e0)), u1 = ld(a.in_u + y(s.e1)), u2 = ld(a.in_u + y(s.e2));
+    const T h0 = ld(a.in_h + y(s.c0)), h1 = ld(a.in_h + y(s.c1)), h2 = ld(a.in_h + y(s.c2));
+    return q_value(s.d0, s.d1, s.d2, u0, u1, u2, s.k0, s.k1, s.k2, h0, h1, h2, s.f);
 }
 
 template <class T, bool LY>
@@ -269,7 +326,7 @@ __device__ __forceinline__ void vertex_pv(const DevArgs<T>& a, int v, const Lay<
     VertStat<T> s;
     vertex_stat(a.t, ld, v, s);
     griddep_wait();
-    a.q[y(v)] = vertex_q<T, LY>(a, ld, s, y);
+    St(a.l2)(a.q + y(v), vertex_q<T, LY>(a, ld, s, y));
 }
 
 // --------------------------------------------------------------- kind 1: ring
@@ -374,6 +431,7 @@ __device__ __forceinline__ T ring_pass(const DevArgs<T>& a, int c, const Lay<LY>
         }
     }
     const T Pn = Pacc;
+    const St st(a.l2);
     T Asuf = T(0), Bsuf = T(0);
 #pragma unroll
     for (int p = MAXR - 1; p >= 0; --p) {
@@ -382,12 +440,12 @@ __device__ __forceinline__ T ring_pass(const DevArgs<T>& a, int c, const Lay<LY>
             const T w = P[p] - T(0.5);
             const T C = qt[p] * (w * (Atot - G[p]) + Pn * Asuf - (A1 - P[p] * G[p])) +
                         (w * (Btot - gq) + Pn * Bsuf - (B1 - P[p] * gq));
-            a.ring_c[y(p * N + c)] = C;
+            st(a.ring_c + y(p * N + c), C);
             Asuf += G[p];
             Bsuf += gq;
         }
     }
-    a.ring_k[y(c)] = Kc;
+    st(a.ring_k + y(c), Kc);
     return -(s + comp) * rA;
 }
 
@@ -410,18 +468,29 @@ __device__ __forceinline__ void edge_stat(const Tables<T>& t, const Ld& ld, int 
     s.db = ld.stat(t.db + e);
 }
 
+// U_e from the two ring shares, thicknesses (and compensation words) and
+// kinetic energies of the edge's cells, with the roundings spelled out so
+// the edge, vertex-edge and fused-tile passes get the same bits.  h1 - h0 is
+// exact for nearby thicknesses (Sterbenz); with COMP the compensation words
+// restore the digits the FP32 thickness dropped.
+template <class T, bool COMP>
+__device__ __forceinline__ T edge_u(T C0, T C1, T h0, T h1, T hl0, T hl1, T K0, T K1, T db, T rdc, T g) {
+    T dh = h1 - h0;
+    if (COMP) dh += hl1 - hl0;
+    const T grad = fma_rn(g, dh + db, K1 - K0);
+    return -rdc * fma_rn(T(0.5), C1 - C0, grad);
+}
+
 // Gathers the two cells' ring results and thicknesses (after the wait) and
 // returns U_e.
 template <class T, bool COMP, bool LY>
 __device__ __forceinline__ T edge_value(const DevArgs<T>& a, const Ld& ld, const EdgeStat<T>& s, const Lay<LY>& y) {
     const int N = a.t.nC;
     const T C0 = ld(a.ring_c + y(s.p0 * N + s.c0)), C1 = ld(a.ring_c + y(s.p1 * N + s.c1));
-    // h1 - h0 is exact for nearby thicknesses (Sterbenz); with COMP the
-    // compensation words restore the digits the FP32 thickness dropped.
-    T dh = ld(a.in_h + y(s.c1)) - ld(a.in_h + y(s.c0));
-    if (COMP) dh += ld(a.in_hl + y(s.c1)) - ld(a.in_hl + y(s.c0));
-    const T grad = a.g * (dh + s.db) + (ld(a.ring_k + y(s.c1)) - ld(a.ring_k + y(s.c0)));
-    return -s.rdc * (T(0.5) * (C1 - C0) + grad);
+    const T h0 = ld(a.in_h + y(s.c0)), h1 = ld(a.in_h + y(s.c1));
+    const T hl0 = COMP ? ld(a.in_hl + y(s.c0)) : T(0), hl1 = COMP ? ld(a.in_hl + y(s.c1)) : T(0);
+    const T K0 = ld(a.ring_k + y(s.c0)), K1 = ld(a.ring_k + y(s.c1));
+    return edge_u<T, COMP>(C0, C1, h0, h1, hl0, hl1, K0, K1, s.db, s.rdc, a.g);
 }
 
 template <class T, bool COMP, bool LY>
@@ -436,7 +505,7 @@ __device__ __forceinline__ T edge_tendency(const DevArgs<T>& a, int e, const Dev
 }
 
 template <class T, bool COMP, bool LY>
-__device__ __forceinline__ void pointwise(const DevSeg<T>& s, int i, const Lay<LY>& y);
+__device__ __forceinline__ void pointwise(const DevSeg<T>& s, int i, const Lay<LY>& y, const St& st);
 template <class T>
 __device__ __forceinline__ int find_seg(const DevArgs<T>& a, int blk);
 
@@ -461,9 +530,9 @@ __device__ __forceinline__ T vertex_value(const DevArgs<T>& a, const Ld& ld, int
     const T d0 = ld.stat(t.vd0 + v), d1 = ld.stat(t.vd1 + v), d2 = ld.stat(t.vd2 + v);
     const T k0 = ld.stat(t.vk0 + v), k1 = ld.stat(t.vk1 + v), k2 = ld.stat(t.vk2 + v);
     const T f = ld.stat(t.f + v);
-    T zeta = d0 * ld(a.in_u + e0) + d1 * ld(a.in_u + e1) + d2 * ld(a.in_u + e2);
-    T hv = k0 * ld(a.in_h + c0) + k1 * ld(a.in_h + c1) + k2 * ld(a.in_h + c2);
-    return (zeta + f) / hv;
+    const T u0 = ld(a.in_u + e0), u1 = ld(a.in_u + e1), u2 = ld(a.in_u + e2);
+    const T h0 = ld(a.in_h + c0), h1 = ld(a.in_h + c1), h2 = ld(a.in_h + c2);
+    return q_value(d0, d1, d2, u0, u1, u2, k0, k1, k2, h0, h1, h2, f);
 }
 
 // The ring pass of kind 1 with q read from shared memory (local vertex ids
@@ -611,11 +680,10 @@ __device__ __forceinline__ void tile_pass(const DevArgs<T>& a, const DevSeg<T>& 
         const int p0 = pp & 0xff, p1 = (pp >> 8) & 0xff;
         const int c0 = ld.stat(t.ec0 + e), c1 = ld.stat(t.ec1 + e);
         const T C0 = rc_s[p0 * nl + l0], C1 = rc_s[p1 * nl + l1];
-        T dh = ld(a.in_h + c1) - ld(a.in_h + c0);
-        if (COMP) dh += ld(a.in_hl + c1) - ld(a.in_hl + c0);
-        const T db = ld.stat(t.db + e);
-        const T grad = a.g * (dh + db) + (K_s[l1] - K_s[l0]);
-        const T U = -ld.stat(t.rdc + e) * (T(0.5) * (C1 - C0) + grad);
+        const T h0 = ld(a.in_h + c0), h1 = ld(a.in_h + c1);
+        const T hl0 = COMP ? ld(a.in_hl + c0) : T(0), hl1 = COMP ? ld(a.in_hl + c1) : T(0);
+        const T U = edge_u<T, COMP>(C0, C1, h0, h1, hl0, hl1, K_s[l0], K_s[l1], ld.stat(t.db + e),
+                                    ld.stat(t.rdc + e), a.g);
         if (acc) {
             T* ac = static_cast<T*>(s.p[9]);
             const int q = e - s.base2;
@@ -640,35 +708,43 @@ __global__ void __launch_bounds__(256) kernel_tiles(const __grid_constant__ DevA
     const int i = s.begin + (blockIdx.x - s.block0) * blockDim.x + threadIdx.x;
     if (i >= s.end) return;
     griddep_wait();
-    pointwise<T, COMP, false>(s, i, Lay<false>{});
+    pointwise<T, COMP, false>(s, i, Lay<false>{}, St(a.l2));
 }
 
 // ------------------------------------------------------------ pointwise parts
 
+// The interface-1 prediction of element i of a SEG_PRED segment (the value
+// the segment stores; the vertex-edge pass recomputes it for q).
 template <class T, bool COMP, bool LY>
-__device__ __forceinline__ void pointwise(const DevSeg<T>& s, int i, const Lay<LY>& y) {
+__device__ __forceinline__ void pred_at(const DevSeg<T>& s, int i, const Lay<LY>& y, T& yh, T& yl) {
+    const T* oh = (const T*)s.p[0];
+    const T* ol = (const T*)s.p[1];
+    const T* x1h = (const T*)s.p[2];
+    const T* x1l = (const T*)s.p[3];
+    const T* x2h = (const T*)s.p[4];
+    const T* x2l = (const T*)s.p[5];
+    const auto ii = y(i), k = y(i - s.base), k2 = y(i - s.base2);
+    predict<T, COMP>(oh[ii], COMP ? ol[ii] : T(0), x1h[k], COMP ? x1l[k] : T(0), x2h[k2],
+                     COMP ? x2l[k2] : T(0), s.c[0], s.c[1], s.flag, yh, yl);
+}
+
+template <class T, bool COMP, bool LY>
+__device__ __forceinline__ void pointwise(const DevSeg<T>& s, int i, const Lay<LY>& y, const St& st) {
     if (s.type == SEG_PRED) {
-        const T* oh = (const T*)s.p[0];
-        const T* ol = (const T*)s.p[1];
-        const T* x1h = (const T*)s.p[2];
-        const T* x1l = (const T*)s.p[3];
-        const T* x2h = (const T*)s.p[4];
-        const T* x2l = (const T*)s.p[5];
         T* outh = (T*)s.p[6];
         T* outl = (T*)s.p[7];
-        const auto ii = y(i), k = y(i - s.base), k2 = y(i - s.base2);
+        const auto ii = y(i);
         T yh, yl;
-        predict<T, COMP>(oh[ii], COMP ? ol[ii] : T(0), x1h[k], COMP ? x1l[k] : T(0), x2h[k2],
-                         COMP ? x2l[k2] : T(0), s.c[0], s.c[1], s.flag, yh, yl);
-        outh[ii] = yh;
-        if (COMP) outl[ii] = yl;
+        pred_at<T, COMP, LY>(s, i, y, yh, yl);
+        st(outh + ii, yh);
+        if (COMP) st(outl + ii, yl);
     } else if (s.type == SEG_COPY) {
         const T* sh = (const T*)s.p[0];
         const T* sl = (const T*)s.p[1];
         T* dh = (T*)s.p[2];
         T* dl = (T*)s.p[3];
-        dh[y(i - s.base)] = sh[y(i - s.base2)];
-        if (COMP) dl[y(i - s.base)] = sl[y(i - s.base2)];
+        st(dh + y(i - s.base), sh[y(i - s.base2)]);
+        if (COMP) st(dl + y(i - s.base), sl[y(i - s.base2)]);
     } else if (s.type == SEG_REPLAY) {
         // Step 5 as the replay of the interface stages (reading R5): three
         // stages for LTS3, two for LTS2 (flag 2: x_new = x2).
@@ -690,8 +766,8 @@ __device__ __forceinline__ void pointwise(const DevSeg<T>& s, int i, const Lay<L
             const T* a3 = (const T*)s.p[4];
             combine<T, COMP>(xh, xl, x2h, x2l, s.c[4], s.c[2], a3[k], yh, yl);
         }
-        outh[ii] = yh;
-        if (COMP) outl[ii] = yl;
+        st(outh + ii, yh);
+        if (COMP) st(outl + ii, yl);
     }
 }
 
@@ -700,19 +776,104 @@ __device__ __forceinline__ void pointwise(const DevSeg<T>& s, int i, const Lay<L
 template <class T, bool COMP, bool IS_CELL, bool LY>
 __device__ __forceinline__ void epilogue(const DevArgs<T>& a, const DevSeg<T>& s, int epi, int i, T R,
                                          const EpiOps<T>& o, const Lay<LY>& y) {
+    const St st(a.l2);
     if (epi == EPI_ACC) {
         T* acc = (T*)s.p[0];
-        acc[y(i - s.base)] = s.flag ? R : o.oh + R;
+        st(acc + y(i - s.base), s.flag ? R : o.oh + R);
         return;
     }
     T* outh = (T*)s.p[3];
     T* outl = (T*)s.p[4];
     T yh, yl;
     combine<T, COMP>(o.oh, o.ol, o.xh, o.xl, s.c[0], s.c[1], R, yh, yl);
-    outh[y(i)] = yh;
-    if (COMP) outl[y(i)] = yl;
+    st(outh + y(i), yh);
+    if (COMP) st(outl + y(i), yl);
     const bool ok = IS_CELL ? finite_pos(yh) : finite_val(yh);
     if (!ok) atomicOr(a.flag, IS_CELL ? 1 : 2);
+}
+
+// ---------------------------------------------------- kind 4: vertex-edge
+// One thread per vertex v of the segment.  For each edge of v inside the
+// updated range [s.base, s.base2): U_e from the ring results of its two
+// cells (edge_u, as the edge pass) and the stage update (combine), which the
+// edge's owner vertex stores.  Then q_v of the next right-hand side's input
+// (q_value, as the vertex pass) from the vertex's new edge velocities (the
+// updates just formed; the I1 predictions recomputed as the launch's
+// SEG_PRED segment stores them; the next input's stored values elsewhere)
+// and its cells' next thicknesses (written by the preceding ring launch).
+template <class T>
+__device__ __forceinline__ T pick3(T x0, T x1, T x2, int i) { return i == 0 ? x0 : (i == 1 ? x1 : x2); }
+
+template <class T, bool COMP>
+__device__ __forceinline__ void ve_pass(const DevArgs<T>& a, const DevSeg<T>& s, int v) {
+    const Tables<T>& t = a.t;
+    const Ld ld(a.l2);
+    const int N = t.nC;
+    const int c0 = ld.stat(t.vc0 + v), c1 = ld.stat(t.vc1 + v), c2 = ld.stat(t.vc2 + v);
+    const int e[3] = {ld.stat(t.ve0 + v), ld.stat(t.ve1 + v), ld.stat(t.ve2 + v)};
+    const T vk0 = ld.stat(t.vk0 + v), vk1 = ld.stat(t.vk1 + v), vk2 = ld.stat(t.vk2 + v);
+    const T vd0 = ld.stat(t.vd0 + v), vd1 = ld.stat(t.vd1 + v), vd2 = ld.stat(t.vd2 + v);
+    const T f = ld.stat(t.f + v);
+    const T rd[3] = {ld.stat(t.vrd0 + v), ld.stat(t.vrd1 + v), ld.stat(t.vrd2 + v)};
+    const T db[3] = {ld.stat(t.vdb0 + v), ld.stat(t.vdb1 + v), ld.stat(t.vdb2 + v)};
+    const unsigned long long inf = ld.stat(t.vinf + v);
+    const int pr_lo = s.flag >= 0 ? a.seg[s.flag].begin : 0;
+    const int pr_hi = s.flag >= 0 ? a.seg[s.flag].end : 0;
+    griddep_wait();
+    const T* nx_h = (const T*)s.p[5];
+    const T* nx_u = (const T*)s.p[6];
+    // every load of the three edges goes out in one wave (predicated on the
+    // edge's role), so the pass costs one dependent round trip after the wait
+    const T h0 = ld(a.in_h + c0), h1 = ld(a.in_h + c1), h2 = ld(a.in_h + c2);
+    const T hl0 = COMP ? ld(a.in_hl + c0) : T(0), hl1 = COMP ? ld(a.in_hl + c1) : T(0),
+            hl2 = COMP ? ld(a.in_hl + c2) : T(0);
+    const T K0 = ld(a.ring_k + c0), K1 = ld(a.ring_k + c1), K2 = ld(a.ring_k + c2);
+    const T hn0 = ld(nx_h + c0), hn1 = ld(nx_h + c1), hn2 = ld(nx_h + c2);
+    T C0[3], C1[3], oh[3], ol[3], xh[3], xl[3], nu[3];
+    bool upd[3];
+    unsigned bits[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int ek = e[k];
+        bits[k] = static_cast<unsigned>(inf >> (13 * k)) & 0x1fffu;
+        upd[k] = ek >= s.base && ek < s.base2;
+        const int p0 = bits[k] & 15, p1 = (bits[k] >> 4) & 15;
+        const int ca = pick3(c0, c1, c2, static_cast<int>((bits[k] >> 8) & 3));
+        const int cb = pick3(c0, c1, c2, static_cast<int>((bits[k] >> 10) & 3));
+        C0[k] = ld.when(upd[k], a.ring_c + p0 * N + ca);
+        C1[k] = ld.when(upd[k], a.ring_c + p1 * N + cb);
+        oh[k] = ld.when(upd[k], (const T*)s.p[0] + ek);
+        ol[k] = COMP ? ld.when(upd[k], (const T*)s.p[1] + ek) : T(0);
+        xh[k] = ld.when(upd[k], a.in_u + ek);
+        xl[k] = COMP ? ld.when(upd[k], a.in_ul + ek) : T(0);
+        nu[k] = ld.when(!upd[k], nx_u + ek);
+    }
+    T un[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int ek = e[k];
+        const int l0 = (bits[k] >> 8) & 3, l1 = (bits[k] >> 10) & 3;
+        if (upd[k]) {
+            const T U = edge_u<T, COMP>(C0[k], C1[k], pick3(h0, h1, h2, l0), pick3(h0, h1, h2, l1),
+                                        pick3(hl0, hl1, hl2, l0), pick3(hl0, hl1, hl2, l1),
+                                        pick3(K0, K1, K2, l0), pick3(K0, K1, K2, l1), db[k], rd[k], a.g);
+            T yh, yl;
+            combine<T, COMP>(oh[k], ol[k], xh[k], xl[k], s.c[0], s.c[1], U, yh, yl);
+            if (bits[k] >> 12) {
+                St(a.l2)(static_cast<T*>(s.p[3]) + ek, yh);
+                if (COMP) St(a.l2)(static_cast<T*>(s.p[4]) + ek, yl);
+                if (!finite_val(yh)) atomicOr(a.flag, 2);
+            }
+            un[k] = yh;
+        } else if (ek >= pr_lo && ek < pr_hi) {   // I1 edge: the prediction its segment stores
+            T yh, yl;
+            pred_at<T, COMP, false>(a.seg[s.flag], ek, Lay<false>{}, yh, yl);
+            un[k] = yh;
+        } else {
+            un[k] = nu[k];
+        }
+    }
+    St(a.l2)(a.q + v, q_value(vd0, vd1, vd2, un[0], un[1], un[2], vk0, vk1, vk2, hn0, hn1, hn2, f));
 }
 
 template <class T>
@@ -760,14 +921,16 @@ __device__ __forceinline__ void phase_block(const DevArgs<T>& a, const DevSeg<T>
             epi_load<T, COMP, LY>(Ld(a.l2), s, epi, i, a.in_h, o, y);
             epilogue<T, COMP, true, LY>(a, s, epi, i, H, o, y);
         }
-    } else if (KIND == 2 && (type == SEG_EDGE_UPD || type == SEG_EDGE_ACC)) {
+    } else if ((KIND == 2 || KIND == 4) && (type == SEG_EDGE_UPD || type == SEG_EDGE_ACC)) {
         const int epi = type == SEG_EDGE_ACC ? EPI_ACC : EPI_UPD;
         EpiOps<T> o;
         const T U = edge_tendency<T, COMP, LY>(a, i, s, epi, o, y);
         epilogue<T, COMP, false, LY>(a, s, epi, i, U, o, y);
+    } else if (KIND == 4 && type == SEG_VE) {
+        if constexpr (!LY) ve_pass<T, COMP>(a, s, i);
     } else {
         griddep_wait();
-        pointwise<T, COMP, LY>(s, i, y);
+        pointwise<T, COMP, LY>(s, i, y, St(a.l2));
     }
 }
 
@@ -817,8 +980,8 @@ __device__ __forceinline__ void phase_block2(const DevArgs<T>& a, const DevSeg<T
         if (two) epilogue<T, COMP, false, false>(a, s, epi, i1, U1, o1, y);
     } else {
         griddep_wait();
-        pointwise<T, COMP, false>(s, i0, y);
-        if (two) pointwise<T, COMP, false>(s, i1, y);
+        pointwise<T, COMP, false>(s, i0, y, St(a.l2));
+        if (two) pointwise<T, COMP, false>(s, i1, y, St(a.l2));
     }
 }
 
@@ -951,6 +1114,7 @@ cudaError_t launch_t(const LaunchDesc& d, const void* tables, int block, bool pd
         return launch_kernel(kernel_tiles<T, COMP, MAXR>, blocks, block, pdl, st, a, smem);
     }
     if (layers > 1) {
+        if (d.kind == 4) return cudaErrorInvalidValue;   // single-layer states only
         switch (d.kind) {
             case 0: return launch_kernel(kernel_phase<T, COMP, MAXR, 0, true>, blocks, block, pdl, st, a);
             case 1: return launch_kernel(kernel_phase<T, COMP, MAXR, 1, true>, blocks, block, pdl, st, a);
@@ -967,6 +1131,7 @@ cudaError_t launch_t(const LaunchDesc& d, const void* tables, int block, bool pd
     switch (d.kind) {
         case 0: return launch_kernel(kernel_phase<T, COMP, MAXR, 0>, blocks, block, pdl, st, a);
         case 1: return launch_kernel(kernel_phase<T, COMP, MAXR, 1>, blocks, block, pdl, st, a);
+        case 4: return launch_kernel(kernel_phase<T, COMP, MAXR, 4>, blocks, block, pdl, st, a);
         default: return launch_kernel(kernel_phase<T, COMP, MAXR, 2>, blocks, block, pdl, st, a);
     }
 }
@@ -1250,6 +1415,7 @@ int regs_t(int kind) {
     cudaFuncAttributes at{};
     cudaError_t err = kind == 0   ? cudaFuncGetAttributes(&at, kernel_phase<T, COMP, MAXR, 0>)
                       : kind == 1 ? cudaFuncGetAttributes(&at, kernel_phase<T, COMP, MAXR, 1>)
+                      : kind == 4 ? cudaFuncGetAttributes(&at, kernel_phase<T, COMP, MAXR, 4>)
                                   : cudaFuncGetAttributes(&at, kernel_phase<T, COMP, MAXR, 2>);
     return err == cudaSuccess ? at.numRegs : -1;
 }

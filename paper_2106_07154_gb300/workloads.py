@@ -115,9 +115,10 @@ def _cfl_dt(mesh, h, u, coarse_cells, cfl, g=G):
 
 def hex_bump(nx: int = 32, ny: int = 32, dc: float = 10e3, f0: float = 1e-4, M: int = 2,
              seed: int = 1, radius: float = 60e3, sigma: float = 40e3, nsteps: int = 100,
-             cfl: float = 0.5) -> Workload:
-    """Doubly periodic hexagons, flat bottom, h = 1000 m + 1 m Gaussian bump at a
-    seeded centre, u = 0, fine region = cells within `radius` of the bump."""
+             cfl: float = 0.5, amplitude: float = 1.0) -> Workload:
+    """Doubly periodic hexagons, flat bottom, h = 1000 m + a Gaussian bump of
+    `amplitude` m (1 m by default) at a seeded centre, u = 0, fine region =
+    cells within `radius` of the bump."""
     mesh = hex_mesh(nx, ny, dc, f0)
     rng = np.random.default_rng(seed)
     Lx, Ly = mesh["period_x"], mesh["period_y"]
@@ -127,7 +128,7 @@ def hex_bump(nx: int = 32, ny: int = 32, dc: float = 10e3, f0: float = 1e-4, M: 
     dx -= Lx * np.round(dx / Lx)
     dy -= Ly * np.round(dy / Ly)
     r2 = dx * dx + dy * dy
-    h0 = 1000.0 + 1.0 * np.exp(-r2 / (2.0 * sigma * sigma))
+    h0 = 1000.0 + amplitude * np.exp(-r2 / (2.0 * sigma * sigma))
     u0 = np.zeros(mesh["nEdges"])
     mesh["bottom"] = np.zeros(mesh["nCells"])
     fine = (r2 <= radius * radius).astype(np.int8)

@@ -77,7 +77,20 @@ def test_fp64_hex_100_steps(hexw, hex_ref):
     h, u, _ = run_gpu(hexw, 100, lts.LTS_FP64)
     assert rel(h, hex_ref[0]) <= TOL64
     du = float(np.max(np.abs(u - hex_ref[1])))
-    assert du <= max(TOL64 * float(np.max(np.abs(hex_ref[1]))), u_floor64(hexw, 100))
+    umax = float(np.max(np.abs(hex_ref[1])))
+    print(f"FP64 hex u: |du| {du:.3e} m/s, relative {du / umax:.3e}, "
+          f"1e-12 relative {TOL64 * umax:.3e}, conditioning floor {u_floor64(hexw, 100):.3e}")
+    assert du <= max(TOL64 * umax, u_floor64(hexw, 100))
+
+
+def test_fp64_hex_strict_with_fast_flow():
+    """cfg1's geometry with O(m/s) velocities (a 50 m bump, so u reaches a
+    few m/s): the plain 1e-12 relative bound holds for u with no floor."""
+    w = W.hex_bump(amplitude=50.0)
+    h, u, _ = run_gpu(w, 100, lts.LTS_FP64)
+    rh, ru = run_oracle(w, 100)
+    print(f"FP64 hex (50 m bump): h {rel(h, rh):.3e}, u {rel(u, ru):.3e}, max|u| {np.abs(ru).max():.3f} m/s")
+    assert rel(h, rh) <= TOL64 and rel(u, ru) <= TOL64
 
 
 def test_fp64_sphere_100_steps(sphw, sph_ref):
@@ -88,9 +101,12 @@ def test_fp64_sphere_100_steps(sphw, sph_ref):
 
 def test_fp32_hex_100_steps(hexw, hex_ref):
     h, u, _ = run_gpu(hexw, 100, lts.LTS_FP32)
-    # the hex case is a 1 m bump on 1000 m: compare the perturbation too
     assert rel(h, hex_ref[0]) <= TOL32_H
     assert rel(u, hex_ref[1]) <= TOL32_U
+    # the hex case is a 1 m bump on 1000 m: the full-field norm above is the
+    # stated criterion; the error of the perturbation alone is reported
+    pert = rel(h - 1000.0, hex_ref[0] - 1000.0)
+    print(f"FP32 hex: h {rel(h, hex_ref[0]):.3e} (perturbation alone {pert:.3e}), u {rel(u, hex_ref[1]):.3e}")
 
 
 def test_fp32_sphere_100_steps(sphw, sph_ref):
@@ -235,6 +251,30 @@ def test_two_elements_per_thread_bitwise(sphw, precision, mode, order):
                        mode=mode, order=order, elems_per_thread=ept, use_graph=graph) as m:
             m.step(5)
             out.append(m.read()[:2])
+    for h, u in out[1:]:
+        assert np.array_equal(h, out[0][0]) and np.array_equal(u, out[0][1])
+
+
+@pytest.mark.parametrize("precision", [lts.LTS_FP64, lts.LTS_FP32])
+@pytest.mark.parametrize("M,layers_i", [(1, 1), (2, 1), (3, 1), (4, 2), (8, 1)])
+def test_vertex_edge_pass_bitwise(sphw, precision, M, layers_i):
+    """The vertex-edge plan (every fine right-hand side after the first is a
+    ring launch and a vertex-edge launch that also forms the next q_v; the
+    third stages alternate between two buffers) equals the plan with a
+    separate vertex launch per right-hand side bit for bit, for odd and even
+    M, thick interfaces, with the graph and with direct launches."""
+    out, kinds = [], []
+    for ve, graph in ((False, True), (True, True), (True, False)):
+        with lts.Model(sphw.mesh, sphw.fine_mask, M, sphw.h0, sphw.u0, sphw.dt * M / sphw.M,
+                       precision=precision, interface_layers=layers_i, vertex_edge=ve,
+                       use_graph=graph) as m:
+            kinds.append(m.stats()["launches_per_kind"])
+            m.step(4)
+            out.append(m.read()[:2])
+    # 3M - 1 vertex-edge launches replace as many edge and vertex launches
+    fused = 3 * M - 1
+    assert kinds[1][4] == fused and kinds[0][4] == 0
+    assert kinds[1][0] == kinds[0][0] - fused and kinds[1][2] == kinds[0][2] - fused
     for h, u in out[1:]:
         assert np.array_equal(h, out[0][0]) and np.array_equal(u, out[0][1])
 
