@@ -117,6 +117,17 @@ __device__ __forceinline__ double ld_state_if(bool p, const double* q, uint64_t 
 LTS_LD_HINT(uint32_t, "b32", LTS_R)
 LTS_LD_HINT(float, "f32", LTS_F)
 LTS_LD_HINT(double, "f64", LTS_D)
+__device__ __forceinline__ int4 ld_static(const int4* q, uint64_t p) {
+    int4 x;
+    asm("ld.global.nc.L2::cache_hint.v4.b32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=r"(x.x), "=r"(x.y), "=r"(x.z), "=r"(x.w) : "l"(q), "l"(p));
+    return x;
+}
+__device__ __forceinline__ float2 ld_static(const float2* q, uint64_t p) {
+    float2 x;
+    asm("ld.global.nc.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(x.x), "=f"(x.y) : "l"(q), "l"(p));
+    return x;
+}
 __device__ __forceinline__ uint8_t ld_static(const uint8_t* q, uint64_t p) {
     uint32_t x;
     asm("ld.global.nc.L2::cache_hint.u8 %0, [%1], %2;" : "=r"(x) : "l"(q), "l"(p));
@@ -340,113 +351,160 @@ __device__ __forceinline__ void vertex_pv(const DevArgs<T>& a, int v, const Lay<
 // where S_{j->p} = sum of R_m over the vertices met going counter-clockwise
 // from e_j to e_p (so w_{e_p,e_j} = n_{e_j,c} (-n_{e_p,c}) (S_{j->p} - 1/2),
 // t_{e_p,v_{p-1}} = -n_{e_p,c} on a counter-clockwise ring).  With prefix sums
-// P_p = R_0 + ... + R_{p-1}, S_{j->p} = P_p - P_j + [j > p] P_n, so
-//   C_p = qt_p [(P_p - 1/2) A_p + P_n Asuf_p - A'_p] + [(P_p - 1/2) B_p + P_n Bsuf_p - B'_p]
-// with A_p = sum_{j!=p} G_j, A'_p = sum_{j!=p} P_j G_j, Asuf_p = sum_{j>p} G_j
-// and B the same with G_j qt_j: the weight sum regrouped into O(n) work.
-// The first UNCOND slots are loaded without waiting for the cell's degree
-// (padding slots are valid copies of slot 0), so the table loads and the
-// state gathers of a thread are issued as two independent waves.  Seven
-// slots cover the heptagons of variable-resolution Voronoi meshes (about one
-// cell in eleven, so nearly every warp has one), whose last slot would
-// otherwise cost the warp a further round trip.
-constexpr int UNCOND = 7;
-static_assert(UNCOND <= kSlotRowsMin, "the slot tables must hold the unconditional slots");
+// P_p = R_0 + ... + R_{p-1}, S_{j->p} = P_p - P_j + [j > p] P_n.  Writing
+// A = sum_j G_j, A' = sum_j P_j G_j, Asuf_p = sum_{j>p} G_j and B, B', Bsuf
+// the same with b_j = G_j qt_j, the sum over j != p regroups into O(n) work:
+//   C_p = qt_p (w_p A - A' + P_n Asuf_p) + (w_p B - B' + P_n Bsuf_p) + b_p,
+// w_p = P_p - 1/2 (the j = p terms of A and B cancel into the last b_p).
 
-template <class T, bool COMP, int MAXR, bool LY>
-__device__ __forceinline__ T ring_pass(const DevArgs<T>& a, int c, const Lay<LY>& y) {
-    const Tables<T>& t = a.t;
-    const Ld ld(a.l2);
-    const int N = t.nC;
-    const int n = ld.stat(t.cn + c);
-    // static ring tables of the first UNCOND slots, before the wait
-    int E0[UNCOND], NB0[UNCOND], V0[UNCOND];
-    T SNL0[UNCOND], R0[UNCOND], SK0[UNCOND];
-#pragma unroll
-    for (int j = 0; j < UNCOND; ++j) {
-        E0[j] = ld.stat(t.se + j * N + c);
-        NB0[j] = ld.stat(t.sn + j * N + c);
-        V0[j] = ld.stat(t.sv + j * N + c);
-        SNL0[j] = ld.stat(t.snl + j * N + c);
-        R0[j] = ld.stat(t.sR + j * N + c);
-        SK0[j] = ld.stat(t.sK + j * N + c);
-    }
-    const T rA = ld.stat(t.rA + c);
-    griddep_wait();
-    const T hc = ld(a.in_h + y(c));
-    T G[MAXR], qv[MAXR], R[MAXR];
+// The ring arithmetic of one cell from its gathered slot values (slots
+// j >= n are ignored), shared by the ring pass and the fused tiles so both
+// give the same bits.  Returns H_c; C[p] for p < n and K_c on output.
+template <class T, bool COMP, int NR>
+__device__ __forceinline__ T ring_core(int n, T hc, T rA, const T (&uj)[NR], const T (&hn)[NR],
+                                       const T (&qv)[NR], const T (&snl)[NR], const T (&Rj)[NR],
+                                       const T (&sK)[NR], T (&C)[NR], T& Kc_out) {
+    T G[NR], R[NR];
     T Kc = T(0), s = T(0), comp = T(0);
 #pragma unroll
-    for (int j = 0; j < MAXR; ++j) {
-        if (j < UNCOND || j < n) {
-            const int e = j < UNCOND ? E0[j % UNCOND] : ld.stat(t.se + j * N + c);
-            const int nb = j < UNCOND ? NB0[j % UNCOND] : ld.stat(t.sn + j * N + c);
-            const int v = j < UNCOND ? V0[j % UNCOND] : ld.stat(t.sv + j * N + c);
-            const T snl = j < UNCOND ? SNL0[j % UNCOND] : ld.stat(t.snl + j * N + c);
-            const T Rj = j < UNCOND ? R0[j % UNCOND] : ld.stat(t.sR + j * N + c);
-            const T sK = j < UNCOND ? SK0[j % UNCOND] : ld.stat(t.sK + j * N + c);
-            const T uj = ld(a.in_u + y(e));
-            const T hnb = ld(a.in_h + y(nb));
-            qv[j] = ld(a.q + y(v));
-            const bool in = j < n;
-            const T F = T(0.5) * (hc + hnb) * uj;
-            const T g = in ? mul_rn(snl, F) : T(0);
-            G[j] = g;
-            R[j] = in ? Rj : T(0);
-            if (in) {
-                Kc += sK * uj * uj;
-                if (COMP) {
-                    T ss, ee;
-                    two_sum(s, g, ss, ee);
-                    s = ss;
-                    comp += ee;
-                } else {
-                    s += g;
-                }
+    for (int j = 0; j < NR; ++j) {
+        const bool in = j < n;
+        const T F = mul_rn(mul_rn(T(0.5), hc + hn[j]), uj[j]);
+        const T g = in ? mul_rn(snl[j], F) : T(0);
+        G[j] = g;
+        R[j] = in ? Rj[j] : T(0);
+        if (in) {
+            Kc = fma_rn(mul_rn(sK[j], uj[j]), uj[j], Kc);
+            if (COMP) {
+                T ss, ee;
+                two_sum(s, g, ss, ee);
+                s = ss;
+                comp += ee;
+            } else {
+                s += g;
             }
-        } else {
-            G[j] = T(0);
-            R[j] = T(0);
-            qv[j] = T(0);
         }
     }
     // q at v_{n-1} closes the ring for slot 0
     T qlast = qv[0];
 #pragma unroll
-    for (int j = 1; j < MAXR; ++j)
+    for (int j = 1; j < NR; ++j)
         if (j == n - 1) qlast = qv[j];
-    T qt[MAXR], P[MAXR];
-    T Pacc = T(0), Atot = T(0), Btot = T(0), A1 = T(0), B1 = T(0);
+    T qt[NR], P[NR], b[NR];
+    T Pacc = T(0), A = T(0), B = T(0), A1 = T(0), B1 = T(0);
 #pragma unroll
-    for (int j = 0; j < MAXR; ++j) {
-        qt[j] = T(0.5) * ((j == 0 ? qlast : qv[j - 1]) + qv[j]);
+    for (int j = 0; j < NR; ++j) {
+        qt[j] = mul_rn(T(0.5), (j == 0 ? qlast : qv[j - 1]) + qv[j]);
         P[j] = Pacc;
+        b[j] = mul_rn(G[j], qt[j]);
         if (j < n) {
             Pacc += R[j];
-            const T gq = G[j] * qt[j];
-            Atot += G[j];
-            Btot += gq;
-            A1 += P[j] * G[j];
-            B1 += P[j] * gq;
+            A += G[j];
+            B += b[j];
+            A1 = fma_rn(P[j], G[j], A1);
+            B1 = fma_rn(P[j], b[j], B1);
         }
     }
     const T Pn = Pacc;
-    const St st(a.l2);
     T Asuf = T(0), Bsuf = T(0);
 #pragma unroll
-    for (int p = MAXR - 1; p >= 0; --p) {
+    for (int p = NR - 1; p >= 0; --p) {
         if (p < n) {
-            const T gq = G[p] * qt[p];
             const T w = P[p] - T(0.5);
-            const T C = qt[p] * (w * (Atot - G[p]) + Pn * Asuf - (A1 - P[p] * G[p])) +
-                        (w * (Btot - gq) + Pn * Bsuf - (B1 - P[p] * gq));
-            st(a.ring_c + y(p * N + c), C);
+            const T al = fma_rn(Pn, Asuf, fma_rn(w, A, -A1));
+            const T be = fma_rn(Pn, Bsuf, fma_rn(w, B, -B1));
+            C[p] = fma_rn(qt[p], al, be) + b[p];
             Asuf += G[p];
-            Bsuf += gq;
+            Bsuf += b[p];
         }
     }
-    st(a.ring_k + y(c), Kc);
+    Kc_out = Kc;
     return -(s + comp) * rA;
+}
+
+// The first UNCOND slots' tables are loaded before the dependency wait
+// without waiting for the cell's degree (padding slots are valid copies of
+// slot 0), so the table loads and the state gathers of a thread are two
+// independent waves.  Seven slots cover the heptagons of variable-resolution
+// Voronoi meshes (about one cell in eleven, so nearly every warp has one),
+// whose last slot would otherwise cost the warp a further round trip.  Each
+// slot is two vector loads in FP32: {edge, neighbour, vertex, n l} and
+// {kite fraction, K coefficient}.
+constexpr int UNCOND = 7;
+static_assert(UNCOND <= kSlotRowsMin, "the slot tables must hold the unconditional slots");
+
+template <class T>
+struct RingSlot {
+    int e, nb, v;
+    T snl, R, sK;
+};
+
+template <class T>
+__device__ __forceinline__ RingSlot<T> ring_slot(const Tables<T>& t, const Ld& ld, int j, int c) {
+    const int N = t.nC;
+    const int4 x = ld.stat(t.sidx + j * N + c);
+    RingSlot<T> r;
+    r.e = x.x;
+    r.nb = x.y;
+    r.v = x.z;
+    if constexpr (sizeof(T) == 4) {
+        const float2 z = ld.stat(t.scf + j * N + c);
+        r.snl = __int_as_float(x.w);
+        r.R = z.x;
+        r.sK = z.y;
+    } else {
+        r.snl = ld.stat(t.snl + j * N + c);
+        r.R = ld.stat(t.sR + j * N + c);
+        r.sK = ld.stat(t.sK + j * N + c);
+    }
+    return r;
+}
+
+// Gathers the state of NR slots (the warp's largest degree, so the unrolled
+// loops run no further than some lane needs) and runs the ring arithmetic.
+template <class T, bool COMP, int NR, bool LY>
+__device__ __forceinline__ T ring_body(const DevArgs<T>& a, const Ld& ld, int c, int n, T rA,
+                                       const RingSlot<T> (&S0)[UNCOND], const Lay<LY>& y) {
+    const int N = a.t.nC;
+    const T hc = ld(a.in_h + y(c));
+    T uj[NR], hn[NR], qv[NR], snl[NR], Rj[NR], sK[NR], C[NR];
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+        const RingSlot<T> r = j < UNCOND ? S0[j % UNCOND] : (j < n ? ring_slot(a.t, ld, j, c) : S0[0]);
+        uj[j] = ld(a.in_u + y(r.e));
+        hn[j] = ld(a.in_h + y(r.nb));
+        qv[j] = ld(a.q + y(r.v));
+        snl[j] = r.snl;
+        Rj[j] = r.R;
+        sK[j] = r.sK;
+    }
+    T Kc;
+    const T H = ring_core<T, COMP, NR>(n, hc, rA, uj, hn, qv, snl, Rj, sK, C, Kc);
+    const St st(a.l2);
+#pragma unroll
+    for (int p = 0; p < NR; ++p)
+        if (p < n) st(a.ring_c + y(p * N + c), C[p]);
+    st(a.ring_k + y(c), Kc);
+    return H;
+}
+
+template <class T, bool COMP, int MAXR, bool LY>
+__device__ __forceinline__ T ring_pass(const DevArgs<T>& a, int c, const Lay<LY>& y) {
+    const Tables<T>& t = a.t;
+    const Ld ld(a.l2);
+    const int n = ld.stat(t.cn + c);
+    RingSlot<T> S0[UNCOND];
+#pragma unroll
+    for (int j = 0; j < UNCOND; ++j) S0[j] = ring_slot(t, ld, j, c);
+    const T rA = ld.stat(t.rA + c);
+    griddep_wait();
+    // the unrolled width follows the largest degree among the warp's cells
+    // (warp-uniform, so the lanes of a warp stay converged)
+    const int nmax = __reduce_max_sync(__activemask(), n);
+    if (nmax <= 6) return ring_body<T, COMP, 6, LY>(a, ld, c, n, rA, S0, y);
+    if (nmax <= 7 || MAXR <= 7) return ring_body<T, COMP, (MAXR < 7 ? MAXR : 7), LY>(a, ld, c, n, rA, S0, y);
+    if (nmax <= 8 || MAXR <= 8) return ring_body<T, COMP, (MAXR < 8 ? MAXR : 8), LY>(a, ld, c, n, rA, S0, y);
+    return ring_body<T, COMP, MAXR, LY>(a, ld, c, n, rA, S0, y);
 }
 
 // --------------------------------------------------------------- kind 2: edge
@@ -544,77 +602,27 @@ __device__ __forceinline__ T ring_local(const DevArgs<T>& a, const Ld& ld, int c
     const int N = t.nC;
     const int n = ld.stat(t.cn + c);
     const T hc = ld(a.in_h + c);
-    T G[MAXR], qv[MAXR], R[MAXR];
-    T Kc = T(0), s = T(0), comp = T(0);
+    T uj[MAXR], hn[MAXR], qv[MAXR], snl[MAXR], Rj[MAXR], sK[MAXR], C[MAXR];
 #pragma unroll
     for (int j = 0; j < MAXR; ++j) {
         if (j < UNCOND || j < n) {
-            const int e = ld.stat(t.se + j * N + c);
-            const int nb = ld.stat(t.sn + j * N + c);
-            const int lv = lsv[j * nl + k];
-            const T snl = ld.stat(t.snl + j * N + c);
-            const T Rj = ld.stat(t.sR + j * N + c);
-            const T sK = ld.stat(t.sK + j * N + c);
-            const T uj = ld(a.in_u + e);
-            const T hnb = ld(a.in_h + nb);
-            qv[j] = q_s[lv];
-            const bool in = j < n;
-            const T F = T(0.5) * (hc + hnb) * uj;
-            const T g = in ? mul_rn(snl, F) : T(0);
-            G[j] = g;
-            R[j] = in ? Rj : T(0);
-            if (in) {
-                Kc += sK * uj * uj;
-                if (COMP) {
-                    T ss, ee;
-                    two_sum(s, g, ss, ee);
-                    s = ss;
-                    comp += ee;
-                } else {
-                    s += g;
-                }
-            }
+            uj[j] = ld(a.in_u + ld.stat(t.se + j * N + c));
+            hn[j] = ld(a.in_h + ld.stat(t.sn + j * N + c));
+            qv[j] = q_s[lsv[j * nl + k]];
+            snl[j] = ld.stat(t.snl + j * N + c);
+            Rj[j] = ld.stat(t.sR + j * N + c);
+            sK[j] = ld.stat(t.sK + j * N + c);
         } else {
-            G[j] = T(0);
-            R[j] = T(0);
-            qv[j] = T(0);
+            uj[j] = hn[j] = qv[j] = snl[j] = Rj[j] = sK[j] = T(0);
         }
     }
-    T qlast = qv[0];
+    T Kc;
+    const T H = ring_core<T, COMP, MAXR>(n, hc, ld.stat(t.rA + c), uj, hn, qv, snl, Rj, sK, C, Kc);
 #pragma unroll
-    for (int j = 1; j < MAXR; ++j)
-        if (j == n - 1) qlast = qv[j];
-    T qt[MAXR], P[MAXR];
-    T Pacc = T(0), Atot = T(0), Btot = T(0), A1 = T(0), B1 = T(0);
-#pragma unroll
-    for (int j = 0; j < MAXR; ++j) {
-        qt[j] = T(0.5) * ((j == 0 ? qlast : qv[j - 1]) + qv[j]);
-        P[j] = Pacc;
-        if (j < n) {
-            Pacc += R[j];
-            const T gq = G[j] * qt[j];
-            Atot += G[j];
-            Btot += gq;
-            A1 += P[j] * G[j];
-            B1 += P[j] * gq;
-        }
-    }
-    const T Pn = Pacc;
-    T Asuf = T(0), Bsuf = T(0);
-#pragma unroll
-    for (int p = MAXR - 1; p >= 0; --p) {
-        if (p < n) {
-            const T gq = G[p] * qt[p];
-            const T w = P[p] - T(0.5);
-            const T C = qt[p] * (w * (Atot - G[p]) + Pn * Asuf - (A1 - P[p] * G[p])) +
-                        (w * (Btot - gq) + Pn * Bsuf - (B1 - P[p] * gq));
-            rc_s[p * nl + k] = C;
-            Asuf += G[p];
-            Bsuf += gq;
-        }
-    }
+    for (int p = 0; p < MAXR; ++p)
+        if (p < n) rc_s[p * nl + k] = C[p];
     K_s[k] = Kc;
-    return -(s + comp) * ld.stat(t.rA + c);
+    return H;
 }
 
 // Stage update or accumulation with explicit arrays (fused kernel epilogue).
@@ -934,8 +942,11 @@ __device__ __forceinline__ void phase_block(const DevArgs<T>& a, const DevSeg<T>
     }
 }
 
+// The ring kind is compiled for four resident 256-thread blocks per SM (64
+// registers): on GB300 this beat both five blocks (48 registers, with
+// spills) and no limit (80 registers, three blocks) on the 655k-cell cap mesh.
 template <class T, bool COMP, int MAXR, int KIND, bool LY = false>
-__global__ void __launch_bounds__(256) kernel_phase(const __grid_constant__ DevArgs<T> a) {
+__global__ void __launch_bounds__(256, (KIND == 1 ? 4 : 1)) kernel_phase(const __grid_constant__ DevArgs<T> a) {
     griddep_launch_dependents();
     const int sidx = find_seg(a, blockIdx.x);
     phase_block<T, COMP, MAXR, KIND, LY>(a, a.seg[sidx], blockIdx.x);

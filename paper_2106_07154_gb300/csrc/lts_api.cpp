@@ -103,6 +103,25 @@ int build_tables(lts_regions_s* R, int which, Tables<T>& t) {
     t.snl = up(co.snl);
     t.sR = up(co.sR);
     t.sK = up(co.sK);
+    {
+        std::vector<int4> sidx(r.se.size());
+        std::vector<float2> scf(sizeof(T) == 4 ? r.se.size() : 0);
+        for (size_t x = 0; x < r.se.size(); ++x) {
+            int bits = 0;
+            if (sizeof(T) == 4) {
+                const float f = static_cast<float>(co.snl[x]);
+                std::memcpy(&bits, &f, sizeof(bits));
+                scf[x].x = static_cast<float>(co.sR[x]);
+                scf[x].y = static_cast<float>(co.sK[x]);
+            }
+            sidx[x].x = r.se[x];
+            sidx[x].y = r.sn[x];
+            sidx[x].z = r.sv[x];
+            sidx[x].w = bits;
+        }
+        t.sidx = up(sidx);
+        t.scf = sizeof(T) == 4 ? up(scf) : nullptr;
+    }
     t.rA = up(co.rA);
     t.b = up(co.b);
     t.ec0 = up(r.ec0);

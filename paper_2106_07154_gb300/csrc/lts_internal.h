@@ -33,6 +33,10 @@ struct Tables {
     const T* snl;        // [maxE*nC]  n_{e,c} l_e      (signed primal length)
     const T* sR;         // [maxE*nC]  A_{c,v_j} / A_c  (kite fraction)
     const T* sK;         // [maxE*nC]  l_e d_e / (4 A_c)
+    // the same slots packed for the ring pass's vector loads: {se, sn, sv,
+    // the bits of snl in FP32 (0 in FP64)} and, in FP32, {sR, sK}
+    const int4* sidx;    // [maxE*nC]
+    const float2* scf;   // [maxE*nC]  (FP32 tables only)
     const T* rA;         // [nC]       1 / A_c
     const T* b;          // [nC]       bottom topography
     // edges
