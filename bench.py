@@ -71,9 +71,6 @@ def parse():
                          "LTS3 step on pure gravity waves)")
     ap.add_argument("--elems-per-thread", type=int, default=0, choices=[0, 1, 2],
                     help="elements per thread of the vertex and edge launches (0 = library default)")
-    ap.add_argument("--vertex-edge", action="store_true",
-                    help="fine right-hand sides as a ring launch and a vertex-edge launch (two "
-                         "launches instead of three)")
     ap.add_argument("--autotune", type=int, default=0,
                     help="time the run with the configuration the library's autotuner picks "
                          "(coarse steps per candidate; 0 = library defaults)")
@@ -403,8 +400,7 @@ def run_lts(args):
                       compensated=True, use_graph=not args.no_graph, stream=stream.cuda_stream,
                       pdl=not args.no_pdl, autotune=tune, tune_ordering=bool(tune), layers=L,
                       order=w.order, interface_layers=w.interface_layers,
-                      elems_per_thread=args.elems_per_thread,
-                      vertex_edge=args.vertex_edge)
+                      elems_per_thread=args.elems_per_thread)
     stats = model.stats()
     model.step(args.warmup)
     torch.cuda.synchronize()
@@ -568,7 +564,6 @@ def extras(args, w, model, stats, stream, h_gpu, u_gpu, diag):
     knobs = {k: tuned[k] for k in ("block_size", "kernel_path", "l2_hints", "coarse_schedule",
                                    "ring_occupancy", "elems_per_thread") if k in tuned}
     knobs.setdefault("elems_per_thread", args.elems_per_thread)
-    knobs["vertex_edge"] = args.vertex_edge
     if "ordering" in tuned:
         knobs["ordering"] = tuned["ordering"]
     prof = lts.Model(w.mesh, w.fine_mask, w.M, w.h0, w.u0, w.dt, w.g, precision=prec,

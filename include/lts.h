@@ -265,16 +265,6 @@ typedef struct lts_params {
                                three-launch path: 1 or 2 elements per thread (2: half
                                the blocks, both elements' loads in flight together);
                                0 = library default.  Results are identical.            */
-    int32_t vertex_edge;    /* 1: in the fine substeps of LTS3 (single region, single
-                               layer, three-launch path) every right-hand side after the
-                               first starts with the ring launch: the preceding edge
-                               launch is a vertex-edge launch (one thread per vertex
-                               updates its three edges, the edge's owner stores them,
-                               and forms q_v of the next input), two launches per
-                               right-hand side instead of three; 0 (default): a vertex
-                               launch for every right-hand side.  Results are
-                               identical; on the 655k-cell cap mesh the vertex-edge
-                               launches are slower than the launches they replace.     */
 } lts_params;
 
 /* Allocates the device state (band order) and uploads (h0, u0), the
@@ -372,12 +362,11 @@ int lts_sync(lts_state s);
  * counterpart): number of kernel launches, and per
  * launch kind k (0 = vertex PV, 1 = cell ring pass with the thickness
  * update, 2 = edge pass with the velocity update, 3 = fused tile kernel
- * doing all three for a tile, 4 = vertex-edge pass: the edge updates and
- * the next right-hand side's q_v) the algorithmic bytes
+ * doing all three for a tile) the algorithmic bytes
  * summed over the step (each array element a launch touches counted once).
  * With profile = 1, ms[k] is the summed event time of those launches in the
  * last lts_step call (0 otherwise).  Arrays of LTS_NKINDS. */
-#define LTS_NKINDS 5
+#define LTS_NKINDS 4
 int lts_step_stats(lts_state s, int32_t* launches_per_step, double* bytes, double* ms,
                    int32_t* launches_per_kind);
 

@@ -97,23 +97,6 @@ __device__ __forceinline__ uint64_t l2_policy(int mode) {
 #define LTS_L(x) "=l"(x)
 LTS_LD_HINT(int, "b32", LTS_R)
 LTS_LD_HINT(unsigned long long, "b64", LTS_L)
-// State loads issued only where p holds (0 otherwise), as one predicated
-// instruction: the load goes out in the same wave as unconditional ones
-// instead of behind a branch.
-__device__ __forceinline__ float ld_state_if(bool p, const float* q, uint64_t pol) {
-    float x = 0.0f;
-    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t"
-                 "@q ld.global.nc.L2::cache_hint.f32 %0, [%1], %3;\n\t}"
-                 : "+f"(x) : "l"(q), "r"(static_cast<int>(p)), "l"(pol) : "memory");
-    return x;
-}
-__device__ __forceinline__ double ld_state_if(bool p, const double* q, uint64_t pol) {
-    double x = 0.0;
-    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t"
-                 "@q ld.global.nc.L2::cache_hint.f64 %0, [%1], %3;\n\t}"
-                 : "+d"(x) : "l"(q), "r"(static_cast<int>(p)), "l"(pol) : "memory");
-    return x;
-}
 LTS_LD_HINT(uint32_t, "b32", LTS_R)
 LTS_LD_HINT(float, "f32", LTS_F)
 LTS_LD_HINT(double, "f64", LTS_D)
@@ -161,8 +144,6 @@ struct Ld {
     __device__ __forceinline__ V stat(const V* q) const { return ld_static(q, pol); }
     template <class V>
     __device__ __forceinline__ V operator()(const V* q) const { return ld_state(q, spol); }
-    template <class V>
-    __device__ __forceinline__ V when(bool p, const V* q) const { return ld_state_if(p, q, spol); }
 };
 
 // ------------------------------------------------------------------ layers
@@ -313,8 +294,8 @@ __device__ __forceinline__ void vertex_stat(const Tables<T>& t, const Ld& ld, in
 }
 
 // q_v from the vertex's three edge velocities and cell thicknesses, with the
-// roundings spelled out, so every pass that forms q (vertex, vertex-edge,
-// fused tiles) gets the same bits.
+// roundings spelled out, so every pass that forms q (vertex, fused tiles)
+// gets the same bits.
 template <class T>
 __device__ __forceinline__ T q_value(T d0, T d1, T d2, T u0, T u1, T u2, T k0, T k1, T k2, T h0, T h1, T h2,
                                      T f) {
@@ -528,7 +509,7 @@ __device__ __forceinline__ void edge_stat(const Tables<T>& t, const Ld& ld, int 
 
 // U_e from the two ring shares, thicknesses (and compensation words) and
 // kinetic energies of the edge's cells, with the roundings spelled out so
-// the edge, vertex-edge and fused-tile passes get the same bits.  h1 - h0 is
+// the edge and fused-tile passes get the same bits.  h1 - h0 is
 // exact for nearby thicknesses (Sterbenz); with COMP the compensation words
 // restore the digits the FP32 thickness dropped.
 template <class T, bool COMP>
@@ -721,8 +702,7 @@ __global__ void __launch_bounds__(256) kernel_tiles(const __grid_constant__ DevA
 
 // ------------------------------------------------------------ pointwise parts
 
-// The interface-1 prediction of element i of a SEG_PRED segment (the value
-// the segment stores; the vertex-edge pass recomputes it for q).
+// The interface-1 prediction of element i of a SEG_PRED segment.
 template <class T, bool COMP, bool LY>
 __device__ __forceinline__ void pred_at(const DevSeg<T>& s, int i, const Lay<LY>& y, T& yh, T& yl) {
     const T* oh = (const T*)s.p[0];
@@ -800,90 +780,6 @@ __device__ __forceinline__ void epilogue(const DevArgs<T>& a, const DevSeg<T>& s
     if (!ok) atomicOr(a.flag, IS_CELL ? 1 : 2);
 }
 
-// ---------------------------------------------------- kind 4: vertex-edge
-// One thread per vertex v of the segment.  For each edge of v inside the
-// updated range [s.base, s.base2): U_e from the ring results of its two
-// cells (edge_u, as the edge pass) and the stage update (combine), which the
-// edge's owner vertex stores.  Then q_v of the next right-hand side's input
-// (q_value, as the vertex pass) from the vertex's new edge velocities (the
-// updates just formed; the I1 predictions recomputed as the launch's
-// SEG_PRED segment stores them; the next input's stored values elsewhere)
-// and its cells' next thicknesses (written by the preceding ring launch).
-template <class T>
-__device__ __forceinline__ T pick3(T x0, T x1, T x2, int i) { return i == 0 ? x0 : (i == 1 ? x1 : x2); }
-
-template <class T, bool COMP>
-__device__ __forceinline__ void ve_pass(const DevArgs<T>& a, const DevSeg<T>& s, int v) {
-    const Tables<T>& t = a.t;
-    const Ld ld(a.l2);
-    const int N = t.nC;
-    const int c0 = ld.stat(t.vc0 + v), c1 = ld.stat(t.vc1 + v), c2 = ld.stat(t.vc2 + v);
-    const int e[3] = {ld.stat(t.ve0 + v), ld.stat(t.ve1 + v), ld.stat(t.ve2 + v)};
-    const T vk0 = ld.stat(t.vk0 + v), vk1 = ld.stat(t.vk1 + v), vk2 = ld.stat(t.vk2 + v);
-    const T vd0 = ld.stat(t.vd0 + v), vd1 = ld.stat(t.vd1 + v), vd2 = ld.stat(t.vd2 + v);
-    const T f = ld.stat(t.f + v);
-    const T rd[3] = {ld.stat(t.vrd0 + v), ld.stat(t.vrd1 + v), ld.stat(t.vrd2 + v)};
-    const T db[3] = {ld.stat(t.vdb0 + v), ld.stat(t.vdb1 + v), ld.stat(t.vdb2 + v)};
-    const unsigned long long inf = ld.stat(t.vinf + v);
-    const int pr_lo = s.flag >= 0 ? a.seg[s.flag].begin : 0;
-    const int pr_hi = s.flag >= 0 ? a.seg[s.flag].end : 0;
-    griddep_wait();
-    const T* nx_h = (const T*)s.p[5];
-    const T* nx_u = (const T*)s.p[6];
-    // every load of the three edges goes out in one wave (predicated on the
-    // edge's role), so the pass costs one dependent round trip after the wait
-    const T h0 = ld(a.in_h + c0), h1 = ld(a.in_h + c1), h2 = ld(a.in_h + c2);
-    const T hl0 = COMP ? ld(a.in_hl + c0) : T(0), hl1 = COMP ? ld(a.in_hl + c1) : T(0),
-            hl2 = COMP ? ld(a.in_hl + c2) : T(0);
-    const T K0 = ld(a.ring_k + c0), K1 = ld(a.ring_k + c1), K2 = ld(a.ring_k + c2);
-    const T hn0 = ld(nx_h + c0), hn1 = ld(nx_h + c1), hn2 = ld(nx_h + c2);
-    T C0[3], C1[3], oh[3], ol[3], xh[3], xl[3], nu[3];
-    bool upd[3];
-    unsigned bits[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const int ek = e[k];
-        bits[k] = static_cast<unsigned>(inf >> (13 * k)) & 0x1fffu;
-        upd[k] = ek >= s.base && ek < s.base2;
-        const int p0 = bits[k] & 15, p1 = (bits[k] >> 4) & 15;
-        const int ca = pick3(c0, c1, c2, static_cast<int>((bits[k] >> 8) & 3));
-        const int cb = pick3(c0, c1, c2, static_cast<int>((bits[k] >> 10) & 3));
-        C0[k] = ld.when(upd[k], a.ring_c + p0 * N + ca);
-        C1[k] = ld.when(upd[k], a.ring_c + p1 * N + cb);
-        oh[k] = ld.when(upd[k], (const T*)s.p[0] + ek);
-        ol[k] = COMP ? ld.when(upd[k], (const T*)s.p[1] + ek) : T(0);
-        xh[k] = ld.when(upd[k], a.in_u + ek);
-        xl[k] = COMP ? ld.when(upd[k], a.in_ul + ek) : T(0);
-        nu[k] = ld.when(!upd[k], nx_u + ek);
-    }
-    T un[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const int ek = e[k];
-        const int l0 = (bits[k] >> 8) & 3, l1 = (bits[k] >> 10) & 3;
-        if (upd[k]) {
-            const T U = edge_u<T, COMP>(C0[k], C1[k], pick3(h0, h1, h2, l0), pick3(h0, h1, h2, l1),
-                                        pick3(hl0, hl1, hl2, l0), pick3(hl0, hl1, hl2, l1),
-                                        pick3(K0, K1, K2, l0), pick3(K0, K1, K2, l1), db[k], rd[k], a.g);
-            T yh, yl;
-            combine<T, COMP>(oh[k], ol[k], xh[k], xl[k], s.c[0], s.c[1], U, yh, yl);
-            if (bits[k] >> 12) {
-                St(a.l2)(static_cast<T*>(s.p[3]) + ek, yh);
-                if (COMP) St(a.l2)(static_cast<T*>(s.p[4]) + ek, yl);
-                if (!finite_val(yh)) atomicOr(a.flag, 2);
-            }
-            un[k] = yh;
-        } else if (ek >= pr_lo && ek < pr_hi) {   // I1 edge: the prediction its segment stores
-            T yh, yl;
-            pred_at<T, COMP, false>(a.seg[s.flag], ek, Lay<false>{}, yh, yl);
-            un[k] = yh;
-        } else {
-            un[k] = nu[k];
-        }
-    }
-    St(a.l2)(a.q + v, q_value(vd0, vd1, vd2, un[0], un[1], un[2], vk0, vk1, vk2, hn0, hn1, hn2, f));
-}
-
 template <class T>
 __device__ __forceinline__ int find_seg(const DevArgs<T>& a, int blk) {
     int s = 0;
@@ -929,13 +825,11 @@ __device__ __forceinline__ void phase_block(const DevArgs<T>& a, const DevSeg<T>
             epi_load<T, COMP, LY>(Ld(a.l2), s, epi, i, a.in_h, o, y);
             epilogue<T, COMP, true, LY>(a, s, epi, i, H, o, y);
         }
-    } else if ((KIND == 2 || KIND == 4) && (type == SEG_EDGE_UPD || type == SEG_EDGE_ACC)) {
+    } else if (KIND == 2 && (type == SEG_EDGE_UPD || type == SEG_EDGE_ACC)) {
         const int epi = type == SEG_EDGE_ACC ? EPI_ACC : EPI_UPD;
         EpiOps<T> o;
         const T U = edge_tendency<T, COMP, LY>(a, i, s, epi, o, y);
         epilogue<T, COMP, false, LY>(a, s, epi, i, U, o, y);
-    } else if (KIND == 4 && type == SEG_VE) {
-        if constexpr (!LY) ve_pass<T, COMP>(a, s, i);
     } else {
         griddep_wait();
         pointwise<T, COMP, LY>(s, i, y, St(a.l2));
@@ -1125,7 +1019,6 @@ cudaError_t launch_t(const LaunchDesc& d, const void* tables, int block, bool pd
         return launch_kernel(kernel_tiles<T, COMP, MAXR>, blocks, block, pdl, st, a, smem);
     }
     if (layers > 1) {
-        if (d.kind == 4) return cudaErrorInvalidValue;   // single-layer states only
         switch (d.kind) {
             case 0: return launch_kernel(kernel_phase<T, COMP, MAXR, 0, true>, blocks, block, pdl, st, a);
             case 1: return launch_kernel(kernel_phase<T, COMP, MAXR, 1, true>, blocks, block, pdl, st, a);
@@ -1142,7 +1035,6 @@ cudaError_t launch_t(const LaunchDesc& d, const void* tables, int block, bool pd
     switch (d.kind) {
         case 0: return launch_kernel(kernel_phase<T, COMP, MAXR, 0>, blocks, block, pdl, st, a);
         case 1: return launch_kernel(kernel_phase<T, COMP, MAXR, 1>, blocks, block, pdl, st, a);
-        case 4: return launch_kernel(kernel_phase<T, COMP, MAXR, 4>, blocks, block, pdl, st, a);
         default: return launch_kernel(kernel_phase<T, COMP, MAXR, 2>, blocks, block, pdl, st, a);
     }
 }
@@ -1426,7 +1318,6 @@ int regs_t(int kind) {
     cudaFuncAttributes at{};
     cudaError_t err = kind == 0   ? cudaFuncGetAttributes(&at, kernel_phase<T, COMP, MAXR, 0>)
                       : kind == 1 ? cudaFuncGetAttributes(&at, kernel_phase<T, COMP, MAXR, 1>)
-                      : kind == 4 ? cudaFuncGetAttributes(&at, kernel_phase<T, COMP, MAXR, 4>)
                                   : cudaFuncGetAttributes(&at, kernel_phase<T, COMP, MAXR, 2>);
     return err == cudaSuccess ? at.numRegs : -1;
 }

@@ -50,39 +50,6 @@ int check_device() {
     return LTS_OK;
 }
 
-// Per-vertex edge data of the vertex-edge pass (see Tables::vinf): for each
-// band-order vertex v and its edge k, the edge's two slots, which of v's
-// cells are its ends, and whether v owns (stores) the edge: the vertex of
-// the edge with the smaller band-order index.
-int vertex_edge_info(const RegionsHost& r, int nV, int nE, std::vector<unsigned long long>& inf) {
-    std::vector<int> owner(nE, 0x7fffffff);
-    for (int q = 0; q < 3; ++q)
-        for (int v = 0; v < nV; ++v) {
-            const int e = r.ve[static_cast<size_t>(q) * nV + v];
-            owner[e] = std::min(owner[e], v);
-        }
-    inf.assign(nV, 0ull);
-    for (int v = 0; v < nV; ++v) {
-        int cells[3];
-        for (int q = 0; q < 3; ++q) cells[q] = r.vc[static_cast<size_t>(q) * nV + v];
-        for (int k = 0; k < 3; ++k) {
-            const int e = r.ve[static_cast<size_t>(k) * nV + v];
-            const int p0 = r.ep[e] & 0xff, p1 = (r.ep[e] >> 8) & 0xff;
-            int l0 = -1, l1 = -1;
-            for (int q = 0; q < 3; ++q) {
-                if (l0 < 0 && cells[q] == r.ec0[e]) l0 = q;
-                if (l1 < 0 && cells[q] == r.ec1[e]) l1 = q;
-            }
-            if (l0 < 0 || l1 < 0 || p0 > 15 || p1 > 15)
-                return set_error(LTS_EINVAL, "vertex %d and its edge %d do not share the edge's cells", v, e);
-            const unsigned long long bits = static_cast<unsigned long long>(p0) | (p1 << 4) | (l0 << 8) |
-                                            (l1 << 10) | ((owner[e] == v ? 1ull : 0ull) << 12);
-            inf[v] |= bits << (13 * k);
-        }
-    }
-    return LTS_OK;
-}
-
 template <class T>
 int build_tables(lts_regions_s* R, int which, Tables<T>& t) {
     const HostMesh& m = R->mesh->m;
@@ -140,21 +107,6 @@ int build_tables(lts_regions_s* R, int which, Tables<T>& t) {
     t.vk0 = vk; t.vk1 = vk + nV; t.vk2 = vk + 2 * nV;
     t.vd0 = vd; t.vd1 = vd + nV; t.vd2 = vd + 2 * nV;
     t.f = up(co.f);
-    {
-        std::vector<unsigned long long> inf;
-        const int rc = vertex_edge_info(r, m.nV, m.nE, inf);
-        if (rc != LTS_OK) return rc;
-        std::vector<T> vrd(3 * nV), vdb(3 * nV);
-        for (size_t x = 0; x < 3 * nV; ++x) {
-            vrd[x] = co.rdc[r.ve[x]];
-            vdb[x] = co.db[r.ve[x]];
-        }
-        const T* drd = up(vrd);
-        const T* ddb = up(vdb);
-        t.vinf = up(inf);
-        t.vrd0 = drd; t.vrd1 = drd + nV; t.vrd2 = drd + 2 * nV;
-        t.vdb0 = ddb; t.vdb1 = ddb + nV; t.vdb2 = ddb + 2 * nV;
-    }
     t.ta = up(r.tile_a);
     t.tbk = up(r.tile_b);
     t.tlsv = up(r.tile_lsv_off);
@@ -181,7 +133,6 @@ int build_tables(lts_regions_s* R, int which, Tables<T>& t) {
 double launch_bytes(const LaunchDesc& d, const RegionsHost& r, int nC, int nE, int nV, size_t T,
                     bool comp, int layers) {
     std::vector<char> mh(nC, 0), mhl(nC, 0), mu(nE, 0), mq(nV, 0), mk(nC, 0);
-    std::vector<char> mnh, mnu;   // vertex-edge pass: the next input's thickness and velocity
     std::vector<char> mrow(nC, 0), mvert(nV, 0);   // fused tiles: ring rows and vertices read
     double tab = 0.0, st = 0.0;   // table bytes, state bytes per layer
     const double c = comp ? 1.0 : 0.0;
@@ -253,30 +204,6 @@ double launch_bytes(const LaunchDesc& d, const RegionsHost& r, int nC, int nE, i
                     }
                 }
                 break;
-            case SEG_VE: {
-                // vc, ve, vinf; vk, vd, f, vrd, vdb; the q write
-                tab += n * (32.0 + 13.0 * T);
-                st += n * T;
-                if (mnh.empty()) {
-                    mnh.assign(nC, 0);
-                    mnu.assign(nE, 0);
-                }
-                std::vector<char> upd(nE, 0);
-                for (int v = g.begin; v < g.end; ++v)
-                    for (int q = 0; q < 3; ++q) {
-                        const int cc = r.vc[static_cast<size_t>(q) * nV + v];
-                        const int e = r.ve[static_cast<size_t>(q) * nV + v];
-                        mh[cc] = mk[cc] = mnh[cc] = 1;
-                        if (comp) mhl[cc] = 1;
-                        if (e >= g.base && e < g.base2) upd[e] = 1;
-                        else mnu[e] = 1;   // the I1 predictions read the same data as their segment
-                    }
-                double nu = 0.0;
-                for (char x : upd) nu += x;
-                // per updated edge: the two ring shares, x_old and x_in (+ lo), x_out (+ lo)
-                st += nu * (2.0 * T + T * (2.0 + 3.0 * c));
-                break;
-            }
             case SEG_PRED:
                 st += n * T * (g.flag ? 2.0 * (1 + c) : 4.0 * (1 + c));
                 break;
@@ -309,8 +236,6 @@ double launch_bytes(const LaunchDesc& d, const RegionsHost& r, int nC, int nE, i
     }
     double cnt = 0.0;
     for (int k = 0; k < nC; ++k) cnt += mh[k] + mhl[k] + mk[k];
-    for (char x : mnh) cnt += x;
-    for (char x : mnu) cnt += x;
     for (char x : mu) cnt += x;
     for (char x : mq) cnt += x;
     return tab + layers * (st + cnt * T);
@@ -353,29 +278,6 @@ struct Planner {
         s.p[9] = stage >= 0 ? S->acc_e[stage] : nullptr;
         s.c[0] = a;
         s.c[1] = D;
-        return s;
-    }
-    // vertex-edge pass over vertex bands vlo..vhi, updating the edges of bands
-    // elo..ehi (x_out = combine(x_old, x_in, a, D, U)); next = the input of
-    // the right-hand side that follows, whose q_v the pass forms
-    SegDesc vedge(int vlo, int vhi, int elo, int ehi, const SV& old, const SV& out, const SV& next, double a,
-                  double D) const {
-        SegDesc s;
-        s.type = SEG_VE;
-        s.elem = ELEM_VERT;
-        s.begin = vb[vlo];
-        s.end = vb[vhi + 1];
-        s.base = eb[elo];
-        s.base2 = eb[ehi + 1];
-        s.p[0] = old.uh;
-        s.p[1] = old.ul;
-        s.p[3] = out.uh;
-        s.p[4] = out.ul;
-        s.p[5] = next.hh;
-        s.p[6] = next.uh;
-        s.c[0] = a;
-        s.c[1] = D;
-        s.flag = -1;
         return s;
     }
     SegDesc ring(int lo, int hi) const {   // ring results only, cell bands lo..hi
@@ -525,19 +427,6 @@ struct Planner {
 
 constexpr double A1 = 0.0, A2 = 0.75, A3 = 1.0 / 3.0;
 
-// Points a launch's vertex-edge segment at its I1 edge prediction (the
-// segment index after empty segments were dropped), so the pass recomputes
-// the predicted velocities for q exactly as that segment stores them.
-void link_vertex_edge(LaunchDesc& d) {
-    int ve = -1, pe = -1;
-    for (int k = 0; k < d.nseg; ++k) {
-        if (d.seg[k].type == SEG_VE) ve = k;
-        if (d.seg[k].type == SEG_PRED && d.seg[k].elem == ELEM_EDGE) pe = k;
-    }
-    if (ve >= 0) d.seg[ve].flag = pe;
-}
-
-
 void plan_lts3(lts_state_s* S, int parity, std::vector<LaunchDesc>& out) {
     const RegionsHost& r = S->reg->r;
     Planner P{S, r, r.cb, r.eb, r.vb, S->kc.comp};
@@ -569,18 +458,12 @@ void plan_lts3(lts_state_s* S, int parity, std::vector<LaunchDesc>& out) {
     const int s1_hi = far ? B_C4 : B_CREST;
     const int s2_hi = far ? B_C2 : B_CREST;
     auto ring_halo = [&](int hi) { return hi < B_CREST ? P.ring(hi + 1, hi + 1) : none; };
-    // vertex-edge plans: the fine substeps' third stages alternate between
-    // x_new and x_tmp, so both hold the coarse halo's old values
-    const bool ve = S->ve;
-    const SV& XT = S->buf[4];
     out.push_back(P.launch(0, X0, {P.vert(B_F3, std::min(s1_hi + 1, (int)B_CREST)),
-                                   P.copy(true, B_I2, B_C2, X0, XN, 0),
-                                   ve ? P.copy(true, B_I2, B_C2, X0, XT, 0) : none}, KEY_STEP1 + 0));
+                                   P.copy(true, B_I2, B_C2, X0, XN, 0)}, KEY_STEP1 + 0));
     out.push_back(P.launch(1, X0, {P.upd(true, B_F2, s1_hi, X0, X0, X1, A1, dt), ring_halo(s1_hi)},
                            KEY_STEP1 + 1));
     out.push_back(P.launch(2, X0, {P.upd(false, B_F2, s1_hi, X0, X0, X1, A1, dt),
                                    P.copy(false, B_I2, B_C2, X0, XN, 0),
-                                   ve ? P.copy(false, B_I2, B_C2, X0, XT, 0) : none,
                                    P.copy(true, B_I1, B_I1, X1, S->P1c, I1)}, KEY_STEP1 + 2));
     out.push_back(P.launch(0, X1, {P.vert(B_F1, std::min(s2_hi + 1, (int)B_CREST)),
                                    P.copy(false, B_I1, B_I1, X1, S->P1e, I1e)}, KEY_STEP2 + 0));
@@ -590,17 +473,12 @@ void plan_lts3(lts_state_s* S, int parity, std::vector<LaunchDesc>& out) {
                                    P.copy(true, B_I1, B_I1, X2, S->P2c, I1)}, KEY_STEP2 + 2));
     const size_t after_step2 = out.size();
     for (auto& d : out) d.l2 = 2;   // Steps 1 and 2 stream the coarse region
-    // Step 3: M fine substeps on F, correction terms on I1 u I2, I1 predicted.
-    // Vertex-edge plans: every right-hand side but the last ends with a
-    // vertex-edge launch that also forms q_v of the next one's input, so
-    // only the first has a vertex launch; the third stage of substep k
-    // writes Y(k+1), with Y(M) = x_new and the buffers alternating before it.
-    auto Y = [&](int j) -> const SV& { return (!ve || (M - j) % 2 == 0) ? XN : XT; };
+    // Step 3: M fine substeps on F, correction terms on I1 u I2, I1 predicted
     for (int k = 0; k < M; ++k) {
-        const SV& old = (k == 0) ? X0 : Y(k);
+        const SV& old = (k == 0) ? X0 : XN;
         for (int s = 1; s <= 3; ++s) {
             const SV& in = (s == 1) ? old : (s == 2 ? X1 : X2);
-            const SV& o = (s == 1) ? X1 : (s == 2 ? X2 : Y(k + 1));
+            const SV& o = (s == 1) ? X1 : (s == 2 ? X2 : XN);
             const double a = (s == 1) ? A1 : (s == 2 ? A2 : A3);
             const double D = (s == 1) ? dtM : (s == 2 ? dtM / 4.0 : 2.0 * dtM / 3.0);
             // prediction of I1 for the next stage that reads it
@@ -615,20 +493,13 @@ void plan_lts3(lts_state_s* S, int parity, std::vector<LaunchDesc>& out) {
                 pc = P.pred(true, X0, o, k + 1, M, 1);
                 pe = P.pred(false, X0, o, k + 1, M, 1);
             }
-            const bool first = k == 0 && s == 1, last = k == M - 1 && s == 3;
-            const SegDesc snap = first ? P.copy(false, B_I1, B_I1, X2, S->P2e, I1e) : none;
+            const SegDesc snap = (k == 0 && s == 1) ? P.copy(false, B_I1, B_I1, X2, S->P2e, I1e) : none;
             const int key = KEY_STEP3 + 9 * k + 3 * (s - 1);
-            if (!ve || first) out.push_back(P.launch(0, in, {P.vert(B_FDEEP, B_C1), snap}, key + 0));
+            out.push_back(P.launch(0, in, {P.vert(B_FDEEP, B_C1), snap}, key + 0));
             out.push_back(P.launch(1, in, {P.upd(true, B_FDEEP, B_F1, old, in, o, a, D),
                                            P.acc(true, s - 1, k == 0), P.ring(B_C1, B_C1), pc}, key + 1));
-            if (ve && !last) {
-                out.push_back(P.launch(4, in, {P.vedge(B_FDEEP, B_C1, B_FDEEP, B_F1, old, o, o, a, D),
-                                               P.acc(false, s - 1, k == 0), pe}, key + 2));
-                link_vertex_edge(out.back());
-            } else {
-                out.push_back(P.launch(2, in, {P.upd(false, B_FDEEP, B_F1, old, in, o, a, D),
-                                               P.acc(false, s - 1, k == 0), pe}, key + 2));
-            }
+            out.push_back(P.launch(2, in, {P.upd(false, B_FDEEP, B_F1, old, in, o, a, D),
+                                           P.acc(false, s - 1, k == 0), pe}, key + 2));
         }
     }
     for (size_t k = after_step2; k < out.size(); ++k) out[k].l2 = 1;   // fine substeps stay in L2
@@ -1073,7 +944,7 @@ int state_alloc(lts_state_s* S) {
     // state-sized arrays hold every layer ([element * L + layer])
     const size_t Ly = static_cast<size_t>(S->kc.layers);
     auto A = [&](size_t n) { return S->arena.alloc(n * Ly * T, err); };
-    for (int k = 0; k < (S->ve ? 5 : 4); ++k) {
+    for (int k = 0; k < 4; ++k) {
         S->buf[k].hh = A(m.nC);
         S->buf[k].uh = A(m.nE);
         if (comp) {
@@ -1595,7 +1466,6 @@ int lts_state_create(lts_mesh mesh, lts_regions reg, const double* h0, const dou
         return set_error(LTS_EINVAL, "coarse_schedule must be LTS_COARSE_FAR, _STEP4 or _SERIAL");
     if (p->kernel_path != 0 && p->kernel_path != 1)
         return set_error(LTS_EINVAL, "kernel_path must be 0 (three launches) or 1 (fused tiles)");
-    if (p->vertex_edge != 0 && p->vertex_edge != 1) return set_error(LTS_EINVAL, "vertex_edge must be 0 or 1");
     {
         const int nv = (reg->r.max_local_verts + 3) & ~3;
         S->kc.tile_smem = static_cast<int>(S->tsz) * (nv + (S->kc.maxdeg + 1) * reg->r.max_local_cells);
@@ -1634,8 +1504,6 @@ int lts_state_create(lts_mesh mesh, lts_regions reg, const double* h0, const dou
     reg->ref++;
     S->reg = reg;
     S->multi = multi;
-    S->ve = p->vertex_edge == 1 && p->mode == LTS_MODE_LTS && reg->r.order == 3 && !multi &&
-            layers == 1 && p->kernel_path == 0;
     rc = state_alloc(S.get());
     if (rc != LTS_OK) {
         release_regions(reg);

@@ -51,14 +51,6 @@ struct Tables {
     const T* vk0; const T* vk1; const T* vk2;         // [nV] A_{c,v} / A_v
     const T* vd0; const T* vd1; const T* vd2;         // [nV] t_{e,v} d_e / A_v
     const T* f;                                        // [nV] Coriolis parameter
-    // vertex-edge pass (kind 4): per vertex v and its edge k = ve_k[v], the
-    // edge's 1/d_e and bottom difference (copies of rdc, db) and, in bits
-    // 13k..13k+12 of vinf[v]: the edge's slot in ec0 (4 bits) and in ec1
-    // (4 bits), which of vc0..vc2 are ec0 and ec1 (2 bits each), and whether
-    // v is the edge's owner, the one of its two vertices that stores it (1)
-    const T* vrd0; const T* vrd1; const T* vrd2;      // [nV]
-    const T* vdb0; const T* vdb1; const T* vdb2;      // [nV]
-    const unsigned long long* vinf;                    // [nV]
     // tiles of the fused kernel (kind 3)
     const int4* ta;      // [ntiles] {cell begin, own cells, halo begin, local cells}
     const int4* tbk;     // [ntiles] {edge begin, edge end, vertex-list begin, local vertices}
@@ -77,18 +69,7 @@ struct Tables {
 // kind 0 (vertex): q_v; kind 1 (ring, one thread per cell): K_i, the
 // per-slot potential-vorticity contributions and H_i with its stage update;
 // kind 2 (edge): U_e from the ring results, with its stage update.
-// Kind 4 (vertex-edge) replaces an edge launch and the next right-hand
-// side's vertex launch: one thread per vertex forms U_e and the update of
-// each of its edges (both vertices of an edge compute it, its owner stores
-// it), then q_v from those new values, so a right-hand side that follows
-// another is two launches.  Pointwise segments (PRED, COPY, REPLAY) may ride
-// in any launch.
-// SEG_VE: begin/end = vertices; base/base2 = the updated edges [base, base2);
-// c[0], c[1] = a, D; p[0], p[1] = x_old (u, lo); p[3], p[4] = x_out (u, lo);
-// p[5] = thickness and p[6] = velocity of the next right-hand side's input
-// (read outside the updated and predicted edges); flag = the launch's
-// segment index of the I1 edge prediction (SEG_PRED), whose values the pass
-// recomputes for q, or -1.
+// Pointwise segments (PRED, COPY, REPLAY) may ride in any launch.
 enum SegType : int {
     SEG_VERT = 0,       // q_v from the launch's input state
     SEG_RING = 1,       // ring results only (halo cells of the updated edges)
@@ -100,9 +81,6 @@ enum SegType : int {
     SEG_COPY = 7,       // dst[i - base_dst] = src[i - base_src]   (hi and lo)
     SEG_REPLAY = 8,     // Step 5: three stage combinations from the accumulated RHS
     SEG_TILE = 9,       // fused right-hand side over tiles [begin, end) (one block per tile)
-    SEG_VE = 10,        // vertex-edge pass over vertices [begin, end): U_e and the update of
-                        // the edges in [base, base2) around each vertex (its owner stores
-                        // them), then q_v of the next right-hand side's input
 };
 
 // Largest cell degree the ring kernel is compiled for (variants 8 and 16).
@@ -133,7 +111,7 @@ enum : int { ELEM_CELL = 0, ELEM_EDGE = 1, ELEM_VERT = 2 };
 enum : int { FAM_FULL = 0, FAM_I1 = 1, FAM_I = 2 };
 
 struct LaunchDesc {
-    int kind = 0;             // 0 = vertex, 1 = ring, 2 = edge, 3 = fused tiles, 4 = vertex-edge
+    int kind = 0;             // 0 = vertex, 1 = ring, 2 = edge, 3 = fused tiles
     int nseg = 0;
     SegDesc seg[MAXSEG];
     const void* in_h = nullptr;   // input state (hi words) of the RHS
@@ -225,6 +203,6 @@ struct StateView {
     int device;
     cudaStream_t stream;
 };
-constexpr int NKINDS = 5;
+constexpr int NKINDS = 4;
 
 }  // namespace lts

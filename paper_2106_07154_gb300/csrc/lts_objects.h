@@ -129,10 +129,7 @@ struct lts_state_s {
     std::vector<PendingDiag> pending_diag;
     DeviceArena arena;
     const void* tables = nullptr;
-    SV buf[5];            // [parity] = x_old, [1-parity] = x_new, [2] = x_1st, [3] = x_2nd,
-                          // [4] = x_tmp (vertex-edge plans: the third-stage output of every
-                          // other fine substep, so no substep updates its input in place)
-    bool ve = false;      // the fine substeps run the vertex-edge pass (kind 4)
+    SV buf[4];            // [parity] = x_old, [1-parity] = x_new, [2] = x_1st, [3] = x_2nd
     SV P1c, P1e, P2c, P2e;   // interface-1 snapshots of the coarse 1st / 2nd stage
     void* acc_c[3] = {};  // correction terms on I1 u I2 cells (Steps 3.x.2)
     void* acc_e[3] = {};

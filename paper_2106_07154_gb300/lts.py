@@ -27,8 +27,8 @@ LTS_MODE_LTS = 0
 LTS_MODE_LTS3 = 0
 LTS_MODE_SSPRK3 = 1
 LTS_MODE_SSPRK2 = 2
-LTS_NKINDS = 5
-KIND_NAMES = ("vertex", "ring", "edge", "tile", "vertex_edge")
+LTS_NKINDS = 4
+KIND_NAMES = ("vertex", "ring", "edge", "tile")
 PATH_THREE = 0
 PATH_FUSED = 1
 LTS_ORDER_HILBERT = 0
@@ -83,7 +83,7 @@ class lts_params(C.Structure):
                 ("block_size", C.c_int32), ("profile", C.c_int32), ("pdl", C.c_int32),
                 ("kernel_path", C.c_int32), ("stream", C.c_void_p), ("no_l2_hints", C.c_int32),
                 ("layers", C.c_int32), ("ring_occupancy", C.c_int32), ("coarse_schedule", C.c_int32),
-                ("elems_per_thread", C.c_int32), ("vertex_edge", C.c_int32)]
+                ("elems_per_thread", C.c_int32)]
 
 
 class lts_tune_entry(C.Structure):
@@ -340,20 +340,17 @@ def make_params(g: float, dt: float, precision: int = LTS_FP32, mode: int = LTS_
                 compensated: bool = True, use_graph: bool = True, block_size: int = 0,
                 profile: int = 0, stream: int | None = None, pdl: bool = True,
                 kernel_path: int = 0, l2_hints: bool = True, coarse_schedule: int = 0,
-                layers: int = 1, ring_occupancy: int = 0, elems_per_thread: int = 0,
-                vertex_edge: bool = False):
+                layers: int = 1, ring_occupancy: int = 0, elems_per_thread: int = 0):
     return lts_params(g, dt, precision, mode, int(compensated), int(use_graph), block_size,
                       int(profile), int(pdl), int(kernel_path), stream, int(not l2_hints),
-                      int(layers), int(ring_occupancy), int(coarse_schedule), int(elems_per_thread),
-                      int(vertex_edge))
+                      int(layers), int(ring_occupancy), int(coarse_schedule), int(elems_per_thread))
 
 
 def params_dict(p: lts_params) -> dict:
     return {"block_size": p.block_size, "kernel_path": p.kernel_path, "pdl": bool(p.pdl),
             "l2_hints": not p.no_l2_hints, "coarse_schedule": int(p.coarse_schedule),
             "layers": int(p.layers), "ring_occupancy": int(p.ring_occupancy),
-            "elems_per_thread": int(p.elems_per_thread), "use_graph": bool(p.use_graph),
-            "vertex_edge": bool(p.vertex_edge)}
+            "elems_per_thread": int(p.elems_per_thread), "use_graph": bool(p.use_graph)}
 
 
 def lts_autotune(mesh_h, reg_h, h0, u0, base: lts_params, steps: int = 20,
@@ -579,7 +576,7 @@ class Model:
                  kernel_path: int = 0, tile_cells: int = 0, l2_hints: bool = True,
                  coarse_schedule: int = 0, ordering: int = LTS_ORDER_HILBERT,
                  autotune: int = 0, tune_ordering: bool = False, order: int = 3, layers: int = 1,
-                 ring_occupancy: int = 0, elems_per_thread: int = 0, vertex_edge: bool = False):
+                 ring_occupancy: int = 0, elems_per_thread: int = 0):
         """autotune > 0: time that many coarse steps per candidate configuration
         (lts_autotune) and build the state with the fastest; the choice is in
         self.tuned.  layers > 1: h0, u0 (and read/write) are [layers][nCells],
@@ -602,7 +599,7 @@ class Model:
             lts_regions_ordering(self.reg_h, ordering)
         p = make_params(g, dt, precision, mode, compensated, use_graph, block_size, profile, stream,
                         pdl, kernel_path, l2_hints, coarse_schedule, self.layers, ring_occupancy,
-                        elems_per_thread, vertex_edge)
+                        elems_per_thread)
         h0 = np.ascontiguousarray(h0, np.float64).reshape(-1)
         u0 = np.ascontiguousarray(u0, np.float64).reshape(-1)
         if h0.size != self.layers * self.nC or u0.size != self.layers * self.nE:

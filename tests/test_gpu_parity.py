@@ -255,30 +255,6 @@ def test_two_elements_per_thread_bitwise(sphw, precision, mode, order):
         assert np.array_equal(h, out[0][0]) and np.array_equal(u, out[0][1])
 
 
-@pytest.mark.parametrize("precision", [lts.LTS_FP64, lts.LTS_FP32])
-@pytest.mark.parametrize("M,layers_i", [(1, 1), (2, 1), (3, 1), (4, 2), (8, 1)])
-def test_vertex_edge_pass_bitwise(sphw, precision, M, layers_i):
-    """The vertex-edge plan (every fine right-hand side after the first is a
-    ring launch and a vertex-edge launch that also forms the next q_v; the
-    third stages alternate between two buffers) equals the plan with a
-    separate vertex launch per right-hand side bit for bit, for odd and even
-    M, thick interfaces, with the graph and with direct launches."""
-    out, kinds = [], []
-    for ve, graph in ((False, True), (True, True), (True, False)):
-        with lts.Model(sphw.mesh, sphw.fine_mask, M, sphw.h0, sphw.u0, sphw.dt * M / sphw.M,
-                       precision=precision, interface_layers=layers_i, vertex_edge=ve,
-                       use_graph=graph) as m:
-            kinds.append(m.stats()["launches_per_kind"])
-            m.step(4)
-            out.append(m.read()[:2])
-    # 3M - 1 vertex-edge launches replace as many edge and vertex launches
-    fused = 3 * M - 1
-    assert kinds[1][4] == fused and kinds[0][4] == 0
-    assert kinds[1][0] == kinds[0][0] - fused and kinds[1][2] == kinds[0][2] - fused
-    for h, u in out[1:]:
-        assert np.array_equal(h, out[0][0]) and np.array_equal(u, out[0][1])
-
-
 def test_elems_per_thread_is_checked(sphw):
     with pytest.raises(lts.LtsError) as ei:
         lts.Model(sphw.mesh, sphw.fine_mask, sphw.M, sphw.h0, sphw.u0, sphw.dt, elems_per_thread=3)
