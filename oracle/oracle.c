@@ -13,8 +13,7 @@
  * order; results are written only to the index sets the algorithm names.
  * There is no blocking, fusion or reordering.
  *
- * Readings of the paper where it is silent, garbled or inconsistent (each is
- * listed in the design notes):
+ * Readings of the paper where it is silent, garbled or inconsistent:
  *  R1 (Eq. 5, garbled): Fbar^e = {edges of Fbar^c cells} \ F^e.  Step 3
  *     advances the fine edges F^e u Fbar^e (all edges of F^c cells that are
  *     not interface edges); Step 3's initialisation covers the same set.

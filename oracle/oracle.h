@@ -22,9 +22,10 @@
  *   l_e = dvEdge (primal Voronoi edge length), d_e = dcEdge (dual edge,
  *   cell-to-cell distance), A_i = areaCell, A_v = areaTriangle.
  *
- * Parity status (also recorded in the design notes): every function here is
- * pinned by the CPU tests (closed forms, invariants, brute force, and the
- * M = 1 identity of the paper's Remark in Section 2.2).  The paper prints no
+ * Parity status: every function here is pinned by the CPU tests (closed
+ * forms, invariants, brute force, the M = 1 identity of the paper's Remark
+ * in Section 2.2, and for the energy of reading R8 a closed form and its
+ * conservation by the semi-discrete system of Eq. (1)).  The paper prints no
  * solution values, so no pin compares against a printed number.
  */
 #ifndef LTS_ORACLE_H

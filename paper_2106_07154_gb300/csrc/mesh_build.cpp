@@ -10,8 +10,10 @@
 //
 // Geometry (Appendix B): x_v is the circumcentre of its Delaunay triangle,
 // x_e the midpoint of the cell pair (where the cell-cell arc meets the
-// vertex-vertex arc of a Voronoi diagram), d_e = |x_c1 - x_c0|, l_e =
-// |x_v1 - x_v0|, kite (i, v) = signed area of (x_i, x_e1, x_v, x_e2),
+// vertex-vertex arc of a Voronoi diagram), d_e = the distance from x_c0 to
+// x_c1 and l_e = the distance from x_v0 to x_v1 (great-circle arcs of
+// radius R on the sphere, straight lines on the plane), kite (i, v) =
+// signed area of (x_i, x_e1, x_v, x_e2),
 // A_i = sum of the kites of cell i, A_v = sum of the kites at vertex v.
 // Orientation: cellsOnEdge[2e] is the larger cell index (the Remark of
 // Appendix B: i1 > i2 => n_{e,i1} = 1); verticesOnEdge[2e+1] is the left end.

@@ -311,7 +311,19 @@ def two_caps(n: int = 2621442, seed: int = 5, lloyd_iters: int = 200, cfl: float
 
 
 def workload(name: str, **kw) -> Workload:
-    """The named synthetic workloads (sizes and recipes in the design notes)."""
+    """The named synthetic workloads, seeded stand-ins for the meshes of the
+    paper's Section 3 (which are not available):
+      hex_1024            32x32 doubly periodic hexagons, dc = 10 km, f-plane, flat
+                          bottom, 1 m Gaussian bump (sigma 40 km) at a seeded centre,
+                          fine region a 60 km circle, M = 2
+      scvt_40962          spherical SCVT (200 Lloyd iterations), 4:1 cap of radius 15
+                          degrees (tanh width 5) at (3 pi/2, pi/6), balanced zonal flow
+                          u0 = 20 m/s, 2000 m Gaussian mountain, M = 4
+      scvt_655362         the same recipe at 655,362 cells with an 8:1 cap, M = 8
+      scvt_2562           small test sphere (4:1 cap, 60 Lloyd iterations)
+      scvt_2621442_2caps  two caps (8:1 with M = 8, 4:1 with M = 4), 32 seeded
+                          ridges, 5 m of spectral-slope -3 noise
+      ensemble64          64 uneven spheres (see ensemble)"""
     if name == "hex_1024":          # 32x32 periodic hexagons, M = 2, 100 coarse steps
         return hex_bump(**kw)
     if name == "scvt_40962":        # 4:1 cap, M = 4, 500 coarse steps
