@@ -247,6 +247,43 @@ def predicted_speedup(counts, M):
                                                                 "coarse": int(nC)}}
 
 
+def set_omp_threads(n: int) -> bool:
+    """Sets the OpenMP thread count of the calling thread (the oracle's
+    parallel loops then use n threads); False if libgomp is not loaded."""
+    import ctypes
+
+    try:
+        ctypes.CDLL("libgomp.so.1").omp_set_num_threads(int(n))
+        return True
+    except (OSError, AttributeError):
+        return False
+
+
+def oracle_single_thread(w, budget_s=20.0):
+    """The oracle on one host thread: LTS3 coarse steps of the full mesh until
+    `budget_s` is spent (at least one); cell-updates/s, steps, seconds."""
+    import oracle
+
+    o = oracle.Oracle(w.mesh)
+    labels = oracle_labels(o, w)
+    cores = oracle.num_threads()
+    if not set_omp_threads(1):
+        return None
+    try:
+        h, u = w.h0, w.u0
+        steps, t = 0, 0.0
+        while steps == 0 or t < budget_s:
+            t0 = time.perf_counter()
+            h, u = oracle_lts(o, w, h, u, 1, labels)
+            t += time.perf_counter() - t0
+            steps += 1
+            if steps >= 3:
+                break
+    finally:
+        set_omp_threads(cores)
+    return w.nCells * steps / t, steps, t
+
+
 def oracle_sample(w, nsteps_cap=3, budget_s=20.0):
     """Times the FP64 oracle's LTS3 coarse step on the full workload; returns
     (cell-updates/s, steps, seconds, threads, result)."""
@@ -676,6 +713,41 @@ def extras(args, w, model, stats, stream, h_gpu, u_gpu, diag):
     out["cpu_baseline"] = {"value": cells_per_s, "unit": UNIT, "cores": cores, "kind": "oracle",
                            "sample": f"{n_or} LTS3 coarse step(s) of the full mesh by the FP64 C "
                                      f"oracle ({t_or:.1f} s)", "cpu": cpu_model()}
+    st1 = oracle_single_thread(w)
+    if st1 is not None:
+        out["cpu_baseline"]["single_thread"] = {
+            "value": st1[0], "unit": UNIT, "cores": 1,
+            "sample": f"{st1[1]} LTS3 coarse step(s) of the full mesh by the FP64 C oracle on one "
+                      f"thread ({st1[2]:.1f} s)"}
+    # ---- the workload's own run length (hex_1024: 100 coarse steps,
+    #      scvt_40962: 500): FP32 and FP64 against the oracle after that many
+    #      steps, and the drift of mass and energy, where the oracle needs at
+    #      most a minute for them on the host cores
+    if t_or / n_or * w.nsteps <= 60.0:
+        import oracle
+
+        o = oracle.Oracle(w.mesh)
+        labels = oracle_labels(o, w)
+        t0 = time.perf_counter()
+        rhn, run_ = oracle_lts(o, w, w.h0, w.u0, w.nsteps, labels)
+        t_full = time.perf_counter() - t0
+        res = {"coarse_steps": w.nsteps,
+               "oracle": {"seconds": t_full, "value": nC * w.nsteps / t_full, "unit": UNIT,
+                          "cores": cores,
+                          "mass_drift": (o.mass(rhn) - o.mass(w.h0)) / o.mass(w.h0),
+                          "energy_drift": (o.energy(rhn, run_, w.g) - o.energy(w.h0, w.u0, w.g))
+                          / o.energy(w.h0, w.u0, w.g)}}
+        for name, p_ in (("fp32", lts.LTS_FP32), ("fp64", lts.LTS_FP64)):
+            with lts.Model(w.mesh, w.fine_mask, w.M, w.h0, w.u0, w.dt, w.g, precision=p_,
+                           compensated=True, stream=stream.cuda_stream) as m_:
+                _, _, d0 = m_.read()
+                m_.step(w.nsteps)
+                hn, un_, dn = m_.read()
+            res[name] = {"h_rel_maxnorm": float(np.max(np.abs(hn - rhn)) / np.max(np.abs(rhn))),
+                         "u_rel_maxnorm": float(np.max(np.abs(un_ - run_)) / np.max(np.abs(run_))),
+                         "mass_drift": (dn["mass"] - d0["mass"]) / d0["mass"],
+                         "energy_drift": (dn["energy"] - d0["energy"]) / d0["energy"]}
+        out["run_vs_oracle"] = res
     out["error_vs_oracle_1step"] = {
         "h_rel_maxnorm": float(np.max(np.abs(h1 - rh)) / np.max(np.abs(rh))),
         "u_rel_maxnorm": float(np.max(np.abs(u1 - ru)) / np.max(np.abs(ru)))}
@@ -885,6 +957,43 @@ def run_ensemble(args):
                                 "kind": "oracle", "cpu": cpu_model(),
                                 "sample": f"one LTS3 coarse step of the two smallest members "
                                           f"({cells} cells) by the FP64 C oracle ({t_or:.1f} s)"}
+        cores = oracle.num_threads()
+        if set_omp_threads(1):
+            t0 = time.perf_counter()
+            for i in small:
+                w = ws[i]
+                o = oracle.Oracle(w.mesh)
+                cl, el = o.regions(w.fine_mask)
+                o.lts3(w.h0, w.u0, cl, el, w.M, w.dt, 1, g=w.g)
+            t1 = time.perf_counter() - t0
+            set_omp_threads(cores)
+            line["cpu_baseline"]["single_thread"] = {
+                "value": cells / t1, "unit": UNIT, "cores": 1,
+                "sample": f"the same step on one thread ({t1:.1f} s)"}
+        # the two smallest members as an ensemble of their own: 20 coarse steps
+        # in FP32 against the oracle, and the drift of mass and energy
+        nref = 20
+        sub = [lts.Model(ws[i].mesh, ws[i].fine_mask, ws[i].M, ws[i].h0, ws[i].u0, ws[i].dt, ws[i].g,
+                         precision=lts.LTS_FP32, compensated=True) for i in small]
+        d0s = [m.read()[2] for m in sub]
+        sens = lts.Ensemble(sub, stream=stream.cuda_stream)
+        sens.step(nref)
+        chk = []
+        for j, i in enumerate(small):
+            w = ws[i]
+            hg, ug, dn = sens.read(j)
+            o = oracle.Oracle(w.mesh)
+            cl, el = o.regions(w.fine_mask)
+            rh, ru = o.lts3(w.h0, w.u0, cl, el, w.M, w.dt, nref, g=w.g)
+            chk.append({"cells": w.nCells, "M": w.M, "coarse_steps": nref,
+                        "h_rel_maxnorm": float(np.max(np.abs(hg - rh)) / np.max(np.abs(rh))),
+                        "u_rel_maxnorm": float(np.max(np.abs(ug - ru)) / np.max(np.abs(ru))),
+                        "mass_drift": (dn["mass"] - d0s[j]["mass"]) / d0s[j]["mass"],
+                        "energy_drift": (dn["energy"] - d0s[j]["energy"]) / d0s[j]["energy"]})
+        sens.close()
+        for m in sub:
+            m.close()
+        line["members_vs_oracle"] = chk
     ens.close()
     for m in models:
         m.close()

@@ -160,6 +160,13 @@ int build_union_tables(lts_ensemble_s* E, Tables<T>& t) {
     t.snl = up(snl);
     t.sR = up(sR);
     t.sK = up(sK);
+    {
+        std::vector<int4> sidx;
+        std::vector<float2> scf;
+        pack_ring_slots<T>(se, sn, sv, snl, sR, sK, sidx, scf);
+        t.sidx = up(sidx);
+        t.scf = sizeof(T) == 4 ? up(scf) : nullptr;
+    }
     t.rA = up(rA);
     t.b = up(b);
     t.ec0 = up(ec0);

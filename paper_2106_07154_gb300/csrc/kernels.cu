@@ -990,9 +990,17 @@ void fill_args(DevArgs<T>& a, const LaunchDesc& d, const void* tables, int smem,
     a.L = 1;
 }
 
+// A table set without the ring pass's packed slot rows cannot run a ring
+// launch: refused on the host instead of faulting on the device.
+template <class T>
+bool ring_tables_ok(const Tables<T>& t) {
+    return t.sidx != nullptr && (sizeof(T) != 4 || t.scf != nullptr);
+}
+
 template <class T, bool COMP, int MAXR>
 cudaError_t launch_t(const LaunchDesc& d, const void* tables, int block, bool pdl, int smem, int* flag,
                      cudaStream_t st, int layers, int ring_occ, int ept) {
+    if (d.kind == 1 && !ring_tables_ok(*static_cast<const Tables<T>*>(tables))) return cudaErrorInvalidValue;
     DevArgs<T> a;
     fill_args(a, d, tables, smem, flag);
     a.L = layers;
@@ -1042,6 +1050,7 @@ cudaError_t launch_t(const LaunchDesc& d, const void* tables, int block, bool pd
 template <class T, bool COMP, int MAXR>
 cudaError_t launch_table_t(const LaunchDesc& d, const void* dsegs, int nseg, int vblocks, int grid,
                            const void* tables, int block, bool pdl, int* flag, cudaStream_t st) {
+    if (d.kind == 1 && !ring_tables_ok(*static_cast<const Tables<T>*>(tables))) return cudaErrorInvalidValue;
     DevArgs<T> a;
     fill_args(a, d, tables, 0, flag);
     a.nseg = 0;

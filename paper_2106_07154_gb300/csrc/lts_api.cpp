@@ -71,21 +71,9 @@ int build_tables(lts_regions_s* R, int which, Tables<T>& t) {
     t.sR = up(co.sR);
     t.sK = up(co.sK);
     {
-        std::vector<int4> sidx(r.se.size());
-        std::vector<float2> scf(sizeof(T) == 4 ? r.se.size() : 0);
-        for (size_t x = 0; x < r.se.size(); ++x) {
-            int bits = 0;
-            if (sizeof(T) == 4) {
-                const float f = static_cast<float>(co.snl[x]);
-                std::memcpy(&bits, &f, sizeof(bits));
-                scf[x].x = static_cast<float>(co.sR[x]);
-                scf[x].y = static_cast<float>(co.sK[x]);
-            }
-            sidx[x].x = r.se[x];
-            sidx[x].y = r.sn[x];
-            sidx[x].z = r.sv[x];
-            sidx[x].w = bits;
-        }
+        std::vector<int4> sidx;
+        std::vector<float2> scf;
+        pack_ring_slots<T>(r.se, r.sn, r.sv, co.snl, co.sR, co.sK, sidx, scf);
         t.sidx = up(sidx);
         t.scf = sizeof(T) == 4 ? up(scf) : nullptr;
     }

@@ -486,6 +486,34 @@ void coefficient_tables(const HostMesh& m, const RegionsHost& r, CoefTables<T>& 
 template void coefficient_tables<float>(const HostMesh&, const RegionsHost&, CoefTables<float>&);
 template void coefficient_tables<double>(const HostMesh&, const RegionsHost&, CoefTables<double>&);
 
+template <class T>
+void pack_ring_slots(const std::vector<int>& se, const std::vector<int>& sn, const std::vector<int>& sv,
+                     const std::vector<T>& snl, const std::vector<T>& sR, const std::vector<T>& sK,
+                     std::vector<int4>& sidx, std::vector<float2>& scf) {
+    const size_t n = se.size();
+    sidx.resize(n);
+    scf.assign(sizeof(T) == 4 ? n : 0, float2{});
+    for (size_t x = 0; x < n; ++x) {
+        int bits = 0;
+        if (sizeof(T) == 4) {
+            const float f = static_cast<float>(snl[x]);
+            std::memcpy(&bits, &f, sizeof(bits));
+            scf[x].x = static_cast<float>(sR[x]);
+            scf[x].y = static_cast<float>(sK[x]);
+        }
+        sidx[x].x = se[x];
+        sidx[x].y = sn[x];
+        sidx[x].z = sv[x];
+        sidx[x].w = bits;
+    }
+}
+template void pack_ring_slots<float>(const std::vector<int>&, const std::vector<int>&, const std::vector<int>&,
+                                     const std::vector<float>&, const std::vector<float>&,
+                                     const std::vector<float>&, std::vector<int4>&, std::vector<float2>&);
+template void pack_ring_slots<double>(const std::vector<int>&, const std::vector<int>&, const std::vector<int>&,
+                                      const std::vector<double>&, const std::vector<double>&,
+                                      const std::vector<double>&, std::vector<int4>&, std::vector<float2>&);
+
 // TRiSK weight of Eq. (weights) for e' = slot j of cell c and e = slot p,
 // with the path taken counter-clockwise from e' to e (used to validate a
 // caller's weightsOnEdge).

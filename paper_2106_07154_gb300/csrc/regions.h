@@ -74,6 +74,14 @@ int compute_regions_multi(const HostMesh& m, const int8_t* region_of_cell, int n
                           RegionsHost& r);
 template <class T>
 void coefficient_tables(const HostMesh& m, const RegionsHost& r, CoefTables<T>& o);
+// The ring pass's packed slot rows (Tables::sidx, Tables::scf) from the
+// slot-major index and coefficient arrays: {edge, neighbour, vertex, the
+// bits of n l in FP32 (0 in FP64)} and, in FP32 only, {kite fraction, K
+// coefficient}.  Every table set the ring kernel reads must carry them.
+template <class T>
+void pack_ring_slots(const std::vector<int>& se, const std::vector<int>& sn, const std::vector<int>& sv,
+                     const std::vector<T>& snl, const std::vector<T>& sR, const std::vector<T>& sK,
+                     std::vector<int4>& sidx, std::vector<float2>& scf);
 double derived_weight(const HostMesh& m, int c, int j, int p);
 
 }  // namespace lts
