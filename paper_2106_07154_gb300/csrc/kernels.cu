@@ -51,6 +51,8 @@ struct DevArgs {
     int l2;           // 0 no hint, 1 keep in L2 (evict_last), 2 stream (evict_first)
     int smem;         // dynamic shared memory of the launch (fused tiles)
     int L;            // layers per element (multi-layer states; 1 otherwise)
+    int lpt;          // multi-layer states: layers per thread (consecutive layers of one element)
+    int G;            // multi-layer states: thread groups per element, ceil(L / lpt)
     // segment-table launches (ensembles): segments in device memory
     const DevSeg<T>* gseg;
     int ngseg;
@@ -338,69 +340,110 @@ __device__ __forceinline__ void vertex_pv(const DevArgs<T>& a, int v, const Lay<
 //   C_p = qt_p (w_p A - A' + P_n Asuf_p) + (w_p B - B' + P_n Bsuf_p) + b_p,
 // w_p = P_p - 1/2 (the j = p terms of A and B cancel into the last b_p).
 
+// Arithmetic of the ring core on a value type V: one layer in T (float or
+// double), or two layers in float2, where every operation is one packed
+// Blackwell FP32x2 instruction whose lanes round exactly as the scalar
+// operation (so a two-layer run equals two one-layer runs bit for bit).
+template <class V>
+struct VA;
+template <>
+struct VA<float> {
+    static __device__ __forceinline__ float cst(float x) { return x; }
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+    static __device__ __forceinline__ float neg(float a) { return -a; }
+};
+template <>
+struct VA<double> {
+    static __device__ __forceinline__ double cst(double x) { return x; }
+    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+    static __device__ __forceinline__ double neg(double a) { return -a; }
+};
+template <>
+struct VA<float2> {
+    static __device__ __forceinline__ float2 cst(float x) { return make_float2(x, x); }
+    static __device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+    static __device__ __forceinline__ float2 neg(float2 a) { return make_float2(-a.x, -a.y); }
+    // a - b is a + (-b) exactly
+    static __device__ __forceinline__ float2 sub(float2 a, float2 b) { return __fadd2_rn(a, neg(b)); }
+    static __device__ __forceinline__ float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+    static __device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+};
+
 // The ring arithmetic of one cell from its gathered slot values (slots
 // j >= n are ignored), shared by the ring pass and the fused tiles so both
-// give the same bits.  Returns H_c; C[p] for p < n and K_c on output.
-template <class T, bool COMP, int NR>
-__device__ __forceinline__ T ring_core(int n, T hc, T rA, const T (&uj)[NR], const T (&hn)[NR],
-                                       const T (&qv)[NR], const T (&snl)[NR], const T (&Rj)[NR],
-                                       const T (&sK)[NR], T (&C)[NR], T& Kc_out) {
-    T G[NR], R[NR];
-    T Kc = T(0), s = T(0), comp = T(0);
+// give the same bits.  V = T for one layer, float2 for two FP32 layers
+// (the slot coefficients then hold the same value in both lanes).
+// Returns H_c; C[p] for p < n and K_c on output.
+template <class V, bool COMP, int NR>
+__device__ __forceinline__ V ring_core(int n, V hc, V rA, const V (&uj)[NR], const V (&hn)[NR],
+                                       const V (&qv)[NR], const V (&snl)[NR], const V (&Rj)[NR],
+                                       const V (&sK)[NR], V (&C)[NR], V& Kc_out) {
+    using A = VA<V>;
+    const V zero = A::cst(0.0f), half = A::cst(0.5f);
+    V G[NR], R[NR];
+    V Kc = zero, s = zero, comp = zero;
 #pragma unroll
     for (int j = 0; j < NR; ++j) {
         const bool in = j < n;
-        const T F = mul_rn(mul_rn(T(0.5), hc + hn[j]), uj[j]);
-        const T g = in ? mul_rn(snl[j], F) : T(0);
+        const V F = A::mul(A::mul(half, A::add(hc, hn[j])), uj[j]);
+        const V g = in ? A::mul(snl[j], F) : zero;
         G[j] = g;
-        R[j] = in ? Rj[j] : T(0);
+        R[j] = in ? Rj[j] : zero;
         if (in) {
-            Kc = fma_rn(mul_rn(sK[j], uj[j]), uj[j], Kc);
+            Kc = A::fma(A::mul(sK[j], uj[j]), uj[j], Kc);
             if (COMP) {
-                T ss, ee;
-                two_sum(s, g, ss, ee);
+                // Knuth's TwoSum of (s, g): s + e == s_old + g exactly
+                const V ss = A::add(s, g);
+                const V bb = A::sub(ss, s);
+                const V ee = A::add(A::sub(s, A::sub(ss, bb)), A::sub(g, bb));
                 s = ss;
-                comp += ee;
+                comp = A::add(comp, ee);
             } else {
-                s += g;
+                s = A::add(s, g);
             }
         }
     }
     // q at v_{n-1} closes the ring for slot 0
-    T qlast = qv[0];
+    V qlast = qv[0];
 #pragma unroll
     for (int j = 1; j < NR; ++j)
         if (j == n - 1) qlast = qv[j];
-    T qt[NR], P[NR], b[NR];
-    T Pacc = T(0), A = T(0), B = T(0), A1 = T(0), B1 = T(0);
+    V qt[NR], P[NR], b[NR];
+    V Pacc = zero, Asum = zero, Bsum = zero, A1 = zero, B1 = zero;
 #pragma unroll
     for (int j = 0; j < NR; ++j) {
-        qt[j] = mul_rn(T(0.5), (j == 0 ? qlast : qv[j - 1]) + qv[j]);
+        qt[j] = A::mul(half, A::add(j == 0 ? qlast : qv[j - 1], qv[j]));
         P[j] = Pacc;
-        b[j] = mul_rn(G[j], qt[j]);
+        b[j] = A::mul(G[j], qt[j]);
         if (j < n) {
-            Pacc += R[j];
-            A += G[j];
-            B += b[j];
-            A1 = fma_rn(P[j], G[j], A1);
-            B1 = fma_rn(P[j], b[j], B1);
+            Pacc = A::add(Pacc, R[j]);
+            Asum = A::add(Asum, G[j]);
+            Bsum = A::add(Bsum, b[j]);
+            A1 = A::fma(P[j], G[j], A1);
+            B1 = A::fma(P[j], b[j], B1);
         }
     }
-    const T Pn = Pacc;
-    T Asuf = T(0), Bsuf = T(0);
+    const V Pn = Pacc;
+    V Asuf = zero, Bsuf = zero;
 #pragma unroll
     for (int p = NR - 1; p >= 0; --p) {
         if (p < n) {
-            const T w = P[p] - T(0.5);
-            const T al = fma_rn(Pn, Asuf, fma_rn(w, A, -A1));
-            const T be = fma_rn(Pn, Bsuf, fma_rn(w, B, -B1));
-            C[p] = fma_rn(qt[p], al, be) + b[p];
-            Asuf += G[p];
-            Bsuf += b[p];
+            const V w = A::sub(P[p], half);
+            const V al = A::fma(Pn, Asuf, A::fma(w, Asum, A::neg(A1)));
+            const V be = A::fma(Pn, Bsuf, A::fma(w, Bsum, A::neg(B1)));
+            C[p] = A::add(A::fma(qt[p], al, be), b[p]);
+            Asuf = A::add(Asuf, G[p]);
+            Bsuf = A::add(Bsuf, b[p]);
         }
     }
     Kc_out = Kc;
-    return -(s + comp) * rA;
+    return A::mul(A::neg(A::add(s, comp)), rA);
 }
 
 // The first UNCOND slots' tables are loaded before the dependency wait
@@ -486,6 +529,58 @@ __device__ __forceinline__ T ring_pass(const DevArgs<T>& a, int c, const Lay<LY>
     if (nmax <= 7 || MAXR <= 7) return ring_body<T, COMP, (MAXR < 7 ? MAXR : 7), LY>(a, ld, c, n, rA, S0, y);
     if (nmax <= 8 || MAXR <= 8) return ring_body<T, COMP, (MAXR < 8 ? MAXR : 8), LY>(a, ld, c, n, rA, S0, y);
     return ring_body<T, COMP, MAXR, LY>(a, ld, c, n, rA, S0, y);
+}
+
+// Two consecutive layers (y.l and y.l + 1) of an FP32 multi-layer state in
+// one ring pass: the slot tables are loaded once, the two layers' state is
+// gathered into float2 values and the ring core runs on both at once.
+template <bool COMP, int NR>
+__device__ __forceinline__ float2 ring_body_pair(const DevArgs<float>& a, const Ld& ld, int c, int n, float rA,
+                                                 const RingSlot<float> (&S0)[UNCOND], const Lay<true>& y0) {
+    const int N = a.t.nC;
+    Lay<true> y1 = y0;
+    y1.l = y0.l + 1;
+    const float2 hc = make_float2(ld(a.in_h + y0(c)), ld(a.in_h + y1(c)));
+    float2 uj[NR], hn[NR], qv[NR], snl[NR], Rj[NR], sK[NR], C[NR];
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+        const RingSlot<float> r = j < UNCOND ? S0[j % UNCOND] : (j < n ? ring_slot(a.t, ld, j, c) : S0[0]);
+        uj[j] = make_float2(ld(a.in_u + y0(r.e)), ld(a.in_u + y1(r.e)));
+        hn[j] = make_float2(ld(a.in_h + y0(r.nb)), ld(a.in_h + y1(r.nb)));
+        qv[j] = make_float2(ld(a.q + y0(r.v)), ld(a.q + y1(r.v)));
+        snl[j] = make_float2(r.snl, r.snl);
+        Rj[j] = make_float2(r.R, r.R);
+        sK[j] = make_float2(r.sK, r.sK);
+    }
+    float2 Kc;
+    const float2 H = ring_core<float2, COMP, NR>(n, hc, make_float2(rA, rA), uj, hn, qv, snl, Rj, sK, C, Kc);
+    const St st(a.l2);
+#pragma unroll
+    for (int p = 0; p < NR; ++p)
+        if (p < n) {
+            st(a.ring_c + y0(p * N + c), C[p].x);
+            st(a.ring_c + y1(p * N + c), C[p].y);
+        }
+    st(a.ring_k + y0(c), Kc.x);
+    st(a.ring_k + y1(c), Kc.y);
+    return H;
+}
+
+template <bool COMP, int MAXR>
+__device__ __forceinline__ float2 ring_pass_pair(const DevArgs<float>& a, int c, const Lay<true>& y0) {
+    const Tables<float>& t = a.t;
+    const Ld ld(a.l2);
+    const int n = ld.stat(t.cn + c);
+    RingSlot<float> S0[UNCOND];
+#pragma unroll
+    for (int j = 0; j < UNCOND; ++j) S0[j] = ring_slot(t, ld, j, c);
+    const float rA = ld.stat(t.rA + c);
+    griddep_wait();
+    const int nmax = __reduce_max_sync(__activemask(), n);
+    if (nmax <= 6) return ring_body_pair<COMP, 6>(a, ld, c, n, rA, S0, y0);
+    if (nmax <= 7 || MAXR <= 7) return ring_body_pair<COMP, (MAXR < 7 ? MAXR : 7)>(a, ld, c, n, rA, S0, y0);
+    if (nmax <= 8 || MAXR <= 8) return ring_body_pair<COMP, (MAXR < 8 ? MAXR : 8)>(a, ld, c, n, rA, S0, y0);
+    return ring_body_pair<COMP, MAXR>(a, ld, c, n, rA, S0, y0);
 }
 
 // --------------------------------------------------------------- kind 2: edge
@@ -794,25 +889,10 @@ __device__ __forceinline__ bool is_ring(int type) {
     return type == SEG_RING || type == SEG_RING_UPD || type == SEG_RING_ACC;
 }
 
-// The work of (virtual) block `vblk` of segment s.
+// The work of element i (one layer, y) of segment s.
 template <class T, bool COMP, int MAXR, int KIND, bool LY>
-__device__ __forceinline__ void phase_block(const DevArgs<T>& a, const DevSeg<T>& s, int vblk) {
+__device__ __forceinline__ void element_work(const DevArgs<T>& a, const DevSeg<T>& s, int i, const Lay<LY>& y) {
     const int type = s.type;
-    const int local = (vblk - s.block0) * blockDim.x + threadIdx.x;
-    int i, l = 0;
-    if (LY) {   // (element, layer), layers fastest
-        const int q = local / a.L;
-        i = s.begin + q;
-        l = local - q * a.L;
-    } else {
-        i = s.begin + local;
-    }
-    if (i >= s.end) return;
-    Lay<LY> y;
-    if constexpr (LY) {
-        y.L = a.L;
-        y.l = l;
-    }
     if (KIND == 0 && type == SEG_VERT) {
         vertex_pv<T, LY>(a, i, y);
     } else if (KIND == 1 && is_ring(type)) {
@@ -836,11 +916,68 @@ __device__ __forceinline__ void phase_block(const DevArgs<T>& a, const DevSeg<T>
     }
 }
 
-// The ring kind is compiled for four resident 256-thread blocks per SM (64
-// registers): on GB300 this beat both five blocks (48 registers, with
-// spills) and no limit (80 registers, three blocks) on the 655k-cell cap mesh.
+// The work of (virtual) block `vblk` of segment s.  Multi-layer states run
+// one thread per (element, group of lpt consecutive layers), groups fastest:
+// the thread repeats the element's work for each of its layers, so its mesh
+// table loads (the same addresses for every layer) are issued once and the
+// layers' state accesses are consecutive words.  Each layer's arithmetic is
+// the single-layer code's.
+template <class T, bool COMP, int MAXR, int KIND, bool LY>
+__device__ __forceinline__ void phase_block(const DevArgs<T>& a, const DevSeg<T>& s, int vblk) {
+    const int local = (vblk - s.block0) * blockDim.x + threadIdx.x;
+    if constexpr (LY) {
+        const int q = local / a.G;
+        const int i = s.begin + q;
+        if (i >= s.end) return;
+        const int l0 = (local - q * a.G) * a.lpt;
+        const int nl = min(a.lpt, a.L - l0);
+        Lay<true> y;
+        y.L = a.L;
+        int k = 0;
+        if constexpr (KIND == 1 && sizeof(T) == 4) {
+            // FP32 ring segments: two layers per ring pass (packed arithmetic)
+            if (is_ring(s.type)) {
+#pragma unroll 1
+                for (; k + 1 < nl; k += 2) {
+                    y.l = l0 + k;
+                    const float2 H = ring_pass_pair<COMP, MAXR>(a, i, y);
+                    if (s.type != SEG_RING) {
+                        const int epi = s.type == SEG_RING_ACC ? EPI_ACC : EPI_UPD;
+                        Lay<true> y1 = y;
+                        y1.l = y.l + 1;
+                        EpiOps<T> o0, o1;
+                        epi_load<T, COMP, true>(Ld(a.l2), s, epi, i, a.in_h, o0, y);
+                        epi_load<T, COMP, true>(Ld(a.l2), s, epi, i, a.in_h, o1, y1);
+                        epilogue<T, COMP, true, true>(a, s, epi, i, H.x, o0, y);
+                        epilogue<T, COMP, true, true>(a, s, epi, i, H.y, o1, y1);
+                    }
+                }
+            }
+        }
+#pragma unroll 1
+        for (; k < nl; ++k) {
+            y.l = l0 + k;
+            element_work<T, COMP, MAXR, KIND, true>(a, s, i, y);
+        }
+    } else {
+        const int i = s.begin + local;
+        if (i >= s.end) return;
+        element_work<T, COMP, MAXR, KIND, false>(a, s, i, Lay<false>{});
+    }
+}
+
+// Resident 256-thread blocks per SM the ring kind is compiled for.  FP32
+// single-layer: four (64 registers), which on GB300 beat both five blocks
+// (48 registers, with spills) and no limit (80 registers, three blocks) on
+// the 655k-cell cap mesh.  Multi-layer states (two layers per ring pass in
+// FP32) and FP64: two (up to 128 registers, no spills); their launches run
+// many waves, so fewer resident blocks cost little.
+template <class T, bool LY>
+constexpr int ring_min_blocks() { return (LY || sizeof(T) == 8) ? 2 : 4; }
+
 template <class T, bool COMP, int MAXR, int KIND, bool LY = false>
-__global__ void __launch_bounds__(256, (KIND == 1 ? 4 : 1)) kernel_phase(const __grid_constant__ DevArgs<T> a) {
+__global__ void __launch_bounds__(256, (KIND == 1 ? ring_min_blocks<T, LY>() : 1))
+    kernel_phase(const __grid_constant__ DevArgs<T> a) {
     griddep_launch_dependents();
     const int sidx = find_seg(a, blockIdx.x);
     phase_block<T, COMP, MAXR, KIND, LY>(a, a.seg[sidx], blockIdx.x);
@@ -984,6 +1121,8 @@ void fill_args(DevArgs<T>& a, const LaunchDesc& d, const void* tables, int smem,
     a.flag = flag;
     a.l2 = d.l2;
     a.smem = smem;
+    a.lpt = 1;
+    a.G = 1;
     a.gseg = nullptr;
     a.ngseg = 0;
     a.vblocks = 0;
@@ -999,18 +1138,20 @@ bool ring_tables_ok(const Tables<T>& t) {
 
 template <class T, bool COMP, int MAXR>
 cudaError_t launch_t(const LaunchDesc& d, const void* tables, int block, bool pdl, int smem, int* flag,
-                     cudaStream_t st, int layers, int ring_occ, int ept) {
+                     cudaStream_t st, int layers, int ring_occ, int ept, int lpt) {
     if (d.kind == 1 && !ring_tables_ok(*static_cast<const Tables<T>*>(tables))) return cudaErrorInvalidValue;
     DevArgs<T> a;
     fill_args(a, d, tables, smem, flag);
     a.L = layers;
+    a.lpt = layers > 1 ? std::max(1, std::min(lpt, layers)) : 1;
+    a.G = (layers + a.lpt - 1) / a.lpt;
     const bool two = ept == 2 && layers == 1 && (d.kind == 0 || d.kind == 2);
     int blocks = 0, ns = 0;
     for (int k = 0; k < d.nseg; ++k) {
         const SegDesc& s = d.seg[k];
         if (s.end <= s.begin) continue;
         a.seg[ns++] = to_dev<T>(s, blocks);
-        blocks += seg_blocks(s, two ? 2 * block : block, layers);
+        blocks += seg_blocks(s, two ? 2 * block : block, a.G);
     }
     a.nseg = ns;
     for (int k = ns; k < MAXSEG; ++k) {
@@ -1184,8 +1325,10 @@ cudaError_t launch_any(const LaunchDesc& d, const void* tables, const KernelConf
                        cudaStream_t s) {
     const int L = kc.layers > 1 ? kc.layers : 1;
     if (kc.maxdeg <= 8)
-        return launch_t<T, COMP, 8>(d, tables, kc.block, kc.pdl, kc.tile_smem, flag, s, L, kc.ring_occ, kc.ept);
-    return launch_t<T, COMP, MAX_DEGREE>(d, tables, kc.block, kc.pdl, kc.tile_smem, flag, s, L, 0, kc.ept);
+        return launch_t<T, COMP, 8>(d, tables, kc.block, kc.pdl, kc.tile_smem, flag, s, L, kc.ring_occ, kc.ept,
+                                    kc.lpt);
+    return launch_t<T, COMP, MAX_DEGREE>(d, tables, kc.block, kc.pdl, kc.tile_smem, flag, s, L, 0, kc.ept,
+                                         kc.lpt);
 }
 
 }  // namespace

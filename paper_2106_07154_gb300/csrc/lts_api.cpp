@@ -1462,6 +1462,7 @@ int lts_state_create(lts_mesh mesh, lts_regions reg, const double* h0, const dou
     S->kc.mindeg = *std::min_element(mesh->m.nEoC.begin(), mesh->m.nEoC.end());
     S->kc.pdl = p->pdl != 0 && p->profile == 0;
     S->kc.layers = layers;
+    S->kc.lpt = std::min(kLayersPerThread, layers);
     if (p->ring_occupancy != 0 && p->ring_occupancy != 6 && p->ring_occupancy != 8)
         return set_error(LTS_EINVAL, "ring_occupancy must be 0, 6 or 8");
     S->kc.ring_occ = p->ring_occupancy;

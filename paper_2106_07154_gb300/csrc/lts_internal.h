@@ -145,6 +145,9 @@ constexpr int KEY_STEP1 = 0, KEY_STEP2 = 3, KEY_SIDE = 10, KEY_STEP3 = 100, KEY_
 constexpr int kSlotRowsMin = 8;
 inline int slot_rows(int maxE) { return maxE > kSlotRowsMin ? maxE : kSlotRowsMin; }
 
+// Consecutive layers of one element per thread in multi-layer states.
+constexpr int kLayersPerThread = 2;
+
 // Elements per thread of the vertex and edge launches when the caller
 // leaves the choice to the library.
 constexpr int LTS_DEFAULT_EPT = 1;
@@ -160,6 +163,7 @@ struct KernelConfig {
     int layers = 1;  // layers per element (multi-layer states)
     int ring_occ = 0;  // FP32 ring pass built for 6 or 8 resident blocks per SM (0: default)
     int ept = 1;       // elements per thread of the vertex and edge kinds (1 or 2)
+    int lpt = 1;       // multi-layer states: consecutive layers of an element per thread
 };
 
 // kernels.cu
