@@ -533,14 +533,21 @@ __device__ __forceinline__ T ring_pass(const DevArgs<T>& a, int c, const Lay<LY>
 
 // Two consecutive layers (y.l and y.l + 1) of an FP32 multi-layer state in
 // one ring pass: the slot tables are loaded once, the two layers' state is
-// gathered into float2 values and the ring core runs on both at once.
+// gathered into float2 values and the ring core runs on both at once.  The
+// cells' update operands are loaded with the gathers (the many waves of a
+// multi-layer launch leave the registers for them), so the pass has one
+// dependent round trip after the wait; o0.xh, o1.xh are the input
+// thicknesses the ring reads anyway.
 template <bool COMP, int NR>
 __device__ __forceinline__ float2 ring_body_pair(const DevArgs<float>& a, const Ld& ld, int c, int n, float rA,
-                                                 const RingSlot<float> (&S0)[UNCOND], const Lay<true>& y0) {
+                                                 const RingSlot<float> (&S0)[UNCOND], const Lay<true>& y0,
+                                                 EpiOps<float>& o0, EpiOps<float>& o1) {
     const int N = a.t.nC;
     Lay<true> y1 = y0;
     y1.l = y0.l + 1;
     const float2 hc = make_float2(ld(a.in_h + y0(c)), ld(a.in_h + y1(c)));
+    o0.xh = hc.x;
+    o1.xh = hc.y;
     float2 uj[NR], hn[NR], qv[NR], snl[NR], Rj[NR], sK[NR], C[NR];
 #pragma unroll
     for (int j = 0; j < NR; ++j) {
@@ -567,7 +574,8 @@ __device__ __forceinline__ float2 ring_body_pair(const DevArgs<float>& a, const 
 }
 
 template <bool COMP, int MAXR>
-__device__ __forceinline__ float2 ring_pass_pair(const DevArgs<float>& a, int c, const Lay<true>& y0) {
+__device__ __forceinline__ float2 ring_pass_pair(const DevArgs<float>& a, const DevSeg<float>& s, int epi, int c,
+                                                 const Lay<true>& y0, EpiOps<float>& o0, EpiOps<float>& o1) {
     const Tables<float>& t = a.t;
     const Ld ld(a.l2);
     const int n = ld.stat(t.cn + c);
@@ -576,11 +584,17 @@ __device__ __forceinline__ float2 ring_pass_pair(const DevArgs<float>& a, int c,
     for (int j = 0; j < UNCOND; ++j) S0[j] = ring_slot(t, ld, j, c);
     const float rA = ld.stat(t.rA + c);
     griddep_wait();
+    Lay<true> y1 = y0;
+    y1.l = y0.l + 1;
+    epi_load<float, COMP, true>(ld, s, epi, c, nullptr, o0, y0);
+    epi_load<float, COMP, true>(ld, s, epi, c, nullptr, o1, y1);
     const int nmax = __reduce_max_sync(__activemask(), n);
-    if (nmax <= 6) return ring_body_pair<COMP, 6>(a, ld, c, n, rA, S0, y0);
-    if (nmax <= 7 || MAXR <= 7) return ring_body_pair<COMP, (MAXR < 7 ? MAXR : 7)>(a, ld, c, n, rA, S0, y0);
-    if (nmax <= 8 || MAXR <= 8) return ring_body_pair<COMP, (MAXR < 8 ? MAXR : 8)>(a, ld, c, n, rA, S0, y0);
-    return ring_body_pair<COMP, MAXR>(a, ld, c, n, rA, S0, y0);
+    if (nmax <= 6) return ring_body_pair<COMP, 6>(a, ld, c, n, rA, S0, y0, o0, o1);
+    if (nmax <= 7 || MAXR <= 7)
+        return ring_body_pair<COMP, (MAXR < 7 ? MAXR : 7)>(a, ld, c, n, rA, S0, y0, o0, o1);
+    if (nmax <= 8 || MAXR <= 8)
+        return ring_body_pair<COMP, (MAXR < 8 ? MAXR : 8)>(a, ld, c, n, rA, S0, y0, o0, o1);
+    return ring_body_pair<COMP, MAXR>(a, ld, c, n, rA, S0, y0, o0, o1);
 }
 
 // --------------------------------------------------------------- kind 2: edge
@@ -916,6 +930,57 @@ __device__ __forceinline__ void element_work(const DevArgs<T>& a, const DevSeg<T
     }
 }
 
+// Vertex and edge work of two consecutive layers (y.l and y.l + 1) of a
+// multi-layer state: both layers' state loads go out before either layer's
+// arithmetic, so the pair costs one dependent round trip; each layer's
+// arithmetic is the single-layer code's.
+template <class T, bool COMP, int KIND>
+__device__ __forceinline__ void pair_work(const DevArgs<T>& a, const DevSeg<T>& s, int i, const Lay<true>& y0) {
+    const Ld ld(a.l2);
+    Lay<true> y1 = y0;
+    y1.l = y0.l + 1;
+    if (KIND == 0) {
+        VertStat<T> vs;
+        vertex_stat(a.t, ld, i, vs);
+        griddep_wait();
+        const T ua0 = ld(a.in_u + y0(vs.e0)), ua1 = ld(a.in_u + y0(vs.e1)), ua2 = ld(a.in_u + y0(vs.e2));
+        const T ub0 = ld(a.in_u + y1(vs.e0)), ub1 = ld(a.in_u + y1(vs.e1)), ub2 = ld(a.in_u + y1(vs.e2));
+        const T ha0 = ld(a.in_h + y0(vs.c0)), ha1 = ld(a.in_h + y0(vs.c1)), ha2 = ld(a.in_h + y0(vs.c2));
+        const T hb0 = ld(a.in_h + y1(vs.c0)), hb1 = ld(a.in_h + y1(vs.c1)), hb2 = ld(a.in_h + y1(vs.c2));
+        const St st(a.l2);
+        st(a.q + y0(i), q_value(vs.d0, vs.d1, vs.d2, ua0, ua1, ua2, vs.k0, vs.k1, vs.k2, ha0, ha1, ha2, vs.f));
+        st(a.q + y1(i), q_value(vs.d0, vs.d1, vs.d2, ub0, ub1, ub2, vs.k0, vs.k1, vs.k2, hb0, hb1, hb2, vs.f));
+    } else {
+        const int epi = s.type == SEG_EDGE_ACC ? EPI_ACC : EPI_UPD;
+        EdgeStat<T> es;
+        edge_stat(a.t, ld, i, es);
+        griddep_wait();
+        EpiOps<T> o0, o1;
+        epi_load<T, COMP, true>(ld, s, epi, i, a.in_u, o0, y0);
+        epi_load<T, COMP, true>(ld, s, epi, i, a.in_u, o1, y1);
+        const int N = a.t.nC;
+        T g0[8], g1[8];
+        const Lay<true>* ys[2] = {&y0, &y1};
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const Lay<true>& y = *ys[k];
+            T* g = k == 0 ? g0 : g1;
+            g[0] = ld(a.ring_c + y(es.p0 * N + es.c0));
+            g[1] = ld(a.ring_c + y(es.p1 * N + es.c1));
+            g[2] = ld(a.in_h + y(es.c0));
+            g[3] = ld(a.in_h + y(es.c1));
+            g[4] = COMP ? ld(a.in_hl + y(es.c0)) : T(0);
+            g[5] = COMP ? ld(a.in_hl + y(es.c1)) : T(0);
+            g[6] = ld(a.ring_k + y(es.c0));
+            g[7] = ld(a.ring_k + y(es.c1));
+        }
+        const T U0 = edge_u<T, COMP>(g0[0], g0[1], g0[2], g0[3], g0[4], g0[5], g0[6], g0[7], es.db, es.rdc, a.g);
+        const T U1 = edge_u<T, COMP>(g1[0], g1[1], g1[2], g1[3], g1[4], g1[5], g1[6], g1[7], es.db, es.rdc, a.g);
+        epilogue<T, COMP, false, true>(a, s, epi, i, U0, o0, y0);
+        epilogue<T, COMP, false, true>(a, s, epi, i, U1, o1, y1);
+    }
+}
+
 // The work of (virtual) block `vblk` of segment s.  Multi-layer states run
 // one thread per (element, group of lpt consecutive layers), groups fastest:
 // the thread repeats the element's work for each of its layers, so its mesh
@@ -938,19 +1003,27 @@ __device__ __forceinline__ void phase_block(const DevArgs<T>& a, const DevSeg<T>
             // FP32 ring segments: two layers per ring pass (packed arithmetic)
             if (is_ring(s.type)) {
 #pragma unroll 1
+                const int epi = s.type == SEG_RING ? EPI_NONE : s.type == SEG_RING_ACC ? EPI_ACC : EPI_UPD;
                 for (; k + 1 < nl; k += 2) {
                     y.l = l0 + k;
-                    const float2 H = ring_pass_pair<COMP, MAXR>(a, i, y);
-                    if (s.type != SEG_RING) {
-                        const int epi = s.type == SEG_RING_ACC ? EPI_ACC : EPI_UPD;
-                        Lay<true> y1 = y;
-                        y1.l = y.l + 1;
-                        EpiOps<T> o0, o1;
-                        epi_load<T, COMP, true>(Ld(a.l2), s, epi, i, a.in_h, o0, y);
-                        epi_load<T, COMP, true>(Ld(a.l2), s, epi, i, a.in_h, o1, y1);
+                    Lay<true> y1 = y;
+                    y1.l = y.l + 1;
+                    EpiOps<T> o0, o1;
+                    const float2 H = ring_pass_pair<COMP, MAXR>(a, s, epi, i, y, o0, o1);
+                    if (epi != EPI_NONE) {
                         epilogue<T, COMP, true, true>(a, s, epi, i, H.x, o0, y);
                         epilogue<T, COMP, true, true>(a, s, epi, i, H.y, o1, y1);
                     }
+                }
+            }
+        }
+        if constexpr (KIND == 0 || KIND == 2) {
+            if ((KIND == 0 && s.type == SEG_VERT) ||
+                (KIND == 2 && (s.type == SEG_EDGE_UPD || s.type == SEG_EDGE_ACC))) {
+#pragma unroll 1
+                for (; k + 1 < nl; k += 2) {
+                    y.l = l0 + k;
+                    pair_work<T, COMP, KIND>(a, s, i, y);
                 }
             }
         }

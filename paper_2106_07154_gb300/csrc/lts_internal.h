@@ -146,7 +146,7 @@ constexpr int kSlotRowsMin = 8;
 inline int slot_rows(int maxE) { return maxE > kSlotRowsMin ? maxE : kSlotRowsMin; }
 
 // Consecutive layers of one element per thread in multi-layer states.
-constexpr int kLayersPerThread = 2;
+constexpr int kLayersPerThread = 4;
 
 // Elements per thread of the vertex and edge launches when the caller
 // leaves the choice to the library.
