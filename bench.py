@@ -872,8 +872,8 @@ def run_ensemble(args):
             "scaling": "strong" if world > 1 else "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": cfg,
             "gpu_launches": st["launches"] * args.steps, "clocks": clk,
-            "launch": "one CUDA graph per ensemble coarse step, persistent segment-table kernels, "
-                      "programmatic dependent launch",
+            "launch": "one CUDA graph per ensemble coarse step, one segment-table launch per phase "
+                      "for all members (one block per 256-element piece), programmatic dependent launch",
             "segments_per_step": st["segments"]}
     if rank == 0 and not args.no_extras:
         achieved = bytes_step / (ms / args.steps * 1e-3) / 1e9

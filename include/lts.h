@@ -398,7 +398,7 @@ int lts_diagnostics_noalloc(lts_state s, double* d_out);
  * The paper runs one mesh per job; batching independent meshes is an
  * interface of this library.  The members' tables and states are copied
  * into one packed index space; each launch carries the segments (band
- * ranges) of every member in a device table walked by a persistent grid,
+ * ranges) of every member in a device table (each block finds its segment),
  * and a member with a smaller M has no segments in the later substeps.
  * Every member's cells see the same arithmetic as its stand-alone
  * lts_step, so results equal the members' own steps bit for bit.
@@ -408,15 +408,17 @@ typedef struct lts_ensemble_s* lts_ensemble;
 typedef struct lts_ensemble_params {
     int32_t use_graph;      /* 1: capture one ensemble coarse step as a CUDA graph     */
     int32_t pdl;            /* 1: programmatic dependent launch between launches       */
-    int32_t persistent;     /* 1: grid = resident blocks (persistent, default);
-                               0: one block per 256-element piece of a segment         */
+    int32_t persistent;     /* 1: grid = resident blocks, each walking the pieces;
+                               0: one block per 256-element piece of a segment
+                               (default; the faster of the two on GB300)               */
     void* stream;           /* cudaStream_t to enqueue on; NULL = a library stream     */
 } lts_ensemble_params;
 
 /* Builds an ensemble (the paper has no counterpart) of n >= 1 distinct states that live on the current
  * device and share precision, compensation, mode, g, block size and
  * kernel_path 0.  Copies each member's current state in (the members'
- * streams are synchronised first).  p may be NULL (graph, PDL, persistent).
+ * streams are synchronised first).  p may be NULL (graph, PDL, one block
+ * per piece).
  * The members must outlive the ensemble and must not be stepped, written
  * or destroyed while it exists; lts_ensemble_read brings a member's own
  * state up to date.  Needs at most 2^31 - 1 cells x maxEdges in total.

@@ -9,8 +9,9 @@
 // launch by launch: launches with the same phase key (step, substep, stage,
 // kind) become one launch whose segment list holds every member's segments.
 // A member with a smaller M simply has no segments in the later substeps.
-// The segment lists live in device memory and a persistent grid walks them
-// (kernel_phase_table), so a launch may carry any number of members.  Each
+// The segment lists live in device memory; each block of a launch finds its
+// segment by a binary search (kernel_phase_table), so a launch may carry any
+// number of members.  Each
 // member's cells see exactly the arithmetic of its stand-alone step.
 #include <algorithm>
 #include <cstring>
@@ -563,7 +564,7 @@ int lts_ensemble_create(const lts_state* members, int32_t n, const lts_ensemble_
     if (rc != LTS_OK) return rc;
     int nsm = 0;
     CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    if (ep && !ep->persistent) nsm = 0;   // one block per virtual block
+    if (!ep || !ep->persistent) nsm = 0;   // one block per virtual block (the default)
     for (int p = 0; p < 2; ++p) {
         rc = build_plan(E.get(), p, nsm);
         if (rc != LTS_OK) return rc;

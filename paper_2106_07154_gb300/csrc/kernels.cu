@@ -81,12 +81,13 @@ __device__ __forceinline__ uint64_t l2_policy(int mode) {
     return p;
 }
 // Loads of mesh tables (never written by any kernel): free to be scheduled.
-#define LTS_LD_HINT(TY, PTXT, CONS)                                                      \
+#define LTS_LD_STATIC(TY, PTXT, CONS)                                                    \
     __device__ __forceinline__ TY ld_static(const TY* q, uint64_t p) {                   \
         TY x;                                                                            \
         asm("ld.global.nc.L2::cache_hint." PTXT " %0, [%1], %2;" : CONS(x) : "l"(q), "l"(p)); \
         return x;                                                                        \
-    }                                                                                    \
+    }
+#define LTS_LD_STATE(TY, PTXT, CONS)                                                     \
     __device__ __forceinline__ TY ld_state(const TY* q, uint64_t p) {                    \
         TY x;                                                                            \
         asm volatile("ld.global.nc.L2::cache_hint." PTXT " %0, [%1], %2;"                \
@@ -96,12 +97,12 @@ __device__ __forceinline__ uint64_t l2_policy(int mode) {
 #define LTS_R(x) "=r"(x)
 #define LTS_F(x) "=f"(x)
 #define LTS_D(x) "=d"(x)
-#define LTS_L(x) "=l"(x)
-LTS_LD_HINT(int, "b32", LTS_R)
-LTS_LD_HINT(unsigned long long, "b64", LTS_L)
-LTS_LD_HINT(uint32_t, "b32", LTS_R)
-LTS_LD_HINT(float, "f32", LTS_F)
-LTS_LD_HINT(double, "f64", LTS_D)
+LTS_LD_STATIC(int, "b32", LTS_R)
+LTS_LD_STATIC(uint32_t, "b32", LTS_R)
+LTS_LD_STATIC(float, "f32", LTS_F)
+LTS_LD_STATIC(double, "f64", LTS_D)
+LTS_LD_STATE(float, "f32", LTS_F)
+LTS_LD_STATE(double, "f64", LTS_D)
 __device__ __forceinline__ int4 ld_static(const int4* q, uint64_t p) {
     int4 x;
     asm("ld.global.nc.L2::cache_hint.v4.b32 {%0, %1, %2, %3}, [%4], %5;"
@@ -1002,8 +1003,8 @@ __device__ __forceinline__ void phase_block(const DevArgs<T>& a, const DevSeg<T>
         if constexpr (KIND == 1 && sizeof(T) == 4) {
             // FP32 ring segments: two layers per ring pass (packed arithmetic)
             if (is_ring(s.type)) {
-#pragma unroll 1
                 const int epi = s.type == SEG_RING ? EPI_NONE : s.type == SEG_RING_ACC ? EPI_ACC : EPI_UPD;
+#pragma unroll 1
                 for (; k + 1 < nl; k += 2) {
                     y.l = l0 + k;
                     Lay<true> y1 = y;
@@ -1117,10 +1118,10 @@ __global__ void __launch_bounds__(256, MINB) kernel_ring_occ(const __grid_consta
     phase_block<float, COMP, 8, 1, false>(a, a.seg[sidx], blockIdx.x);
 }
 
-// Segment-table variant (ensembles of meshes: one launch carries the
-// segments of every member, more than fit in the kernel parameters).  A
-// persistent grid walks the virtual blocks; each finds its segment by a
-// binary search over the segments' first virtual block.
+// Segment-table variant (ensembles of meshes, and states with several fine
+// regions: one launch carries more segments than fit in the kernel
+// parameters).  Each virtual block finds its segment by a binary search over
+// the segments' first virtual block.
 template <class T>
 __device__ __forceinline__ int find_gseg(const DevArgs<T>& a, int vblk) {
     int lo = 0, hi = a.ngseg - 1;
@@ -1132,11 +1133,22 @@ __device__ __forceinline__ int find_gseg(const DevArgs<T>& a, int vblk) {
     return lo;
 }
 
-template <class T, bool COMP, int MAXR, int KIND>
-__global__ void __launch_bounds__(256) kernel_phase_table(const __grid_constant__ DevArgs<T> a) {
+// PERSIST: a grid of resident blocks walks the virtual blocks in turn;
+// otherwise one block per virtual block.  The loop keeps loop-invariant
+// values live across its iterations (the persistent ring takes about 110
+// registers uncapped and spills under the cap), so the one-shot form is the
+// one that compiles like kernel_phase.
+template <class T, bool COMP, int MAXR, int KIND, bool PERSIST>
+__global__ void __launch_bounds__(256, (KIND == 1 ? ring_min_blocks<T, false>() : 1))
+    kernel_phase_table(const __grid_constant__ DevArgs<T> a) {
     griddep_launch_dependents();
-    for (int vb = blockIdx.x; vb < a.vblocks; vb += gridDim.x)
+    if (PERSIST) {
+        for (int vb = blockIdx.x; vb < a.vblocks; vb += gridDim.x)
+            phase_block<T, COMP, MAXR, KIND, false>(a, a.gseg[find_gseg(a, vb)], vb);
+    } else {
+        const int vb = blockIdx.x;
         phase_block<T, COMP, MAXR, KIND, false>(a, a.gseg[find_gseg(a, vb)], vb);
+    }
 }
 
 template <class K, class A>
@@ -1273,11 +1285,18 @@ cudaError_t launch_table_t(const LaunchDesc& d, const void* dsegs, int nseg, int
     a.ngseg = nseg;
     a.vblocks = vblocks;
     if (vblocks == 0 || nseg == 0) return cudaSuccess;
-    grid = grid > 0 ? std::min(grid, vblocks) : vblocks;
-    switch (d.kind) {
-        case 0: return launch_kernel(kernel_phase_table<T, COMP, MAXR, 0>, grid, block, pdl, st, a);
-        case 1: return launch_kernel(kernel_phase_table<T, COMP, MAXR, 1>, grid, block, pdl, st, a);
-        case 2: return launch_kernel(kernel_phase_table<T, COMP, MAXR, 2>, grid, block, pdl, st, a);
+    if (grid > 0 && grid < vblocks) {
+        switch (d.kind) {
+            case 0: return launch_kernel(kernel_phase_table<T, COMP, MAXR, 0, true>, grid, block, pdl, st, a);
+            case 1: return launch_kernel(kernel_phase_table<T, COMP, MAXR, 1, true>, grid, block, pdl, st, a);
+            case 2: return launch_kernel(kernel_phase_table<T, COMP, MAXR, 2, true>, grid, block, pdl, st, a);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    switch (d.kind) {   // the grid covers every virtual block: one block each
+        case 0: return launch_kernel(kernel_phase_table<T, COMP, MAXR, 0, false>, vblocks, block, pdl, st, a);
+        case 1: return launch_kernel(kernel_phase_table<T, COMP, MAXR, 1, false>, vblocks, block, pdl, st, a);
+        case 2: return launch_kernel(kernel_phase_table<T, COMP, MAXR, 2, false>, vblocks, block, pdl, st, a);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -1443,9 +1462,9 @@ int encode_t(const SegDesc* segs, int n, int block, std::vector<unsigned char>& 
 template <class T, bool COMP, int MAXR>
 int table_occupancy_t(int kind, int block) {
     int nb = 0;
-    cudaError_t e = kind == 0   ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel_phase_table<T, COMP, MAXR, 0>, block, 0)
-                    : kind == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel_phase_table<T, COMP, MAXR, 1>, block, 0)
-                                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel_phase_table<T, COMP, MAXR, 2>, block, 0);
+    cudaError_t e = kind == 0   ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel_phase_table<T, COMP, MAXR, 0, true>, block, 0)
+                    : kind == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel_phase_table<T, COMP, MAXR, 1, true>, block, 0)
+                                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel_phase_table<T, COMP, MAXR, 2, true>, block, 0);
     return e == cudaSuccess ? nb : -1;
 }
 }  // namespace

@@ -450,7 +450,7 @@ def lts_diagnostics_noalloc(state_h, d_out_ptr: int):
 
 
 def lts_ensemble_create(state_handles, use_graph: bool = True, pdl: bool = True,
-                        persistent: bool = True, stream: int | None = None):
+                        persistent: bool = False, stream: int | None = None):
     arr = (C.c_void_p * len(state_handles))(*[C.c_void_p(h.value if isinstance(h, C.c_void_p) else h)
                                                for h in state_handles])
     p = lts_ensemble_params(int(use_graph), int(pdl), int(persistent), stream)
@@ -508,7 +508,7 @@ def lts_ensemble_stats(ens_h):
 class Ensemble:
     """Several Models advanced together (one launch per phase for all)."""
 
-    def __init__(self, models, use_graph: bool = True, pdl: bool = True, persistent: bool = True,
+    def __init__(self, models, use_graph: bool = True, pdl: bool = True, persistent: bool = False,
                  stream: int | None = None):
         self.models = list(models)
         self._pending = []

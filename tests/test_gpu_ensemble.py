@@ -74,8 +74,8 @@ def test_ensemble_members_equal_standalone_bitwise(members, precision):
         m.close()
 
 
-@pytest.mark.parametrize("use_graph,persistent,pdl", [(False, True, True), (True, False, True),
-                                                      (True, True, False)])
+@pytest.mark.parametrize("use_graph,persistent,pdl", [(False, False, True), (True, True, True),
+                                                      (False, True, False), (True, False, False)])
 def test_ensemble_launch_modes_identical(members, use_graph, persistent, pdl):
     ref = alone(members, lts.LTS_FP32, 4)
     ms = models(members, lts.LTS_FP32)
