@@ -53,6 +53,8 @@ struct DevArgs {
     int L;            // layers per element (multi-layer states; 1 otherwise)
     int lpt;          // multi-layer states: layers per thread (consecutive layers of one element)
     int G;            // multi-layer states: thread groups per element, ceil(L / lpt)
+    int v2;           // multi-layer states: 1 when every pair of layers a thread runs is one
+                      // aligned two-word access (checked on the host), else 0
     // segment-table launches (ensembles): segments in device memory
     const DevSeg<T>* gseg;
     int ngseg;
@@ -103,6 +105,34 @@ LTS_LD_STATIC(float, "f32", LTS_F)
 LTS_LD_STATIC(double, "f64", LTS_D)
 LTS_LD_STATE(float, "f32", LTS_F)
 LTS_LD_STATE(double, "f64", LTS_D)
+// Two consecutive layers of one element (words x and x + 1) in one access.
+// Used only by launches whose host has checked that every such pair starts
+// on a multiple of the pair's size (even layer count, even first layer of
+// every pair, aligned buffers).
+template <class T>
+struct Vec2;
+template <>
+struct Vec2<float> {
+    using type = float2;
+};
+template <>
+struct Vec2<double> {
+    using type = double2;
+};
+template <class T>
+using vec2_t = typename Vec2<T>::type;
+__device__ __forceinline__ float2 ld_state2(const float* q, uint64_t p) {
+    float2 x;
+    asm volatile("ld.global.nc.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;"
+                 : "=f"(x.x), "=f"(x.y) : "l"(q), "l"(p) : "memory");
+    return x;
+}
+__device__ __forceinline__ double2 ld_state2(const double* q, uint64_t p) {
+    double2 x;
+    asm volatile("ld.global.nc.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;"
+                 : "=d"(x.x), "=d"(x.y) : "l"(q), "l"(p) : "memory");
+    return x;
+}
 __device__ __forceinline__ int4 ld_static(const int4* q, uint64_t p) {
     int4 x;
     asm("ld.global.nc.L2::cache_hint.v4.b32 {%0, %1, %2, %3}, [%4], %5;"
@@ -127,6 +157,14 @@ __device__ __forceinline__ void st_hint(float* q, float v, uint64_t p) {
 __device__ __forceinline__ void st_hint(double* q, double v, uint64_t p) {
     asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(q), "d"(v), "l"(p) : "memory");
 }
+__device__ __forceinline__ void st_hint(float* q, float2 v, uint64_t p) {
+    asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(q), "f"(v.x), "f"(v.y), "l"(p)
+                 : "memory");
+}
+__device__ __forceinline__ void st_hint(double* q, double2 v, uint64_t p) {
+    asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1, %2}, %3;" ::"l"(q), "d"(v.x), "d"(v.y), "l"(p)
+                 : "memory");
+}
 // Policy of a launch mode's state accesses (see above): the fine launches'
 // state goes first, like the coarse launches' data.
 __device__ __forceinline__ int state_mode(int m) { return m == 1 ? 2 : m; }
@@ -136,6 +174,9 @@ struct St {
     __device__ __forceinline__ explicit St(int m) : pol(l2_policy(state_mode(m))) {}
     template <class V>
     __device__ __forceinline__ void operator()(V* q, V v) const { st_hint(q, v, pol); }
+    // words q[0], q[1] (two layers) in one aligned access
+    template <class V>
+    __device__ __forceinline__ void pair(V* q, vec2_t<V> v) const { st_hint(q, v, pol); }
 };
 
 // Read-only loads with the launch's L2 policy: `stat` for mesh tables, `operator()`
@@ -147,6 +188,9 @@ struct Ld {
     __device__ __forceinline__ V stat(const V* q) const { return ld_static(q, pol); }
     template <class V>
     __device__ __forceinline__ V operator()(const V* q) const { return ld_state(q, spol); }
+    // state words q[0], q[1] (two layers) in one aligned access
+    template <class V>
+    __device__ __forceinline__ vec2_t<V> pair(const V* q) const { return ld_state2(q, spol); }
 };
 
 // ------------------------------------------------------------------ layers
@@ -273,6 +317,40 @@ __device__ __forceinline__ void epi_load(const Ld& ld, const DevSeg<T>& s, int m
         o.ol = COMP ? ld((const T*)s.p[1] + y(i)) : T(0);
         if (in_x) o.xh = ld(in_x + y(i));
         o.xl = COMP ? ld((const T*)s.p[2] + y(i)) : T(0);
+    }
+}
+
+// epi_load of two consecutive layers (y.l, y.l + 1) with one access per array.
+template <class T, bool COMP>
+__device__ __forceinline__ void epi_load_pair(const Ld& ld, const DevSeg<T>& s, int mode, int i, const T* in_x,
+                                              EpiOps<T>& o0, EpiOps<T>& o1, const Lay<true>& y) {
+    using V = vec2_t<T>;
+    if (mode == EPI_ACC) {
+        if (s.flag) {
+            o0.oh = o1.oh = T(0);
+        } else {
+            const V v = ld.pair((const T*)s.p[0] + y(i - s.base));
+            o0.oh = v.x, o1.oh = v.y;
+        }
+    } else if (mode == EPI_UPD) {
+        const V oh = ld.pair((const T*)s.p[0] + y(i));
+        o0.oh = oh.x, o1.oh = oh.y;
+        if (COMP) {
+            const V ol = ld.pair((const T*)s.p[1] + y(i));
+            o0.ol = ol.x, o1.ol = ol.y;
+        } else {
+            o0.ol = o1.ol = T(0);
+        }
+        if (in_x) {
+            const V x = ld.pair(in_x + y(i));
+            o0.xh = x.x, o1.xh = x.y;
+        }
+        if (COMP) {
+            const V xl = ld.pair((const T*)s.p[2] + y(i));
+            o0.xl = xl.x, o1.xl = xl.y;
+        } else {
+            o0.xl = o1.xl = T(0);
+        }
     }
 }
 
@@ -534,7 +612,8 @@ __device__ __forceinline__ T ring_pass(const DevArgs<T>& a, int c, const Lay<LY>
 
 // Two consecutive layers (y.l and y.l + 1) of an FP32 multi-layer state in
 // one ring pass: the slot tables are loaded once, the two layers' state is
-// gathered into float2 values and the ring core runs on both at once.  The
+// gathered into float2 values (one aligned two-word access each) and the
+// ring core runs on both at once.  The
 // cells' update operands are loaded with the gathers (the many waves of a
 // multi-layer launch leave the registers for them), so the pass has one
 // dependent round trip after the wait; o0.xh, o1.xh are the input
@@ -544,18 +623,16 @@ __device__ __forceinline__ float2 ring_body_pair(const DevArgs<float>& a, const 
                                                  const RingSlot<float> (&S0)[UNCOND], const Lay<true>& y0,
                                                  EpiOps<float>& o0, EpiOps<float>& o1) {
     const int N = a.t.nC;
-    Lay<true> y1 = y0;
-    y1.l = y0.l + 1;
-    const float2 hc = make_float2(ld(a.in_h + y0(c)), ld(a.in_h + y1(c)));
+    const float2 hc = ld.pair(a.in_h + y0(c));
     o0.xh = hc.x;
     o1.xh = hc.y;
     float2 uj[NR], hn[NR], qv[NR], snl[NR], Rj[NR], sK[NR], C[NR];
 #pragma unroll
     for (int j = 0; j < NR; ++j) {
         const RingSlot<float> r = j < UNCOND ? S0[j % UNCOND] : (j < n ? ring_slot(a.t, ld, j, c) : S0[0]);
-        uj[j] = make_float2(ld(a.in_u + y0(r.e)), ld(a.in_u + y1(r.e)));
-        hn[j] = make_float2(ld(a.in_h + y0(r.nb)), ld(a.in_h + y1(r.nb)));
-        qv[j] = make_float2(ld(a.q + y0(r.v)), ld(a.q + y1(r.v)));
+        uj[j] = ld.pair(a.in_u + y0(r.e));
+        hn[j] = ld.pair(a.in_h + y0(r.nb));
+        qv[j] = ld.pair(a.q + y0(r.v));
         snl[j] = make_float2(r.snl, r.snl);
         Rj[j] = make_float2(r.R, r.R);
         sK[j] = make_float2(r.sK, r.sK);
@@ -565,12 +642,8 @@ __device__ __forceinline__ float2 ring_body_pair(const DevArgs<float>& a, const 
     const St st(a.l2);
 #pragma unroll
     for (int p = 0; p < NR; ++p)
-        if (p < n) {
-            st(a.ring_c + y0(p * N + c), C[p].x);
-            st(a.ring_c + y1(p * N + c), C[p].y);
-        }
-    st(a.ring_k + y0(c), Kc.x);
-    st(a.ring_k + y1(c), Kc.y);
+        if (p < n) st.pair(a.ring_c + y0(p * N + c), C[p]);
+    st.pair(a.ring_k + y0(c), Kc);
     return H;
 }
 
@@ -585,10 +658,7 @@ __device__ __forceinline__ float2 ring_pass_pair(const DevArgs<float>& a, const 
     for (int j = 0; j < UNCOND; ++j) S0[j] = ring_slot(t, ld, j, c);
     const float rA = ld.stat(t.rA + c);
     griddep_wait();
-    Lay<true> y1 = y0;
-    y1.l = y0.l + 1;
-    epi_load<float, COMP, true>(ld, s, epi, c, nullptr, o0, y0);
-    epi_load<float, COMP, true>(ld, s, epi, c, nullptr, o1, y1);
+    epi_load_pair<float, COMP>(ld, s, epi, c, nullptr, o0, o1, y0);
     const int nmax = __reduce_max_sync(__activemask(), n);
     if (nmax <= 6) return ring_body_pair<COMP, 6>(a, ld, c, n, rA, S0, y0, o0, o1);
     if (nmax <= 7 || MAXR <= 7)
@@ -890,6 +960,29 @@ __device__ __forceinline__ void epilogue(const DevArgs<T>& a, const DevSeg<T>& s
     if (!ok) atomicOr(a.flag, IS_CELL ? 1 : 2);
 }
 
+// The epilogue of two consecutive layers (y.l, y.l + 1): each layer's
+// arithmetic is the single-layer epilogue's, the stores one access per array.
+template <class T, bool COMP, bool IS_CELL>
+__device__ __forceinline__ void epilogue_pair(const DevArgs<T>& a, const DevSeg<T>& s, int epi, int i, T R0, T R1,
+                                              const EpiOps<T>& o0, const EpiOps<T>& o1, const Lay<true>& y) {
+    using V = vec2_t<T>;
+    const St st(a.l2);
+    if (epi == EPI_ACC) {
+        V v;
+        v.x = s.flag ? R0 : o0.oh + R0;
+        v.y = s.flag ? R1 : o1.oh + R1;
+        st.pair((T*)s.p[0] + y(i - s.base), v);
+        return;
+    }
+    V yh, yl;
+    combine<T, COMP>(o0.oh, o0.ol, o0.xh, o0.xl, s.c[0], s.c[1], R0, yh.x, yl.x);
+    combine<T, COMP>(o1.oh, o1.ol, o1.xh, o1.xl, s.c[0], s.c[1], R1, yh.y, yl.y);
+    st.pair((T*)s.p[3] + y(i), yh);
+    if (COMP) st.pair((T*)s.p[4] + y(i), yl);
+    const bool ok = IS_CELL ? finite_pos(yh.x) && finite_pos(yh.y) : finite_val(yh.x) && finite_val(yh.y);
+    if (!ok) atomicOr(a.flag, IS_CELL ? 1 : 2);
+}
+
 template <class T>
 __device__ __forceinline__ int find_seg(const DevArgs<T>& a, int blk) {
     int s = 0;
@@ -932,53 +1025,45 @@ __device__ __forceinline__ void element_work(const DevArgs<T>& a, const DevSeg<T
 }
 
 // Vertex and edge work of two consecutive layers (y.l and y.l + 1) of a
-// multi-layer state: both layers' state loads go out before either layer's
-// arithmetic, so the pair costs one dependent round trip; each layer's
-// arithmetic is the single-layer code's.
+// multi-layer state: each state word is one aligned two-word access for both
+// layers, all of them out before either layer's arithmetic, so the pair
+// costs one dependent round trip; each layer's arithmetic is the
+// single-layer code's.
 template <class T, bool COMP, int KIND>
 __device__ __forceinline__ void pair_work(const DevArgs<T>& a, const DevSeg<T>& s, int i, const Lay<true>& y0) {
+    using V = vec2_t<T>;
     const Ld ld(a.l2);
-    Lay<true> y1 = y0;
-    y1.l = y0.l + 1;
     if (KIND == 0) {
         VertStat<T> vs;
         vertex_stat(a.t, ld, i, vs);
         griddep_wait();
-        const T ua0 = ld(a.in_u + y0(vs.e0)), ua1 = ld(a.in_u + y0(vs.e1)), ua2 = ld(a.in_u + y0(vs.e2));
-        const T ub0 = ld(a.in_u + y1(vs.e0)), ub1 = ld(a.in_u + y1(vs.e1)), ub2 = ld(a.in_u + y1(vs.e2));
-        const T ha0 = ld(a.in_h + y0(vs.c0)), ha1 = ld(a.in_h + y0(vs.c1)), ha2 = ld(a.in_h + y0(vs.c2));
-        const T hb0 = ld(a.in_h + y1(vs.c0)), hb1 = ld(a.in_h + y1(vs.c1)), hb2 = ld(a.in_h + y1(vs.c2));
-        const St st(a.l2);
-        st(a.q + y0(i), q_value(vs.d0, vs.d1, vs.d2, ua0, ua1, ua2, vs.k0, vs.k1, vs.k2, ha0, ha1, ha2, vs.f));
-        st(a.q + y1(i), q_value(vs.d0, vs.d1, vs.d2, ub0, ub1, ub2, vs.k0, vs.k1, vs.k2, hb0, hb1, hb2, vs.f));
+        const V u0 = ld.pair(a.in_u + y0(vs.e0)), u1 = ld.pair(a.in_u + y0(vs.e1)), u2 = ld.pair(a.in_u + y0(vs.e2));
+        const V h0 = ld.pair(a.in_h + y0(vs.c0)), h1 = ld.pair(a.in_h + y0(vs.c1)), h2 = ld.pair(a.in_h + y0(vs.c2));
+        V q;
+        q.x = q_value(vs.d0, vs.d1, vs.d2, u0.x, u1.x, u2.x, vs.k0, vs.k1, vs.k2, h0.x, h1.x, h2.x, vs.f);
+        q.y = q_value(vs.d0, vs.d1, vs.d2, u0.y, u1.y, u2.y, vs.k0, vs.k1, vs.k2, h0.y, h1.y, h2.y, vs.f);
+        St(a.l2).pair(a.q + y0(i), q);
     } else {
         const int epi = s.type == SEG_EDGE_ACC ? EPI_ACC : EPI_UPD;
         EdgeStat<T> es;
         edge_stat(a.t, ld, i, es);
         griddep_wait();
         EpiOps<T> o0, o1;
-        epi_load<T, COMP, true>(ld, s, epi, i, a.in_u, o0, y0);
-        epi_load<T, COMP, true>(ld, s, epi, i, a.in_u, o1, y1);
+        epi_load_pair<T, COMP>(ld, s, epi, i, a.in_u, o0, o1, y0);
         const int N = a.t.nC;
-        T g0[8], g1[8];
-        const Lay<true>* ys[2] = {&y0, &y1};
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const Lay<true>& y = *ys[k];
-            T* g = k == 0 ? g0 : g1;
-            g[0] = ld(a.ring_c + y(es.p0 * N + es.c0));
-            g[1] = ld(a.ring_c + y(es.p1 * N + es.c1));
-            g[2] = ld(a.in_h + y(es.c0));
-            g[3] = ld(a.in_h + y(es.c1));
-            g[4] = COMP ? ld(a.in_hl + y(es.c0)) : T(0);
-            g[5] = COMP ? ld(a.in_hl + y(es.c1)) : T(0);
-            g[6] = ld(a.ring_k + y(es.c0));
-            g[7] = ld(a.ring_k + y(es.c1));
+        const V C0 = ld.pair(a.ring_c + y0(es.p0 * N + es.c0)), C1 = ld.pair(a.ring_c + y0(es.p1 * N + es.c1));
+        const V h0 = ld.pair(a.in_h + y0(es.c0)), h1 = ld.pair(a.in_h + y0(es.c1));
+        V hl0, hl1;
+        if (COMP) {
+            hl0 = ld.pair(a.in_hl + y0(es.c0));
+            hl1 = ld.pair(a.in_hl + y0(es.c1));
+        } else {
+            hl0.x = hl0.y = hl1.x = hl1.y = T(0);
         }
-        const T U0 = edge_u<T, COMP>(g0[0], g0[1], g0[2], g0[3], g0[4], g0[5], g0[6], g0[7], es.db, es.rdc, a.g);
-        const T U1 = edge_u<T, COMP>(g1[0], g1[1], g1[2], g1[3], g1[4], g1[5], g1[6], g1[7], es.db, es.rdc, a.g);
-        epilogue<T, COMP, false, true>(a, s, epi, i, U0, o0, y0);
-        epilogue<T, COMP, false, true>(a, s, epi, i, U1, o1, y1);
+        const V K0 = ld.pair(a.ring_k + y0(es.c0)), K1 = ld.pair(a.ring_k + y0(es.c1));
+        const T U0 = edge_u<T, COMP>(C0.x, C1.x, h0.x, h1.x, hl0.x, hl1.x, K0.x, K1.x, es.db, es.rdc, a.g);
+        const T U1 = edge_u<T, COMP>(C0.y, C1.y, h0.y, h1.y, hl0.y, hl1.y, K0.y, K1.y, es.db, es.rdc, a.g);
+        epilogue_pair<T, COMP, false>(a, s, epi, i, U0, U1, o0, o1, y0);
     }
 }
 
@@ -1000,27 +1085,24 @@ __device__ __forceinline__ void phase_block(const DevArgs<T>& a, const DevSeg<T>
         Lay<true> y;
         y.L = a.L;
         int k = 0;
+        // pairs of layers only where the host found every pair aligned
+        // (otherwise each layer runs the single-layer code, the same bits)
         if constexpr (KIND == 1 && sizeof(T) == 4) {
             // FP32 ring segments: two layers per ring pass (packed arithmetic)
-            if (is_ring(s.type)) {
+            if (a.v2 && is_ring(s.type)) {
                 const int epi = s.type == SEG_RING ? EPI_NONE : s.type == SEG_RING_ACC ? EPI_ACC : EPI_UPD;
 #pragma unroll 1
                 for (; k + 1 < nl; k += 2) {
                     y.l = l0 + k;
-                    Lay<true> y1 = y;
-                    y1.l = y.l + 1;
                     EpiOps<T> o0, o1;
                     const float2 H = ring_pass_pair<COMP, MAXR>(a, s, epi, i, y, o0, o1);
-                    if (epi != EPI_NONE) {
-                        epilogue<T, COMP, true, true>(a, s, epi, i, H.x, o0, y);
-                        epilogue<T, COMP, true, true>(a, s, epi, i, H.y, o1, y1);
-                    }
+                    if (epi != EPI_NONE) epilogue_pair<T, COMP, true>(a, s, epi, i, H.x, H.y, o0, o1, y);
                 }
             }
         }
         if constexpr (KIND == 0 || KIND == 2) {
-            if ((KIND == 0 && s.type == SEG_VERT) ||
-                (KIND == 2 && (s.type == SEG_EDGE_UPD || s.type == SEG_EDGE_ACC))) {
+            if (a.v2 && ((KIND == 0 && s.type == SEG_VERT) ||
+                         (KIND == 2 && (s.type == SEG_EDGE_UPD || s.type == SEG_EDGE_ACC)))) {
 #pragma unroll 1
                 for (; k + 1 < nl; k += 2) {
                     y.l = l0 + k;
@@ -1208,10 +1290,27 @@ void fill_args(DevArgs<T>& a, const LaunchDesc& d, const void* tables, int smem,
     a.smem = smem;
     a.lpt = 1;
     a.G = 1;
+    a.v2 = 0;
     a.gseg = nullptr;
     a.ngseg = 0;
     a.vblocks = 0;
     a.L = 1;
+}
+
+// Multi-layer launches: a pair of layers (l, l + 1) of element x sits at
+// words x L + l and x L + l + 1; with L and every pair's first layer even
+// (L and the layers per thread even) and every array the launch touches
+// aligned to two words, each pair is one aligned two-word access.
+template <class T>
+bool pairs_aligned(const DevArgs<T>& a, const LaunchDesc& d) {
+    if (a.L < 2 || (a.L & 1) || (a.lpt & 1)) return false;
+    auto ok = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) % (2 * sizeof(T))) == 0; };
+    if (!ok(a.in_h) || !ok(a.in_hl) || !ok(a.in_u) || !ok(a.in_ul) || !ok(a.q) || !ok(a.ring_c) || !ok(a.ring_k))
+        return false;
+    for (int k = 0; k < d.nseg; ++k)
+        for (int m = 0; m < 10; ++m)
+            if (!ok(d.seg[k].p[m])) return false;
+    return true;
 }
 
 // A table set without the ring pass's packed slot rows cannot run a ring
@@ -1230,6 +1329,7 @@ cudaError_t launch_t(const LaunchDesc& d, const void* tables, int block, bool pd
     a.L = layers;
     a.lpt = layers > 1 ? std::max(1, std::min(lpt, layers)) : 1;
     a.G = (layers + a.lpt - 1) / a.lpt;
+    a.v2 = pairs_aligned(a, d) ? 1 : 0;
     const bool two = ept == 2 && layers == 1 && (d.kind == 0 || d.kind == 2);
     int blocks = 0, ns = 0;
     for (int k = 0; k < d.nseg; ++k) {

@@ -47,8 +47,24 @@ def test_identical_layers_equal_single_layer_bitwise(sphw, precision, L):
     assert abs(dL["mass"] - L * d1["mass"]) <= 1e-13 * L * d1["mass"]
 
 
-def test_layers_match_oracle_each(sphw):
-    L, n = 3, 10
+@pytest.mark.parametrize("precision,comp", [(lts.LTS_FP64, False), (lts.LTS_FP32, True), (lts.LTS_FP32, False)])
+@pytest.mark.parametrize("L", [3, 4, 6])
+def test_different_layers_equal_their_single_layer_runs_bitwise(sphw, precision, comp, L):
+    """Each layer of a state whose layers differ equals the single-layer run
+    from that layer's initial state, bit for bit.  Even L runs pairs of
+    layers through two-word accesses, so a swapped lane would fail here;
+    L = 6 also has a thread with a single pair (layers 4, 5); odd L runs
+    every layer through the single-layer code."""
+    h0, u0 = perturbed(sphw, L)
+    hL, uL, _ = run(sphw, h0, u0, 4, precision, layers=L, compensated=comp)
+    for k in range(L):
+        h1, u1, _ = run(sphw, h0[k], u0[k], 4, precision, compensated=comp)
+        assert np.array_equal(hL[k], h1) and np.array_equal(uL[k], u1), k
+
+
+@pytest.mark.parametrize("L", [3, 4])
+def test_layers_match_oracle_each(sphw, L):
+    n = 10
     h0, u0 = perturbed(sphw, L)
     hL, uL, _ = run(sphw, h0, u0, n, lts.LTS_FP64, layers=L)
     o = oracle.Oracle(sphw.mesh)
@@ -58,21 +74,22 @@ def test_layers_match_oracle_each(sphw):
         assert rel(hL[k], rh) <= 1e-12 and rel(uL[k], ru) <= 1e-12, k
 
 
+@pytest.mark.parametrize("precision", [lts.LTS_FP64, lts.LTS_FP32])
 @pytest.mark.parametrize("mode,order", [(lts.LTS_MODE_LTS, 2), (lts.LTS_MODE_SSPRK3, 3)])
-def test_layers_other_integrators(sphw, mode, order):
+def test_layers_other_integrators(sphw, mode, order, precision):
     L = 4
     dt = sphw.dt / (2 * sphw.M)
-    with lts.Model(sphw.mesh, sphw.fine_mask, sphw.M, sphw.h0, sphw.u0, dt, sphw.g,
-                   precision=lts.LTS_FP64, mode=mode, order=order) as m:
-        m.step(3)
-        h1, u1, _ = m.read()
-    with lts.Model(sphw.mesh, sphw.fine_mask, sphw.M, np.tile(sphw.h0, (L, 1)),
-                   np.tile(sphw.u0, (L, 1)), dt, sphw.g, precision=lts.LTS_FP64, mode=mode,
-                   order=order, layers=L) as m:
+    h0, u0 = perturbed(sphw, L)
+    with lts.Model(sphw.mesh, sphw.fine_mask, sphw.M, h0, u0, dt, sphw.g, precision=precision,
+                   mode=mode, order=order, layers=L) as m:
         m.step(3)
         hL, uL, _ = m.read()
     for k in range(L):
-        assert np.array_equal(hL[k], h1) and np.array_equal(uL[k], u1)
+        with lts.Model(sphw.mesh, sphw.fine_mask, sphw.M, h0[k], u0[k], dt, sphw.g,
+                       precision=precision, mode=mode, order=order) as m:
+            m.step(3)
+            h1, u1, _ = m.read()
+        assert np.array_equal(hL[k], h1) and np.array_equal(uL[k], u1), k
 
 
 def test_layers_write_read_roundtrip_and_checks(sphw):
