@@ -284,14 +284,15 @@ def oracle_single_thread(w, budget_s=20.0):
     return w.nCells * steps / t, steps, t
 
 
-def oracle_sample(w, nsteps_cap=3, budget_s=20.0):
-    """Times the FP64 oracle's LTS3 coarse step on the full workload; returns
+def oracle_sample(w, nsteps_cap=3, budget_s=20.0, h0=None, u0=None):
+    """Times the FP64 oracle's LTS3 coarse step on the full workload (from
+    h0, u0 when given, else the workload's initial state); returns
     (cell-updates/s, steps, seconds, threads, result)."""
     import oracle
 
     o = oracle.Oracle(w.mesh)
     labels = oracle_labels(o, w)
-    h, u = w.h0, w.u0
+    h, u = (w.h0, w.u0) if h0 is None else (h0, u0)
     steps, t_total = 0, 0.0
     while steps < nsteps_cap and t_total < budget_s:
         t0 = time.perf_counter()
@@ -509,6 +510,27 @@ def run_lts(args):
         line["error_vs_oracle_1step"] = {
             "h_rel_maxnorm": float(np.max(np.abs(h1 - rh)) / np.max(np.abs(rh))),
             "u_rel_maxnorm": float(np.max(np.abs(u1 - ru)) / np.max(np.abs(ru)))}
+    if L > 1 and not args.no_extras and rank == 0:
+        # multi-layer state: the oracle's coarse step on three of its layers
+        # (first, middle, last) and the GPU's error on them after one step
+        sample = sorted({0, L // 2, L - 1})
+        one = lts.Model(w.mesh, w.fine_mask, w.M, h0, u0, w.dt, w.g, precision=prec, compensated=True,
+                        stream=stream.cuda_stream, layers=L, order=w.order,
+                        interface_layers=w.interface_layers)
+        one.step(1)
+        h1, u1, _ = one.read()
+        one.close()
+        t_or, eh, eu, cores = 0.0, 0.0, 0.0, 1
+        for k in sample:
+            _, _, t, cores, (rh, ru) = oracle_sample(w, nsteps_cap=1, h0=h0[k], u0=u0[k])
+            t_or += t
+            eh = max(eh, float(np.max(np.abs(h1[k] - rh)) / np.max(np.abs(rh))))
+            eu = max(eu, float(np.max(np.abs(u1[k] - ru)) / np.max(np.abs(ru))))
+        line["cpu_baseline"] = {"value": w.nCells * len(sample) / t_or, "unit": UNIT, "cores": cores,
+                                "kind": "oracle", "cpu": cpu_model(),
+                                "sample": f"one coarse step of layers {sample} of the full mesh by the FP64 C "
+                                          f"oracle ({scheme(w)}, {t_or:.1f} s; cell-layer updates)"}
+        line["error_vs_oracle_1step"] = {"layers": sample, "h_rel_maxnorm": eh, "u_rel_maxnorm": eu}
     if not args.no_extras and rank == 0 and L == 1 and not np.ndim(w.M) and not is_variant(w):
         args._ms = ms
         line.update(extras(args, w, model, stats, stream, h_gpu, u_gpu, diag))

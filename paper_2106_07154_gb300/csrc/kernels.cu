@@ -55,6 +55,8 @@ struct DevArgs {
     int G;            // multi-layer states: thread groups per element, ceil(L / lpt)
     int v2;           // multi-layer states: 1 when every pair of layers a thread runs is one
                       // aligned two-word access (checked on the host), else 0
+    int v4;           // FP32 multi-layer states: 1 when every thread's four layers are one
+                      // aligned four-word access (checked on the host), else 0
     // segment-table launches (ensembles): segments in device memory
     const DevSeg<T>* gseg;
     int ngseg;
@@ -165,6 +167,51 @@ __device__ __forceinline__ void st_hint(double* q, double2 v, uint64_t p) {
     asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1, %2}, %3;" ::"l"(q), "d"(v.x), "d"(v.y), "l"(p)
                  : "memory");
 }
+// W consecutive layers of one element (W = 2 or 4 words) in one access, for
+// launches whose host has checked that every such group is aligned to its
+// size.
+template <class T, int W>
+struct Lanes {
+    T v[W];
+};
+template <int W>
+__device__ __forceinline__ Lanes<float, W> ld_lanes(const float* q, uint64_t p) {
+    static_assert(W == 2 || W == 4, "two or four FP32 words per access");
+    Lanes<float, W> r;
+    if constexpr (W == 2) {
+        const float2 x = ld_state2(q, p);
+        r.v[0] = x.x, r.v[1] = x.y;
+    } else {
+        asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                     : "=f"(r.v[0]), "=f"(r.v[1]), "=f"(r.v[2]), "=f"(r.v[3]) : "l"(q), "l"(p) : "memory");
+    }
+    return r;
+}
+template <int W>
+__device__ __forceinline__ Lanes<double, W> ld_lanes(const double* q, uint64_t p) {
+    static_assert(W == 2, "two FP64 words per access");
+    const double2 x = ld_state2(q, p);
+    Lanes<double, W> r;
+    r.v[0] = x.x, r.v[1] = x.y;
+    return r;
+}
+template <int W>
+__device__ __forceinline__ void st_lanes(float* q, const Lanes<float, W>& v, uint64_t p) {
+    static_assert(W == 2 || W == 4, "two or four FP32 words per access");
+    if constexpr (W == 2) {
+        st_hint(q, make_float2(v.v[0], v.v[1]), p);
+    } else {
+        asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(q), "f"(v.v[0]),
+                     "f"(v.v[1]), "f"(v.v[2]), "f"(v.v[3]), "l"(p)
+                     : "memory");
+    }
+}
+template <int W>
+__device__ __forceinline__ void st_lanes(double* q, const Lanes<double, W>& v, uint64_t p) {
+    static_assert(W == 2, "two FP64 words per access");
+    st_hint(q, make_double2(v.v[0], v.v[1]), p);
+}
+
 // Policy of a launch mode's state accesses (see above): the fine launches'
 // state goes first, like the coarse launches' data.
 __device__ __forceinline__ int state_mode(int m) { return m == 1 ? 2 : m; }
@@ -177,6 +224,9 @@ struct St {
     // words q[0], q[1] (two layers) in one aligned access
     template <class V>
     __device__ __forceinline__ void pair(V* q, vec2_t<V> v) const { st_hint(q, v, pol); }
+    // words q[0..W-1] (W layers) in one aligned access
+    template <int W, class V>
+    __device__ __forceinline__ void lanes(V* q, const Lanes<V, W>& v) const { st_lanes<W>(q, v, pol); }
 };
 
 // Read-only loads with the launch's L2 policy: `stat` for mesh tables, `operator()`
@@ -191,6 +241,9 @@ struct Ld {
     // state words q[0], q[1] (two layers) in one aligned access
     template <class V>
     __device__ __forceinline__ vec2_t<V> pair(const V* q) const { return ld_state2(q, spol); }
+    // state words q[0..W-1] (W layers) in one aligned access
+    template <int W, class V>
+    __device__ __forceinline__ Lanes<V, W> lanes(const V* q) const { return ld_lanes<W>(q, spol); }
 };
 
 // ------------------------------------------------------------------ layers
@@ -320,36 +373,34 @@ __device__ __forceinline__ void epi_load(const Ld& ld, const DevSeg<T>& s, int m
     }
 }
 
-// epi_load of two consecutive layers (y.l, y.l + 1) with one access per array.
-template <class T, bool COMP>
-__device__ __forceinline__ void epi_load_pair(const Ld& ld, const DevSeg<T>& s, int mode, int i, const T* in_x,
-                                              EpiOps<T>& o0, EpiOps<T>& o1, const Lay<true>& y) {
-    using V = vec2_t<T>;
+// epi_load of W consecutive layers (y.l .. y.l + W - 1) with one access per
+// array.
+template <class T, bool COMP, int W>
+__device__ __forceinline__ void epi_load_group(const Ld& ld, const DevSeg<T>& s, int mode, int i, const T* in_x,
+                                               EpiOps<T> (&o)[W], const Lay<true>& y) {
     if (mode == EPI_ACC) {
         if (s.flag) {
-            o0.oh = o1.oh = T(0);
+#pragma unroll
+            for (int k = 0; k < W; ++k) o[k].oh = T(0);
         } else {
-            const V v = ld.pair((const T*)s.p[0] + y(i - s.base));
-            o0.oh = v.x, o1.oh = v.y;
+            const Lanes<T, W> v = ld.lanes<W>((const T*)s.p[0] + y(i - s.base));
+#pragma unroll
+            for (int k = 0; k < W; ++k) o[k].oh = v.v[k];
         }
     } else if (mode == EPI_UPD) {
-        const V oh = ld.pair((const T*)s.p[0] + y(i));
-        o0.oh = oh.x, o1.oh = oh.y;
+        const Lanes<T, W> oh = ld.lanes<W>((const T*)s.p[0] + y(i));
+#pragma unroll
+        for (int k = 0; k < W; ++k) o[k].oh = oh.v[k], o[k].ol = T(0), o[k].xl = T(0);
         if (COMP) {
-            const V ol = ld.pair((const T*)s.p[1] + y(i));
-            o0.ol = ol.x, o1.ol = ol.y;
-        } else {
-            o0.ol = o1.ol = T(0);
+            const Lanes<T, W> ol = ld.lanes<W>((const T*)s.p[1] + y(i));
+            const Lanes<T, W> xl = ld.lanes<W>((const T*)s.p[2] + y(i));
+#pragma unroll
+            for (int k = 0; k < W; ++k) o[k].ol = ol.v[k], o[k].xl = xl.v[k];
         }
         if (in_x) {
-            const V x = ld.pair(in_x + y(i));
-            o0.xh = x.x, o1.xh = x.y;
-        }
-        if (COMP) {
-            const V xl = ld.pair((const T*)s.p[2] + y(i));
-            o0.xl = xl.x, o1.xl = xl.y;
-        } else {
-            o0.xl = o1.xl = T(0);
+            const Lanes<T, W> x = ld.lanes<W>(in_x + y(i));
+#pragma unroll
+            for (int k = 0; k < W; ++k) o[k].xh = x.v[k];
         }
     }
 }
@@ -616,16 +667,16 @@ __device__ __forceinline__ T ring_pass(const DevArgs<T>& a, int c, const Lay<LY>
 // ring core runs on both at once.  The
 // cells' update operands are loaded with the gathers (the many waves of a
 // multi-layer launch leave the registers for them), so the pass has one
-// dependent round trip after the wait; o0.xh, o1.xh are the input
+// dependent round trip after the wait; o[0].xh, o[1].xh are the input
 // thicknesses the ring reads anyway.
 template <bool COMP, int NR>
 __device__ __forceinline__ float2 ring_body_pair(const DevArgs<float>& a, const Ld& ld, int c, int n, float rA,
                                                  const RingSlot<float> (&S0)[UNCOND], const Lay<true>& y0,
-                                                 EpiOps<float>& o0, EpiOps<float>& o1) {
+                                                 EpiOps<float> (&o)[2]) {
     const int N = a.t.nC;
     const float2 hc = ld.pair(a.in_h + y0(c));
-    o0.xh = hc.x;
-    o1.xh = hc.y;
+    o[0].xh = hc.x;
+    o[1].xh = hc.y;
     float2 uj[NR], hn[NR], qv[NR], snl[NR], Rj[NR], sK[NR], C[NR];
 #pragma unroll
     for (int j = 0; j < NR; ++j) {
@@ -649,7 +700,7 @@ __device__ __forceinline__ float2 ring_body_pair(const DevArgs<float>& a, const 
 
 template <bool COMP, int MAXR>
 __device__ __forceinline__ float2 ring_pass_pair(const DevArgs<float>& a, const DevSeg<float>& s, int epi, int c,
-                                                 const Lay<true>& y0, EpiOps<float>& o0, EpiOps<float>& o1) {
+                                                 const Lay<true>& y0, EpiOps<float> (&o)[2]) {
     const Tables<float>& t = a.t;
     const Ld ld(a.l2);
     const int n = ld.stat(t.cn + c);
@@ -658,14 +709,14 @@ __device__ __forceinline__ float2 ring_pass_pair(const DevArgs<float>& a, const 
     for (int j = 0; j < UNCOND; ++j) S0[j] = ring_slot(t, ld, j, c);
     const float rA = ld.stat(t.rA + c);
     griddep_wait();
-    epi_load_pair<float, COMP>(ld, s, epi, c, nullptr, o0, o1, y0);
+    epi_load_group<float, COMP, 2>(ld, s, epi, c, nullptr, o, y0);
     const int nmax = __reduce_max_sync(__activemask(), n);
-    if (nmax <= 6) return ring_body_pair<COMP, 6>(a, ld, c, n, rA, S0, y0, o0, o1);
+    if (nmax <= 6) return ring_body_pair<COMP, 6>(a, ld, c, n, rA, S0, y0, o);
     if (nmax <= 7 || MAXR <= 7)
-        return ring_body_pair<COMP, (MAXR < 7 ? MAXR : 7)>(a, ld, c, n, rA, S0, y0, o0, o1);
+        return ring_body_pair<COMP, (MAXR < 7 ? MAXR : 7)>(a, ld, c, n, rA, S0, y0, o);
     if (nmax <= 8 || MAXR <= 8)
-        return ring_body_pair<COMP, (MAXR < 8 ? MAXR : 8)>(a, ld, c, n, rA, S0, y0, o0, o1);
-    return ring_body_pair<COMP, MAXR>(a, ld, c, n, rA, S0, y0, o0, o1);
+        return ring_body_pair<COMP, (MAXR < 8 ? MAXR : 8)>(a, ld, c, n, rA, S0, y0, o);
+    return ring_body_pair<COMP, MAXR>(a, ld, c, n, rA, S0, y0, o);
 }
 
 // --------------------------------------------------------------- kind 2: edge
@@ -960,26 +1011,28 @@ __device__ __forceinline__ void epilogue(const DevArgs<T>& a, const DevSeg<T>& s
     if (!ok) atomicOr(a.flag, IS_CELL ? 1 : 2);
 }
 
-// The epilogue of two consecutive layers (y.l, y.l + 1): each layer's
+// The epilogue of W consecutive layers (y.l .. y.l + W - 1): each layer's
 // arithmetic is the single-layer epilogue's, the stores one access per array.
-template <class T, bool COMP, bool IS_CELL>
-__device__ __forceinline__ void epilogue_pair(const DevArgs<T>& a, const DevSeg<T>& s, int epi, int i, T R0, T R1,
-                                              const EpiOps<T>& o0, const EpiOps<T>& o1, const Lay<true>& y) {
-    using V = vec2_t<T>;
+template <class T, bool COMP, bool IS_CELL, int W>
+__device__ __forceinline__ void epilogue_group(const DevArgs<T>& a, const DevSeg<T>& s, int epi, int i,
+                                               const T (&R)[W], const EpiOps<T> (&o)[W], const Lay<true>& y) {
     const St st(a.l2);
     if (epi == EPI_ACC) {
-        V v;
-        v.x = s.flag ? R0 : o0.oh + R0;
-        v.y = s.flag ? R1 : o1.oh + R1;
-        st.pair((T*)s.p[0] + y(i - s.base), v);
+        Lanes<T, W> v;
+#pragma unroll
+        for (int k = 0; k < W; ++k) v.v[k] = s.flag ? R[k] : o[k].oh + R[k];
+        st.lanes<W>((T*)s.p[0] + y(i - s.base), v);
         return;
     }
-    V yh, yl;
-    combine<T, COMP>(o0.oh, o0.ol, o0.xh, o0.xl, s.c[0], s.c[1], R0, yh.x, yl.x);
-    combine<T, COMP>(o1.oh, o1.ol, o1.xh, o1.xl, s.c[0], s.c[1], R1, yh.y, yl.y);
-    st.pair((T*)s.p[3] + y(i), yh);
-    if (COMP) st.pair((T*)s.p[4] + y(i), yl);
-    const bool ok = IS_CELL ? finite_pos(yh.x) && finite_pos(yh.y) : finite_val(yh.x) && finite_val(yh.y);
+    Lanes<T, W> yh, yl;
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+        combine<T, COMP>(o[k].oh, o[k].ol, o[k].xh, o[k].xl, s.c[0], s.c[1], R[k], yh.v[k], yl.v[k]);
+        ok = ok && (IS_CELL ? finite_pos(yh.v[k]) : finite_val(yh.v[k]));
+    }
+    st.lanes<W>((T*)s.p[3] + y(i), yh);
+    if (COMP) st.lanes<W>((T*)s.p[4] + y(i), yl);
     if (!ok) atomicOr(a.flag, IS_CELL ? 1 : 2);
 }
 
@@ -1024,46 +1077,54 @@ __device__ __forceinline__ void element_work(const DevArgs<T>& a, const DevSeg<T
     }
 }
 
-// Vertex and edge work of two consecutive layers (y.l and y.l + 1) of a
-// multi-layer state: each state word is one aligned two-word access for both
-// layers, all of them out before either layer's arithmetic, so the pair
-// costs one dependent round trip; each layer's arithmetic is the
-// single-layer code's.
-template <class T, bool COMP, int KIND>
-__device__ __forceinline__ void pair_work(const DevArgs<T>& a, const DevSeg<T>& s, int i, const Lay<true>& y0) {
-    using V = vec2_t<T>;
+// Vertex and edge work of W consecutive layers (y.l .. y.l + W - 1) of a
+// multi-layer state: each state word is one aligned W-word access for all
+// W layers, all of them out before any layer's arithmetic, so the group
+// costs one dependent round trip and one set of table loads; each layer's
+// arithmetic is the single-layer code's.
+template <class T, bool COMP, int KIND, int W>
+__device__ __forceinline__ void group_work(const DevArgs<T>& a, const DevSeg<T>& s, int i, const Lay<true>& y0) {
+    using G = Lanes<T, W>;
     const Ld ld(a.l2);
     if (KIND == 0) {
         VertStat<T> vs;
         vertex_stat(a.t, ld, i, vs);
         griddep_wait();
-        const V u0 = ld.pair(a.in_u + y0(vs.e0)), u1 = ld.pair(a.in_u + y0(vs.e1)), u2 = ld.pair(a.in_u + y0(vs.e2));
-        const V h0 = ld.pair(a.in_h + y0(vs.c0)), h1 = ld.pair(a.in_h + y0(vs.c1)), h2 = ld.pair(a.in_h + y0(vs.c2));
-        V q;
-        q.x = q_value(vs.d0, vs.d1, vs.d2, u0.x, u1.x, u2.x, vs.k0, vs.k1, vs.k2, h0.x, h1.x, h2.x, vs.f);
-        q.y = q_value(vs.d0, vs.d1, vs.d2, u0.y, u1.y, u2.y, vs.k0, vs.k1, vs.k2, h0.y, h1.y, h2.y, vs.f);
-        St(a.l2).pair(a.q + y0(i), q);
+        const G u0 = ld.lanes<W>(a.in_u + y0(vs.e0)), u1 = ld.lanes<W>(a.in_u + y0(vs.e1)),
+                u2 = ld.lanes<W>(a.in_u + y0(vs.e2));
+        const G h0 = ld.lanes<W>(a.in_h + y0(vs.c0)), h1 = ld.lanes<W>(a.in_h + y0(vs.c1)),
+                h2 = ld.lanes<W>(a.in_h + y0(vs.c2));
+        G q;
+#pragma unroll
+        for (int k = 0; k < W; ++k)
+            q.v[k] = q_value(vs.d0, vs.d1, vs.d2, u0.v[k], u1.v[k], u2.v[k], vs.k0, vs.k1, vs.k2, h0.v[k], h1.v[k],
+                             h2.v[k], vs.f);
+        St(a.l2).lanes<W>(a.q + y0(i), q);
     } else {
         const int epi = s.type == SEG_EDGE_ACC ? EPI_ACC : EPI_UPD;
         EdgeStat<T> es;
         edge_stat(a.t, ld, i, es);
         griddep_wait();
-        EpiOps<T> o0, o1;
-        epi_load_pair<T, COMP>(ld, s, epi, i, a.in_u, o0, o1, y0);
+        EpiOps<T> o[W];
+        epi_load_group<T, COMP, W>(ld, s, epi, i, a.in_u, o, y0);
         const int N = a.t.nC;
-        const V C0 = ld.pair(a.ring_c + y0(es.p0 * N + es.c0)), C1 = ld.pair(a.ring_c + y0(es.p1 * N + es.c1));
-        const V h0 = ld.pair(a.in_h + y0(es.c0)), h1 = ld.pair(a.in_h + y0(es.c1));
-        V hl0, hl1;
+        const G C0 = ld.lanes<W>(a.ring_c + y0(es.p0 * N + es.c0)), C1 = ld.lanes<W>(a.ring_c + y0(es.p1 * N + es.c1));
+        const G h0 = ld.lanes<W>(a.in_h + y0(es.c0)), h1 = ld.lanes<W>(a.in_h + y0(es.c1));
+        G hl0, hl1;
         if (COMP) {
-            hl0 = ld.pair(a.in_hl + y0(es.c0));
-            hl1 = ld.pair(a.in_hl + y0(es.c1));
+            hl0 = ld.lanes<W>(a.in_hl + y0(es.c0));
+            hl1 = ld.lanes<W>(a.in_hl + y0(es.c1));
         } else {
-            hl0.x = hl0.y = hl1.x = hl1.y = T(0);
+#pragma unroll
+            for (int k = 0; k < W; ++k) hl0.v[k] = hl1.v[k] = T(0);
         }
-        const V K0 = ld.pair(a.ring_k + y0(es.c0)), K1 = ld.pair(a.ring_k + y0(es.c1));
-        const T U0 = edge_u<T, COMP>(C0.x, C1.x, h0.x, h1.x, hl0.x, hl1.x, K0.x, K1.x, es.db, es.rdc, a.g);
-        const T U1 = edge_u<T, COMP>(C0.y, C1.y, h0.y, h1.y, hl0.y, hl1.y, K0.y, K1.y, es.db, es.rdc, a.g);
-        epilogue_pair<T, COMP, false>(a, s, epi, i, U0, U1, o0, o1, y0);
+        const G K0 = ld.lanes<W>(a.ring_k + y0(es.c0)), K1 = ld.lanes<W>(a.ring_k + y0(es.c1));
+        T U[W];
+#pragma unroll
+        for (int k = 0; k < W; ++k)
+            U[k] = edge_u<T, COMP>(C0.v[k], C1.v[k], h0.v[k], h1.v[k], hl0.v[k], hl1.v[k], K0.v[k], K1.v[k], es.db,
+                                   es.rdc, a.g);
+        epilogue_group<T, COMP, false, W>(a, s, epi, i, U, o, y0);
     }
 }
 
@@ -1094,19 +1155,31 @@ __device__ __forceinline__ void phase_block(const DevArgs<T>& a, const DevSeg<T>
 #pragma unroll 1
                 for (; k + 1 < nl; k += 2) {
                     y.l = l0 + k;
-                    EpiOps<T> o0, o1;
-                    const float2 H = ring_pass_pair<COMP, MAXR>(a, s, epi, i, y, o0, o1);
-                    if (epi != EPI_NONE) epilogue_pair<T, COMP, true>(a, s, epi, i, H.x, H.y, o0, o1, y);
+                    EpiOps<T> o[2];
+                    const float2 H = ring_pass_pair<COMP, MAXR>(a, s, epi, i, y, o);
+                    if (epi != EPI_NONE) {
+                        const T R[2] = {H.x, H.y};
+                        epilogue_group<T, COMP, true, 2>(a, s, epi, i, R, o, y);
+                    }
                 }
             }
         }
         if constexpr (KIND == 0 || KIND == 2) {
             if (a.v2 && ((KIND == 0 && s.type == SEG_VERT) ||
                          (KIND == 2 && (s.type == SEG_EDGE_UPD || s.type == SEG_EDGE_ACC)))) {
+                if constexpr (sizeof(T) == 4) {
+                    // four layers in one pass where the host found every
+                    // group of four aligned
+                    if (a.v4 && nl == 4) {
+                        y.l = l0;
+                        group_work<T, COMP, KIND, 4>(a, s, i, y);
+                        k = 4;
+                    }
+                }
 #pragma unroll 1
                 for (; k + 1 < nl; k += 2) {
                     y.l = l0 + k;
-                    pair_work<T, COMP, KIND>(a, s, i, y);
+                    group_work<T, COMP, KIND, 2>(a, s, i, y);
                 }
             }
         }
@@ -1291,20 +1364,23 @@ void fill_args(DevArgs<T>& a, const LaunchDesc& d, const void* tables, int smem,
     a.lpt = 1;
     a.G = 1;
     a.v2 = 0;
+    a.v4 = 0;
     a.gseg = nullptr;
     a.ngseg = 0;
     a.vblocks = 0;
     a.L = 1;
 }
 
-// Multi-layer launches: a pair of layers (l, l + 1) of element x sits at
-// words x L + l and x L + l + 1; with L and every pair's first layer even
-// (L and the layers per thread even) and every array the launch touches
-// aligned to two words, each pair is one aligned two-word access.
+// Multi-layer launches: W consecutive layers (l .. l + W - 1) of element x
+// sit at words x L + l .. x L + l + W - 1.  With L and every group's first
+// layer multiples of W (L and the layers per thread multiples of W) and
+// every array the launch touches aligned to W words, each group is one
+// aligned W-word access.
 template <class T>
-bool pairs_aligned(const DevArgs<T>& a, const LaunchDesc& d) {
-    if (a.L < 2 || (a.L & 1) || (a.lpt & 1)) return false;
-    auto ok = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) % (2 * sizeof(T))) == 0; };
+bool groups_aligned(const DevArgs<T>& a, const LaunchDesc& d, int W) {
+    if (a.L < W || a.L % W || a.lpt % W) return false;
+    const uintptr_t bytes = static_cast<uintptr_t>(W) * sizeof(T);
+    auto ok = [bytes](const void* p) { return (reinterpret_cast<uintptr_t>(p) % bytes) == 0; };
     if (!ok(a.in_h) || !ok(a.in_hl) || !ok(a.in_u) || !ok(a.in_ul) || !ok(a.q) || !ok(a.ring_c) || !ok(a.ring_k))
         return false;
     for (int k = 0; k < d.nseg; ++k)
@@ -1329,7 +1405,8 @@ cudaError_t launch_t(const LaunchDesc& d, const void* tables, int block, bool pd
     a.L = layers;
     a.lpt = layers > 1 ? std::max(1, std::min(lpt, layers)) : 1;
     a.G = (layers + a.lpt - 1) / a.lpt;
-    a.v2 = pairs_aligned(a, d) ? 1 : 0;
+    a.v2 = groups_aligned(a, d, 2) ? 1 : 0;
+    a.v4 = sizeof(T) == 4 && groups_aligned(a, d, 4) ? 1 : 0;
     const bool two = ept == 2 && layers == 1 && (d.kind == 0 || d.kind == 2);
     int blocks = 0, ns = 0;
     for (int k = 0; k < d.nseg; ++k) {

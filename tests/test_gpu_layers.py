@@ -48,13 +48,15 @@ def test_identical_layers_equal_single_layer_bitwise(sphw, precision, L):
 
 
 @pytest.mark.parametrize("precision,comp", [(lts.LTS_FP64, False), (lts.LTS_FP32, True), (lts.LTS_FP32, False)])
-@pytest.mark.parametrize("L", [3, 4, 6])
+@pytest.mark.parametrize("L", [3, 4, 6, 8])
 def test_different_layers_equal_their_single_layer_runs_bitwise(sphw, precision, comp, L):
     """Each layer of a state whose layers differ equals the single-layer run
-    from that layer's initial state, bit for bit.  Even L runs pairs of
-    layers through two-word accesses, so a swapped lane would fail here;
-    L = 6 also has a thread with a single pair (layers 4, 5); odd L runs
-    every layer through the single-layer code."""
+    from that layer's initial state, bit for bit, so a swapped or shifted
+    lane would fail here.  Even L runs pairs of layers through two-word
+    accesses (L = 6 also has a thread with a single pair, layers 4 and 5);
+    with L a multiple of four the FP32 vertex and edge passes run a thread's
+    four layers through four-word accesses (L = 8: two groups per element);
+    odd L runs every layer through the single-layer code."""
     h0, u0 = perturbed(sphw, L)
     hL, uL, _ = run(sphw, h0, u0, 4, precision, layers=L, compensated=comp)
     for k in range(L):
