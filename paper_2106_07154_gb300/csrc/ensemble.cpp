@@ -168,6 +168,15 @@ int build_union_tables(lts_ensemble_s* E, Tables<T>& t) {
         t.sidx = up(sidx);
         t.scf = sizeof(T) == 4 ? up(scf) : nullptr;
     }
+    {
+        std::vector<int4> erow, vri;
+        std::vector<float4> vrd, vrk;
+        pack_edge_vertex_rows<T>(ec0, ec1, ep, rdc, vc, ve, vd, vk, f, erow, vri, vrd, vrk);
+        t.erow = up(erow);
+        t.vri = up(vri);
+        t.vrd = sizeof(T) == 4 ? up(vrd) : nullptr;
+        t.vrk = sizeof(T) == 4 ? up(vrk) : nullptr;
+    }
     t.rA = up(rA);
     t.b = up(b);
     t.ec0 = up(ec0);

@@ -141,6 +141,12 @@ __device__ __forceinline__ int4 ld_static(const int4* q, uint64_t p) {
         : "=r"(x.x), "=r"(x.y), "=r"(x.z), "=r"(x.w) : "l"(q), "l"(p));
     return x;
 }
+__device__ __forceinline__ float4 ld_static(const float4* q, uint64_t p) {
+    float4 x;
+    asm("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=f"(x.x), "=f"(x.y), "=f"(x.z), "=f"(x.w) : "l"(q), "l"(p));
+    return x;
+}
 __device__ __forceinline__ float2 ld_static(const float2* q, uint64_t p) {
     float2 x;
     asm("ld.global.nc.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(x.x), "=f"(x.y) : "l"(q), "l"(p));
@@ -418,11 +424,21 @@ struct VertStat {
 
 template <class T>
 __device__ __forceinline__ void vertex_stat(const Tables<T>& t, const Ld& ld, int v, VertStat<T>& s) {
-    s.e0 = ld.stat(t.ve0 + v), s.e1 = ld.stat(t.ve1 + v), s.e2 = ld.stat(t.ve2 + v);
-    s.c0 = ld.stat(t.vc0 + v), s.c1 = ld.stat(t.vc1 + v), s.c2 = ld.stat(t.vc2 + v);
-    s.d0 = ld.stat(t.vd0 + v), s.d1 = ld.stat(t.vd1 + v), s.d2 = ld.stat(t.vd2 + v);
-    s.k0 = ld.stat(t.vk0 + v), s.k1 = ld.stat(t.vk1 + v), s.k2 = ld.stat(t.vk2 + v);
-    s.f = ld.stat(t.f + v);
+    // packed rows: {e0, e1, e2, c0}, and in FP32 {d0, d1, d2, f}, {k0, k1, k2, c1}
+    const int4 ie = ld.stat(t.vri + v);
+    s.e0 = ie.x, s.e1 = ie.y, s.e2 = ie.z, s.c0 = ie.w;
+    s.c2 = ld.stat(t.vc2 + v);
+    if constexpr (sizeof(T) == 4) {
+        const float4 d = ld.stat(t.vrd + v);
+        const float4 k = ld.stat(t.vrk + v);
+        s.d0 = d.x, s.d1 = d.y, s.d2 = d.z, s.f = d.w;
+        s.k0 = k.x, s.k1 = k.y, s.k2 = k.z, s.c1 = __float_as_int(k.w);
+    } else {
+        s.c1 = ld.stat(t.vc1 + v);
+        s.d0 = ld.stat(t.vd0 + v), s.d1 = ld.stat(t.vd1 + v), s.d2 = ld.stat(t.vd2 + v);
+        s.k0 = ld.stat(t.vk0 + v), s.k1 = ld.stat(t.vk1 + v), s.k2 = ld.stat(t.vk2 + v);
+        s.f = ld.stat(t.f + v);
+    }
 }
 
 // q_v from the vertex's three edge velocities and cell thicknesses, with the
@@ -731,10 +747,13 @@ struct EdgeStat {
 
 template <class T>
 __device__ __forceinline__ void edge_stat(const Tables<T>& t, const Ld& ld, int e, EdgeStat<T>& s) {
-    s.c0 = ld.stat(t.ec0 + e), s.c1 = ld.stat(t.ec1 + e);
-    const uint32_t pp = ld.stat(t.ep + e);
+    // packed row {c0, c1, ep, the bits of 1/d_e in FP32}
+    const int4 r = ld.stat(t.erow + e);
+    s.c0 = r.x, s.c1 = r.y;
+    const uint32_t pp = static_cast<uint32_t>(r.z);
     s.p0 = pp & 0xff, s.p1 = (pp >> 8) & 0xff;
-    s.rdc = ld.stat(t.rdc + e);
+    if constexpr (sizeof(T) == 4) s.rdc = __int_as_float(r.w);
+    else s.rdc = ld.stat(t.rdc + e);
     s.db = ld.stat(t.db + e);
 }
 
@@ -1389,17 +1408,21 @@ bool groups_aligned(const DevArgs<T>& a, const LaunchDesc& d, int W) {
     return true;
 }
 
-// A table set without the ring pass's packed slot rows cannot run a ring
-// launch: refused on the host instead of faulting on the device.
+// A table set without the packed rows a launch kind reads (the ring pass's
+// slot rows, the vertex and edge passes' rows) cannot run that kind:
+// refused on the host instead of faulting on the device.
 template <class T>
-bool ring_tables_ok(const Tables<T>& t) {
+bool tables_ok(const Tables<T>& t, int kind) {
+    if (kind == 0) return t.vri != nullptr && (sizeof(T) != 4 || (t.vrd != nullptr && t.vrk != nullptr));
+    if (kind == 2) return t.erow != nullptr;
+    if (kind != 1) return true;
     return t.sidx != nullptr && (sizeof(T) != 4 || t.scf != nullptr);
 }
 
 template <class T, bool COMP, int MAXR>
 cudaError_t launch_t(const LaunchDesc& d, const void* tables, int block, bool pdl, int smem, int* flag,
                      cudaStream_t st, int layers, int ring_occ, int ept, int lpt) {
-    if (d.kind == 1 && !ring_tables_ok(*static_cast<const Tables<T>*>(tables))) return cudaErrorInvalidValue;
+    if (!tables_ok(*static_cast<const Tables<T>*>(tables), d.kind)) return cudaErrorInvalidValue;
     DevArgs<T> a;
     fill_args(a, d, tables, smem, flag);
     a.L = layers;
@@ -1453,7 +1476,7 @@ cudaError_t launch_t(const LaunchDesc& d, const void* tables, int block, bool pd
 template <class T, bool COMP, int MAXR>
 cudaError_t launch_table_t(const LaunchDesc& d, const void* dsegs, int nseg, int vblocks, int grid,
                            const void* tables, int block, bool pdl, int* flag, cudaStream_t st) {
-    if (d.kind == 1 && !ring_tables_ok(*static_cast<const Tables<T>*>(tables))) return cudaErrorInvalidValue;
+    if (!tables_ok(*static_cast<const Tables<T>*>(tables), d.kind)) return cudaErrorInvalidValue;
     DevArgs<T> a;
     fill_args(a, d, tables, 0, flag);
     a.nseg = 0;

@@ -77,6 +77,15 @@ int build_tables(lts_regions_s* R, int which, Tables<T>& t) {
         t.sidx = up(sidx);
         t.scf = sizeof(T) == 4 ? up(scf) : nullptr;
     }
+    {
+        std::vector<int4> erow, vri;
+        std::vector<float4> vrd, vrk;
+        pack_edge_vertex_rows<T>(r.ec0, r.ec1, r.ep, co.rdc, r.vc, r.ve, co.vd, co.vk, co.f, erow, vri, vrd, vrk);
+        t.erow = up(erow);
+        t.vri = up(vri);
+        t.vrd = sizeof(T) == 4 ? up(vrd) : nullptr;
+        t.vrk = sizeof(T) == 4 ? up(vrk) : nullptr;
+    }
     t.rA = up(co.rA);
     t.b = up(co.b);
     t.ec0 = up(r.ec0);

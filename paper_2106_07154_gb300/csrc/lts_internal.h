@@ -51,6 +51,14 @@ struct Tables {
     const T* vk0; const T* vk1; const T* vk2;         // [nV] A_{c,v} / A_v
     const T* vd0; const T* vd1; const T* vd2;         // [nV] t_{e,v} d_e / A_v
     const T* f;                                        // [nV] Coriolis parameter
+    // the edge and vertex operands packed for the vector loads of the edge
+    // and vertex passes: {ec0, ec1, ep, the bits of rdc in FP32 (0 in FP64)},
+    // {ve0, ve1, ve2, vc0} and, in FP32 only, {vd0, vd1, vd2, f} and
+    // {vk0, vk1, vk2, the bits of vc1} (vc2 stays a plain array)
+    const int4* erow;    // [nE]
+    const int4* vri;     // [nV]
+    const float4* vrd;   // [nV]  (FP32 tables only)
+    const float4* vrk;   // [nV]  (FP32 tables only)
     // tiles of the fused kernel (kind 3)
     const int4* ta;      // [ntiles] {cell begin, own cells, halo begin, local cells}
     const int4* tbk;     // [ntiles] {edge begin, edge end, vertex-list begin, local vertices}

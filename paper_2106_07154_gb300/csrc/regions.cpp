@@ -514,6 +514,54 @@ template void pack_ring_slots<double>(const std::vector<int>&, const std::vector
                                       const std::vector<double>&, const std::vector<double>&,
                                       const std::vector<double>&, std::vector<int4>&, std::vector<float2>&);
 
+template <class T>
+void pack_edge_vertex_rows(const std::vector<int>& ec0, const std::vector<int>& ec1,
+                           const std::vector<uint32_t>& ep, const std::vector<T>& rdc, const std::vector<int>& vc,
+                           const std::vector<int>& ve, const std::vector<T>& vd, const std::vector<T>& vk,
+                           const std::vector<T>& f, std::vector<int4>& erow, std::vector<int4>& vri,
+                           std::vector<float4>& vrd, std::vector<float4>& vrk) {
+    const bool fp32 = sizeof(T) == 4;
+    auto bits = [](T x) {
+        const float y = static_cast<float>(x);
+        int b = 0;
+        std::memcpy(&b, &y, sizeof(b));
+        return b;
+    };
+    auto as_float = [](int x) {
+        float y = 0.f;
+        std::memcpy(&y, &x, sizeof(y));
+        return y;
+    };
+    const size_t nE = ec0.size(), nV = f.size();
+    erow.resize(nE);
+    for (size_t e = 0; e < nE; ++e)
+        erow[e] = int4{ec0[e], ec1[e], static_cast<int>(ep[e]), fp32 ? bits(rdc[e]) : 0};
+    vri.resize(nV);
+    vrd.assign(fp32 ? nV : 0, float4{});
+    vrk.assign(fp32 ? nV : 0, float4{});
+    for (size_t v = 0; v < nV; ++v) {
+        vri[v] = int4{ve[v], ve[nV + v], ve[2 * nV + v], vc[v]};
+        if (fp32) {
+            vrd[v] = float4{static_cast<float>(vd[v]), static_cast<float>(vd[nV + v]),
+                            static_cast<float>(vd[2 * nV + v]), static_cast<float>(f[v])};
+            vrk[v] = float4{static_cast<float>(vk[v]), static_cast<float>(vk[nV + v]),
+                            static_cast<float>(vk[2 * nV + v]), as_float(vc[nV + v])};
+        }
+    }
+}
+template void pack_edge_vertex_rows<float>(const std::vector<int>&, const std::vector<int>&,
+                                           const std::vector<uint32_t>&, const std::vector<float>&,
+                                           const std::vector<int>&, const std::vector<int>&,
+                                           const std::vector<float>&, const std::vector<float>&,
+                                           const std::vector<float>&, std::vector<int4>&, std::vector<int4>&,
+                                           std::vector<float4>&, std::vector<float4>&);
+template void pack_edge_vertex_rows<double>(const std::vector<int>&, const std::vector<int>&,
+                                            const std::vector<uint32_t>&, const std::vector<double>&,
+                                            const std::vector<int>&, const std::vector<int>&,
+                                            const std::vector<double>&, const std::vector<double>&,
+                                            const std::vector<double>&, std::vector<int4>&, std::vector<int4>&,
+                                            std::vector<float4>&, std::vector<float4>&);
+
 // TRiSK weight of Eq. (weights) for e' = slot j of cell c and e = slot p,
 // with the path taken counter-clockwise from e' to e (used to validate a
 // caller's weightsOnEdge).

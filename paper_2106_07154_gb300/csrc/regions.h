@@ -82,6 +82,18 @@ template <class T>
 void pack_ring_slots(const std::vector<int>& se, const std::vector<int>& sn, const std::vector<int>& sv,
                      const std::vector<T>& snl, const std::vector<T>& sR, const std::vector<T>& sK,
                      std::vector<int4>& sidx, std::vector<float2>& scf);
+// The edge and vertex passes' packed rows (Tables::erow, vri, vrd, vrk)
+// from the plain edge arrays [nE] and the vertex arrays [3 nV] (entry k of
+// vertex v at k nV + v) and f [nV]: {ec0, ec1, ep, the bits of rdc in FP32
+// (0 in FP64)}, {ve0, ve1, ve2, vc0} and, in FP32 only, {vd0, vd1, vd2, f}
+// and {vk0, vk1, vk2, the bits of vc1}.  Every table set the vertex and edge
+// kernels read must carry them.
+template <class T>
+void pack_edge_vertex_rows(const std::vector<int>& ec0, const std::vector<int>& ec1,
+                           const std::vector<uint32_t>& ep, const std::vector<T>& rdc, const std::vector<int>& vc,
+                           const std::vector<int>& ve, const std::vector<T>& vd, const std::vector<T>& vk,
+                           const std::vector<T>& f, std::vector<int4>& erow, std::vector<int4>& vri,
+                           std::vector<float4>& vrd, std::vector<float4>& vrk);
 double derived_weight(const HostMesh& m, int c, int j, int p);
 
 }  // namespace lts
