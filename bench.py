@@ -962,36 +962,50 @@ def run_ensemble(args):
                                "lts_ensemble_read_async of every member with its FP64 diagnostics, "
                                "one lts_ensemble_sync (pinned host buffers, wall clock)",
                        "round_trip": round_trip}
-        # CPU baseline: the oracle on the two smallest members, one coarse step each
+        # CPU baseline: the oracle's coarse step over every member (passes
+        # repeated until about 8 s of oracle time; tables built outside the
+        # timed region), and on one thread over the members in size order
+        # until about 10 s
         import oracle
 
         small = sorted(range(len(ws)), key=lambda i: ws[i].nCells)[:2]
-        t0 = time.perf_counter()
-        cells = 0
-        for i in small:
-            w = ws[i]
+        prepared = []
+        for w in ws:
             o = oracle.Oracle(w.mesh)
             cl, el = o.regions(w.fine_mask)
-            o.lts3(w.h0, w.u0, cl, el, w.M, w.dt, 1, g=w.g)
-            cells += w.nCells
-        t_or = time.perf_counter() - t0
+            prepared.append((o, cl, el))
+
+        def oracle_steps(order, budget_s):
+            t, cells, n = 0.0, 0, 0
+            for i in order:
+                o, cl, el = prepared[i]
+                w = ws[i]
+                t0 = time.perf_counter()
+                o.lts3(w.h0, w.u0, cl, el, w.M, w.dt, 1, g=w.g)
+                t += time.perf_counter() - t0
+                cells += w.nCells
+                n += 1
+                if t >= budget_s:
+                    break
+            return cells, t, n
+
+        cells, t_or, passes = 0, 0.0, 0
+        while t_or < 8.0 and passes < 3:
+            c, t, _ = oracle_steps(range(len(ws)), float("inf"))
+            cells, t_or, passes = cells + c, t_or + t, passes + 1
         line["cpu_baseline"] = {"value": cells / t_or, "unit": UNIT, "cores": oracle.num_threads(),
                                 "kind": "oracle", "cpu": cpu_model(),
-                                "sample": f"one LTS3 coarse step of the two smallest members "
-                                          f"({cells} cells) by the FP64 C oracle ({t_or:.1f} s)"}
+                                "sample": f"{passes} LTS3 coarse step(s) of each of the {len(ws)} members "
+                                          f"({cells} cell-updates) by the FP64 C oracle ({t_or:.1f} s)"}
         cores = oracle.num_threads()
         if set_omp_threads(1):
-            t0 = time.perf_counter()
-            for i in small:
-                w = ws[i]
-                o = oracle.Oracle(w.mesh)
-                cl, el = o.regions(w.fine_mask)
-                o.lts3(w.h0, w.u0, cl, el, w.M, w.dt, 1, g=w.g)
-            t1 = time.perf_counter() - t0
+            by_size = sorted(range(len(ws)), key=lambda i: ws[i].nCells)
+            c1, t1, n1 = oracle_steps(by_size, 10.0)
             set_omp_threads(cores)
             line["cpu_baseline"]["single_thread"] = {
-                "value": cells / t1, "unit": UNIT, "cores": 1,
-                "sample": f"the same step on one thread ({t1:.1f} s)"}
+                "value": c1 / t1, "unit": UNIT, "cores": 1,
+                "sample": f"one coarse step of the {n1} smallest members ({c1} cells) on one thread ({t1:.1f} s)"}
+        del prepared
         # the two smallest members as an ensemble of their own: 20 coarse steps
         # in FP32 against the oracle, and the drift of mass and energy
         nref = 20
