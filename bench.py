@@ -990,7 +990,7 @@ def run_ensemble(args):
             return cells, t, n
 
         cells, t_or, passes = 0, 0.0, 0
-        while t_or < 8.0 and passes < 3:
+        while t_or < 8.0 and passes < 5:
             c, t, _ = oracle_steps(range(len(ws)), float("inf"))
             cells, t_or, passes = cells + c, t_or + t, passes + 1
         line["cpu_baseline"] = {"value": cells / t_or, "unit": UNIT, "cores": oracle.num_threads(),
