@@ -143,7 +143,14 @@ class ClockSampler:
 # --------------------------------------------------------------------- helpers
 
 def kernel_hash() -> str:
-    return hashlib.sha256(KERNEL_SRC.read_bytes()).hexdigest()[:16]
+    """The first 16 hex digits of the sha256 of kernels.cu's code: comments
+    and blank lines removed, so that a comment edit keeps the committed ncu
+    figures while any change to the code retires them."""
+    src = KERNEL_SRC.read_text()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    code = "\n".join(ln.rstrip() for ln in src.splitlines() if ln.strip())
+    return hashlib.sha256(code.encode()).hexdigest()[:16]
 
 
 def hbm_peak():
@@ -161,7 +168,7 @@ def dram_traffic_per_launch():
         text = TRAFFIC_SUMMARY.read_text()
         m = re.search(r"```json\s*(\{.*?\})\s*```", text, re.S)
         data = json.loads(m.group(1))
-        if data.get("kernels_cu_sha256_16") != kernel_hash():
+        if data.get("kernels_cu_code_sha256_16") != kernel_hash():
             return None
         return float(data["ring_dram_bytes_per_launch"])
     except Exception:
@@ -175,7 +182,7 @@ def device_time_shares():
         text = LAUNCH_SUMMARY.read_text()
         m = re.search(r"```json\s*(\{.*?\})\s*```", text, re.S)
         data = json.loads(m.group(1))
-        if data.get("kernels_cu_sha256_16") != kernel_hash():
+        if data.get("kernels_cu_code_sha256_16") != kernel_hash():
             return None
         return data["shares"]
     except Exception:

@@ -255,10 +255,11 @@ struct Ld {
 // ------------------------------------------------------------------ layers
 // Element index -> array index of the state and the intermediates.  A
 // multi-layer state stores the layers of an element next to each other
-// ([element * L + layer]); its kernels run one thread per (element, layer)
-// with the layers fastest, so the threads of a warp share their table loads
-// (one broadcast transaction) and read the state contiguously.  Mesh tables
-// are indexed by the element alone.  The single-layer map is the identity.
+// ([element * L + layer]); its kernels run one thread per (element, group
+// of consecutive layers) with the groups fastest, so the threads of a warp
+// share their table loads (one broadcast transaction) and read the state
+// contiguously.  Mesh tables are indexed by the element alone.  The
+// single-layer map is the identity.
 template <bool LAYERED>
 struct Lay;
 template <>
@@ -1148,11 +1149,12 @@ __device__ __forceinline__ void group_work(const DevArgs<T>& a, const DevSeg<T>&
 }
 
 // The work of (virtual) block `vblk` of segment s.  Multi-layer states run
-// one thread per (element, group of lpt consecutive layers), groups fastest:
-// the thread repeats the element's work for each of its layers, so its mesh
-// table loads (the same addresses for every layer) are issued once and the
-// layers' state accesses are consecutive words.  Each layer's arithmetic is
-// the single-layer code's.
+// one thread per (element, group of lpt consecutive layers), groups fastest.
+// Where the host found the groups aligned, the thread runs its layers two
+// or four at a time (vertex and edge kinds) or two at a time (FP32 ring),
+// each state word one aligned vector access and the mesh table loads issued
+// once per pass; otherwise it repeats the single-layer work for each layer.
+// Each layer's arithmetic is the single-layer code's.
 template <class T, bool COMP, int MAXR, int KIND, bool LY>
 __device__ __forceinline__ void phase_block(const DevArgs<T>& a, const DevSeg<T>& s, int vblk) {
     const int local = (vblk - s.block0) * blockDim.x + threadIdx.x;
